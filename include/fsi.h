@@ -1,0 +1,245 @@
+/* fsi.h - C ABI of libfsi: matrix-free Q1-hexahedral residuals, Jacobian-vector
+ * products and solvers of the fully Eulerian phase-field FSI method of Mao & Jaiman
+ * (arXiv 2402.10348), on one NVIDIA GB300 (sm_103a).
+ *
+ * Conventions (all calls):
+ *  - Every call returns an int status (fsi_status); no exception crosses the ABI.
+ *    On failure fsi_last_error() returns a message (thread-local, valid until the
+ *    next failing call of the same thread).
+ *  - Field arrays are DEVICE pointers owned by the caller, float64 unless stated.
+ *    A nodal state x has ncomp = 4 + N + 6 n_s component planes of nn nodes each,
+ *    component-major ("structure of arrays"):
+ *        x[c*nn + n],  c = 0..2 velocity v, 3 pressure p, 4..4+N-1 phase
+ *        indicators phi^i, 4+N+6s+m component m of the left Cauchy-Green tensor B^s
+ *        of solid s in the order [B11, B22, B33, B12, B23, B13] (Section 2.5,
+ *        second remark), node n = i + (nx+1)*(j + (ny+1)*k).
+ *  - A block vector is the contiguous slice of a state's planes that a block owns:
+ *        NS     planes 0..3        (4 nn values)        Eq. LS_NS
+ *        AC(i)  plane 4+i          (nn values)          Eq. LS_AC
+ *        B(s)   planes 4+N+6s..+5  (6 nn values)        Eq. LS_MC
+ *  - Work is issued on the mesh's stream (fsi_set_stream; default the legacy
+ *    stream) and is asynchronous unless a call says it synchronises.
+ *  - The library owns only the opaque mesh handle and its workspace (allocated
+ *    with cudaMalloc at creation and on first use of a solver, freed by
+ *    fsi_destroy_mesh).
+ */
+#ifndef FSI_H
+#define FSI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FSI_OK = 0,
+  FSI_EINVAL = 1,   /* invalid argument (sizes, indices, null pointers)        */
+  FSI_ECUDA = 2,    /* a CUDA runtime call failed                               */
+  FSI_ENOCONV = 3,  /* a solver did not reach its tolerance                     */
+  FSI_ENAN = 4,     /* a residual or solver norm is NaN or Inf                  */
+  FSI_ETIMEOUT = 5, /* a bounded device-side wait gave up                       */
+  FSI_ENOMEM = 6    /* device allocation failed                                 */
+} fsi_status;
+
+/* Block identifiers. */
+#define FSI_BLOCK_NS 0
+#define FSI_BLOCK_AC(i) (0x10000 | (i))
+#define FSI_BLOCK_B(s) (0x20000 | (s))
+
+/* Velocity boundary kinds of a box face. */
+#define FSI_BC_NATURAL 0   /* no Dirichlet condition (traction-free outflow)      */
+#define FSI_BC_DIRICHLET 1 /* prescribed velocity                                 */
+
+/* Material phase (Section 2.1.1: rho = sum alpha^i rho^i etc.). */
+typedef struct {
+  double rho;      /* density                                                   */
+  double mu;       /* dynamic viscosity                                         */
+  double mu_L;     /* shear modulus of a Neo-Hookean solid (0 for a fluid)      */
+  int32_t is_solid;/* 1: the phase carries a left Cauchy-Green tensor B^s       */
+  int32_t pad;
+} fsi_phase;
+
+typedef struct {
+  int32_t kind;     /* FSI_BC_NATURAL or FSI_BC_DIRICHLET                       */
+  int32_t priority; /* where Dirichlet faces meet, the higher priority wins;
+                       ties: lowest face index (x-, x+, y-, y+, z-, z+)          */
+  double vel[3];
+} fsi_face_bc;
+
+/* Problem on the box [0,lx]x[0,ly]x[0,lz] with nx*ny*nz uniform Q1 hexahedra. */
+typedef struct {
+  int32_t nx, ny, nz;
+  int32_t n_phase;          /* N <= 16, of which n_s <= 16 solids               */
+  double lx, ly, lz;
+  const fsi_phase* phases;  /* host array of n_phase, copied at creation         */
+  double gravity[3];        /* body force per unit mass                          */
+  double eps;               /* interface thickness (Eq. Allen-Cahn)              */
+  double eta;               /* mobility regularisation (Eq. continuous mobility) */
+  double dt;                /* time step                                         */
+  double rho_inf;           /* generalized-alpha spectral radius (paper: 0)      */
+  double c_i;               /* inverse-estimate constant of tau_m                */
+  fsi_face_bc faces[6];     /* x-, x+, y-, y+, z-, z+                            */
+  int32_t has_box;          /* interior box of prescribed velocity (overrides faces) */
+  int32_t pin_node;         /* node with p = 0, or -1                            */
+  double box_lo[3], box_hi[3], box_vel[3];
+  int32_t device;           /* CUDA device ordinal                               */
+  int32_t pad;
+} fsi_mesh_desc;
+
+typedef struct fsi_mesh fsi_mesh;
+
+/* Generalized-alpha state (Section 2.1.2): device arrays of ncomp*nn doubles. */
+typedef struct {
+  double* x;    /* x^{n+1} (the Newton unknown)                                  */
+  double* xn;   /* x^n                                                           */
+  double* xdn;  /* dx/dt^n                                                       */
+} fsi_state;
+
+/* fsi_jvp / fsi_diag flags */
+#define FSI_ELASTIC_AUG 0x1u /* NS: add the solid-stress linearization (Section 2.4) */
+#define FSI_FP32 0x2u        /* evaluate in float32 (inputs/outputs stay float64)  */
+
+/* --------------------------------------------------------------- mesh */
+
+/* Creates a mesh handle (Section 2: the uniform Q1 discretisation of the box,
+ * the phase table, boundary conditions and time-integration parameters).
+ * Validates sizes (n >= 1, N in 1..16, n_s <= 16, eps > 0, dt > 0, ...):
+ * FSI_EINVAL on bad input, FSI_ENOMEM/FSI_ECUDA on device failures. */
+int fsi_create_mesh(const fsi_mesh_desc* desc, fsi_mesh** out);
+int fsi_destroy_mesh(fsi_mesh* mesh);
+/* stream: a cudaStream_t (NULL = legacy default stream). */
+int fsi_set_stream(fsi_mesh* mesh, void* stream);
+/* ncomp, nn, number of solids. */
+int fsi_mesh_info(const fsi_mesh* mesh, int32_t* ncomp, int64_t* nn, int32_t* n_solid);
+
+/* --------------------------------------------------------------- operators */
+
+/* Residual of one block at state st (Eq. PG_NS, Eq. PPV_AC, Eq. semiCGT), written to
+ * the device block vector r_out.  Velocity Dirichlet rows return x - x_D, the pinned
+ * pressure row returns p.  AC blocks use the phase's frozen gamma, beta (see
+ * fsi_update_ac_coeffs / fsi_set_ac_coeffs). */
+int fsi_residual(fsi_mesh* mesh, int32_t block, const fsi_state* st, double* r_out);
+
+/* Jacobian-vector product y = J(st) dx of one block in x^{n+1} with the stabilisation
+ * parameters, gamma, beta and the other blocks' fields frozen at st (Section 2.5).
+ * Dirichlet rows are the identity.  flags: FSI_ELASTIC_AUG, FSI_FP32. */
+int fsi_jvp(fsi_mesh* mesh, int32_t block, const fsi_state* st, const double* dx, double* y,
+            uint32_t flags);
+
+/* Diagonal of the same linear operator (the Jacobi preconditioner). */
+int fsi_diag(fsi_mesh* mesh, int32_t block, const fsi_state* st, double* d_out, uint32_t flags);
+
+/* Time-dependent mobility gamma^i (Section 2.2.2: RMS over nodes with |phi| <= 0.9 of
+ * the lumped L2-projection of |grad phi^T grad v grad phi| / |grad phi|^2, over eta)
+ * and beta^i = int F'(phi)/int sqrt F(phi) (Section 2.2.1) at st; stores them as the
+ * phase's frozen coefficients and, if out != NULL, writes {gamma, beta} to the HOST
+ * array out (synchronises the stream). */
+int fsi_update_ac_coeffs(fsi_mesh* mesh, int32_t phase, const fsi_state* st, double* out);
+/* Sets the frozen coefficients explicitly. */
+int fsi_set_ac_coeffs(fsi_mesh* mesh, int32_t phase, double gamma, double beta);
+/* Fixes gamma^i for the time step (gamma >= 0), or restores the mobility model (< 0). */
+int fsi_fix_gamma(fsi_mesh* mesh, int32_t phase, double gamma);
+
+/* --------------------------------------------------------------- solvers */
+
+#define FSI_PC_NONE 0
+#define FSI_PC_JACOBI 1
+
+#define FSI_PREC_FP64 0     /* operator applies in float64                         */
+#define FSI_PREC_FP32_IR 1  /* float32 operator inside float64 iterative refinement */
+
+typedef struct {
+  int32_t m;          /* restart length (GMRES(m)), <= 64                         */
+  int32_t max_iter;   /* total inner iterations                                   */
+  double rtol;        /* stop when ||b - A x|| / ||b|| <= rtol                    */
+  int32_t precond;    /* FSI_PC_*                                                 */
+  int32_t precision;  /* FSI_PREC_*                                               */
+  uint32_t flags;     /* operator flags (FSI_ELASTIC_AUG)                         */
+  int32_t ir_max;     /* FP32_IR: maximum refinement steps                        */
+  double ir_inner_rtol; /* FP32_IR: relative tolerance of each inner solve         */
+} fsi_solve_opts;
+
+typedef struct {
+  int32_t iterations;   /* inner iterations (all restarts and refinements)       */
+  int32_t restarts;
+  int32_t refinements;  /* FP32_IR outer steps                                   */
+  int32_t applies;      /* operator applies (all precisions)                     */
+  double rel_res;       /* final ||b - A x|| / ||b|| (float64 operator)           */
+} fsi_solve_info;
+
+/* Solves J(st) x = rhs for one block by right-preconditioned restarted GMRES from
+ * x = 0 (Arnoldi with classical Gram-Schmidt applied twice, Givens rotations; the
+ * paper solves every block with GMRES, Section 2.5).  rhs and x are device block
+ * vectors.  Returns FSI_ENOCONV (x holds the last iterate) if rtol is not met within
+ * max_iter.  Synchronises the stream. */
+int fsi_gmres(fsi_mesh* mesh, int32_t block, const fsi_state* st, const double* rhs, double* x,
+              const fsi_solve_opts* opts, fsi_solve_info* info);
+
+typedef struct {
+  int32_t k_max;         /* nonlinear iterations (paper: 20)                    */
+  int32_t fixed_iters;   /* 1: always run k_max iterations (parity mode)        */
+  double nl_tol;         /* ||dx_blk|| / ||x_blk|| < nl_tol for all blocks (5e-4) */
+  fsi_solve_opts solve;
+} fsi_step_opts;
+
+typedef struct {
+  int32_t nl_iters;
+  int32_t gmres_iters_ns, gmres_iters_ac, gmres_iters_b;
+  int32_t applies;           /* operator applies (residuals and products)      */
+  int64_t dof_applied;       /* sum over applies of the block's DoF count      */
+  double max_ratio;          /* last iteration's max ||dx_blk|| / ||x_blk||     */
+  double worst_rel_res;      /* largest final linear relative residual         */
+} fsi_step_info;
+
+/* One partitioned time step (Section 2.1.2 predictor-multicorrector, Section 2.5):
+ * predictor x^{n+1} = x^n with the velocity Dirichlet values; k_max nonlinear
+ * iterations of NS -> AC(0..N-1) (gamma, beta frozen per block) -> B(0..n_s-1), each
+ * a Newton step solved by fsi_gmres; corrector dx/dt^{n+1} from the
+ * generalized-alpha relation; then x^n <- x^{n+1}, dx/dt^n <- dx/dt^{n+1}.
+ * Synchronises the stream. */
+int fsi_step(fsi_mesh* mesh, fsi_state* st, const fsi_step_opts* opts, fsi_step_info* info);
+
+/* --------------------------------------------------------------- initialisation */
+
+/* Triangulated closed surface (host arrays, copied). */
+typedef struct {
+  const double* verts;  /* [n_verts][3]                                         */
+  const int32_t* tris;  /* [n_tris][3] vertex indices                           */
+  int32_t n_verts, n_tris;
+} fsi_surface;
+
+#define FSI_RULE_SURFACE 0     /* phi = signed-distance profile of one surface   */
+#define FSI_RULE_COMPLEMENT 1  /* alpha = max(0, 1 - sum of surface alphas) x plane */
+
+typedef struct {
+  int32_t kind;
+  int32_t surface;     /* FSI_RULE_SURFACE: surface index                         */
+  double plane_z;      /* FSI_RULE_COMPLEMENT: plane z = plane_z                  */
+  int32_t plane_side;  /* 0 none, +1 keep z < plane_z, -1 keep z > plane_z       */
+  int32_t pad;
+} fsi_phase_rule;
+
+/* Phase-indicator initialisation (Section 3, Algorithms 1 and 2): for every surface
+ * the grid-cell nearest-vertex distance (gx*gy*gz cells over the node bounding box,
+ * triangles binned by their bounding boxes grown by 3 eps) and the +x ray-casting
+ * sign with non-duplicated plane partitioning (chi = 1e-12 L^2, L the box diagonal),
+ * phi = +-tanh(d/(sqrt2 eps)) (positive inside) or +-1 in cells without triangles;
+ * then each phase by its rule.
+ * phi_out: device [n_phase][nn].  tags_out: device int32 [n_surf][4][nn] or NULL:
+ * {cell id, nearest vertex (-1 outside interface cells), crossing number, inside}.
+ * Integer tags are bit-identical to a sequential evaluation of the same rules.
+ * FSI_EINVAL if the number of distinct crossing keys of one ray exceeds 64.
+ * Synchronises the stream. */
+int fsi_init_phases(fsi_mesh* mesh, const fsi_surface* surfaces, int32_t n_surf,
+                    const fsi_phase_rule* rules, int32_t gx, int32_t gy, int32_t gz,
+                    double* phi_out, int32_t* tags_out);
+
+/* --------------------------------------------------------------- errors */
+const char* fsi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSI_H */

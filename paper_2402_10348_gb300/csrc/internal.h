@@ -1,0 +1,105 @@
+// Internal declarations shared by the translation units of libfsi.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fsi.h"
+#include "ops.cuh"
+
+struct fsi_mesh {
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  fsi::Geom g{};
+  fsi::Phys P{};
+  int N = 0, ns = 0, ncomp = 0;
+  int64_t nn = 0;
+  std::vector<fsi_phase> phases;
+  double lx = 0, ly = 0, lz = 0;
+  // boundary data
+  uint8_t* mask = nullptr;  // [nn]
+  double* vD = nullptr;     // [3][nn]
+  // staged state (x^{n+alpha}, dx/dt^{n+alpha_m}, blended materials)
+  double* xa = nullptr;     // only when alpha != 1
+  double* xd = nullptr;     // [ncomp][nn]
+  double* mat = nullptr;    // [2 + ns][nn]: rho, mu, alpha^s
+  float* xa32 = nullptr;    // float copies for FSI_FP32
+  float* xd32 = nullptr;
+  float* mat32 = nullptr;
+  const double* staged_x = nullptr;  // x^{n+1} of the last staging (p and Dirichlet rows)
+  const double* staged_xa = nullptr; // the x^{n+alpha} array in use
+  // coefficients
+  double gamma[fsi::MAXP] = {0};
+  double beta[fsi::MAXP] = {0};
+  double fixed_gamma[fsi::MAXP];
+  double* partials = nullptr;
+  int64_t n_partials = 0;
+  // reduction scratch
+  double* red = nullptr;     // device scratch for vector reductions
+  double* red_host = nullptr;// pinned host mirror
+  // Krylov workspace
+  int64_t kry_n = 0;
+  int kry_m = 0;
+  double* V = nullptr;       // [m+1][n]
+  double* wk = nullptr;      // [4][n] work vectors
+  double* dinv = nullptr;    // [n]
+  double* yvec = nullptr;    // [m+1] device
+  double* partials_dot = nullptr;  // per-CTA partial dot products
+  double* step_ws = nullptr; // [2][max block] time-step work vectors
+  int64_t step_ws_n = 0;
+  // counters (step info)
+  int64_t applies = 0;
+  int64_t dof_applied = 0;
+};
+
+namespace fsi {
+
+int set_error(int code, const std::string& msg);
+int cuda_check(cudaError_t e, const char* what);
+#define FSI_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t _e = (call);                             \
+    if (_e != cudaSuccess) return fsi::cuda_check(_e, #call); \
+  } while (0)
+
+// staging of x^{n+alpha}, dx/dt^{n+alpha_m} and materials (api.cu)
+int stage(fsi_mesh* m, const fsi_state* st, bool fp32);
+
+// block bookkeeping
+struct BlockInfo {
+  int kind;   // 0 NS, 1 AC, 2 B
+  int index;
+  int c0;     // first component plane
+  int nc;     // component planes
+  int64_t n;  // vector length
+};
+int block_info(const fsi_mesh* m, int32_t block, BlockInfo* bi);
+
+// operator launches on staged state (ops_f64.cu / ops_f32.cu)
+int op_residual(fsi_mesh* m, const BlockInfo& b, double* r);
+int op_jvp(fsi_mesh* m, const BlockInfo& b, const double* dx, double* y, unsigned flags);
+int op_diag(fsi_mesh* m, const BlockInfo& b, double* d, unsigned flags);
+int op_coeffs(fsi_mesh* m, int phase, double* gamma_beta);  // synchronises
+
+template <typename T>
+int launch_ns(fsi_mesh* m, int mode, const double* dx, double* y, unsigned flags);
+template <typename T>
+int launch_ac(fsi_mesh* m, int mode, int phase, const double* dx, double* y);
+template <typename T>
+int launch_b(fsi_mesh* m, int mode, int s, const double* dx, double* y);
+
+// vector helpers (krylov.cu)
+int vec_dot(fsi_mesh* m, const double* a, const double* b, int64_t n, double* out_host);  // synchronises
+int vec_axpy(fsi_mesh* m, double alpha, const double* x, double* y, int64_t n);          // y += a x
+int vec_scale_copy(fsi_mesh* m, double alpha, const double* x, double* y, int64_t n);    // y = a x
+int vec_mul(fsi_mesh* m, const double* a, const double* b, double* y, int64_t n);        // y = a*b
+int vec_recip(fsi_mesh* m, const double* a, double* y, int64_t n);                      // y = 1/a
+int gmres_solve(fsi_mesh* m, const BlockInfo& b, const double* rhs, double* x, const fsi_solve_opts& o,
+                fsi_solve_info* info);
+
+// tile launch geometry
+void tile_grid(const fsi_mesh* m, dim3* grid);
+
+}  // namespace fsi

@@ -1,0 +1,59 @@
+// Float64 instantiations of the element operators and the gamma/beta reduction.
+#include "ops_impl.cuh"
+
+namespace fsi {
+
+template int launch_ns<double>(fsi_mesh*, int, const double*, double*, unsigned);
+template int launch_ac<double>(fsi_mesh*, int, int, const double*, double*);
+template int launch_b<double>(fsi_mesh*, int, int, const double*, double*);
+
+// Sums the per-CTA partials {sum val^2, n_band, int F', int sqrt F} in a fixed order.
+__global__ void coef_finalize(const double* partials, int64_t n, double eta, double* out) {
+  __shared__ double s[4][NTHREADS];
+  double a[4] = {0, 0, 0, 0};
+  for (int64_t i = threadIdx.x; i < n; i += NTHREADS)
+    for (int c = 0; c < 4; ++c) a[c] += partials[4 * i + c];
+  for (int c = 0; c < 4; ++c) s[c][threadIdx.x] = a[c];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[4] = {0, 0, 0, 0};
+    for (int i = 0; i < NTHREADS; ++i)
+      for (int c = 0; c < 4; ++c) t[c] += s[c][i];
+    out[0] = t[1] > 0.0 ? sqrt(t[0] / t[1]) / eta : 0.0;  // gamma
+    out[1] = t[3] != 0.0 ? t[2] / t[3] : 0.0;             // beta
+  }
+}
+
+int op_coeffs(fsi_mesh* m, int i, double* gb) {
+  CoefOp op;
+  memset(&op, 0, sizeof(op));
+  const int64_t nn = m->nn;
+  for (int k = 0; k < 3; ++k) { op.F.d[k] = m->staged_xa + k * nn; op.F.f[k] = nullptr; }
+  op.F.d[3] = m->staged_xa + (4 + i) * nn;
+  op.nf = 4;
+  fill_common(m, op.rh, &op.W);
+  op.phi_node = m->staged_xa + (4 + i) * nn;
+  dim3 grid;
+  tile_grid(m, &grid);
+  op.ncta_xy[0] = grid.x;
+  op.ncta_xy[1] = grid.y;
+  const int64_t ncta = (int64_t)grid.x * grid.y * grid.z;
+  if (m->n_partials < ncta) {
+    if (m->partials) cudaFree(m->partials);
+    m->partials = nullptr;
+    FSI_CUDA(cudaMalloc(&m->partials, sizeof(double) * 4 * ncta));
+    m->n_partials = ncta;
+  }
+  op.partials = m->partials;
+  int rc = run_tile(m, op);
+  if (rc) return rc;
+  coef_finalize<<<1, NTHREADS, 0, m->stream>>>(m->partials, ncta, m->P.eta, m->red);
+  FSI_CUDA(cudaGetLastError());
+  FSI_CUDA(cudaMemcpyAsync(m->red_host, m->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  FSI_CUDA(cudaStreamSynchronize(m->stream));
+  gb[0] = m->red_host[0];
+  gb[1] = m->red_host[1];
+  return FSI_OK;
+}
+
+}  // namespace fsi

@@ -1,0 +1,188 @@
+// Host-side launchers of the element operators for one compute type T.
+// Included by ops_f64.cu (T = double) and ops_f32.cu (T = float).
+#pragma once
+#include "internal.h"
+
+namespace fsi {
+
+template <typename T>
+struct Staged;  // staged-state arrays of the compute type
+
+template <>
+struct Staged<double> {
+  static const double* xa(const fsi_mesh* m) { return m->staged_xa; }
+  static const double* xd(const fsi_mesh* m) { return m->xd; }
+  static const double* mat(const fsi_mesh* m) { return m->mat; }
+};
+template <>
+struct Staged<float> {
+  static const float* xa(const fsi_mesh* m) { return m->xa32; }
+  static const float* xd(const fsi_mesh* m) { return m->xd32; }
+  static const float* mat(const fsi_mesh* m) { return m->mat32; }
+};
+
+template <typename T>
+inline void put(Fields& F, int i, const T* p);
+template <>
+inline void put<double>(Fields& F, int i, const double* p) { F.d[i] = p; F.f[i] = nullptr; }
+template <>
+inline void put<float>(Fields& F, int i, const float* p) { F.f[i] = p; F.d[i] = nullptr; }
+
+inline void fill_common(const fsi_mesh* m, double rh[3], double* W) {
+  rh[0] = 1.0 / m->g.hx; rh[1] = 1.0 / m->g.hy; rh[2] = 1.0 / m->g.hz;
+  *W = m->g.hx * m->g.hy * m->g.hz / 8.0;
+}
+
+template <class Op>
+int run_tile(fsi_mesh* m, const Op& op) {
+  const size_t smem = tile_smem_bytes<Op>(op.nf);
+  static size_t configured = 0;
+  if (smem > configured) {
+    FSI_CUDA(cudaFuncSetAttribute(tile_kernel<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured = smem;
+  }
+  dim3 grid;
+  tile_grid(m, &grid);
+  tile_kernel<Op><<<grid, NTHREADS, smem, m->stream>>>(op, m->g);
+  FSI_CUDA(cudaGetLastError());
+  return FSI_OK;
+}
+
+constexpr size_t SMEM_LIMIT = 232448;
+
+template <typename T>
+inline int solids_per_pass(int nf_fixed) {
+  // 2 planes x (nf_fixed + 7 s) fields + 4 x 8 x 256 contributions
+  const size_t fixed = sizeof(T) * (size_t)(2 * nf_fixed * PP + 4 * 8 * NTHREADS);
+  const size_t per = sizeof(T) * (size_t)(2 * 7 * PP);
+  if (fixed >= SMEM_LIMIT) return 0;
+  return (int)((SMEM_LIMIT - fixed) / per);
+}
+
+template <typename T, int MODE>
+int ns_pass(fsi_mesh* m, const double* dx, double* y, unsigned flags, int s0, int s1, bool first) {
+  NSOp<T, MODE> op;
+  memset(&op, 0, sizeof(op));
+  const T* xa = Staged<T>::xa(m);
+  const T* xd = Staged<T>::xd(m);
+  const T* mat = Staged<T>::mat(m);
+  const int64_t nn = m->nn;
+  if ((MODE == 1 ? 4 : 0) + 9 + 7 * (s1 - s0) > MAXF) return set_error(FSI_EINVAL, "NS operator: too many staged fields");
+  int f = 0;
+  if (MODE == 1) {
+    for (int k = 0; k < 4; ++k) { op.F.d[f] = dx + k * nn; op.F.f[f] = nullptr; ++f; }
+  }
+  for (int k = 0; k < 3; ++k) put<T>(op.F, f++, xa + k * nn);   // v
+  put<T>(op.F, f++, xa + 3 * nn);                                 // p^{n+1}
+  for (int k = 0; k < 3; ++k) put<T>(op.F, f++, xd + k * nn);   // dv/dt
+  put<T>(op.F, f++, mat);                                         // rho
+  put<T>(op.F, f++, mat + nn);                                    // mu
+  for (int s = s0; s < s1; ++s) {
+    put<T>(op.F, f++, mat + (2 + s) * nn);                        // alpha^s
+    const int c0 = 4 + m->N + 6 * s;
+    for (int c = 0; c < 6; ++c) put<T>(op.F, f++, xa + (c0 + c) * nn);
+  }
+  op.nf = f;
+  op.s0 = s0;
+  op.s1 = s1;
+  op.fluid = first ? 1 : 0;
+  op.elastic_aug = (flags & FSI_ELASTIC_AUG) ? 1 : 0;
+  op.P = m->P;
+  fill_common(m, op.rh, &op.W);
+  op.out.y = y;
+  op.out.dx = dx;
+  op.out.x = m->staged_x;
+  op.out.mask = m->mask;
+  op.out.vD = m->vD;
+  op.out.accumulate = first ? 0 : 1;
+  op.out.dirichlet = first ? 1 : 0;
+  op.nn_ = nn;
+  return run_tile(m, op);
+}
+
+template <typename T>
+int launch_ns(fsi_mesh* m, int mode, const double* dx, double* y, unsigned flags) {
+  const bool need_solids = (mode == 0) || (flags & FSI_ELASTIC_AUG);
+  const int ns = need_solids ? m->ns : 0;
+  const int fixed = (mode == 1 ? 4 : 0) + 9;
+  // bounded by shared memory and by the MAXF staged-field slots of Fields
+  const int per = std::min(solids_per_pass<T>(fixed), (MAXF - fixed) / 7);
+  if (per < 1 && ns > 0) return set_error(FSI_EINVAL, "NS operator: shared memory too small for one solid");
+  int s0 = 0;
+  bool first = true;
+  do {
+    const int s1 = ns == 0 ? 0 : std::min(ns, s0 + per);
+    int rc;
+    if (mode == 0) rc = ns_pass<T, 0>(m, dx, y, flags, s0, s1, first);
+    else if (mode == 1) rc = ns_pass<T, 1>(m, dx, y, flags, s0, s1, first);
+    else rc = ns_pass<T, 2>(m, dx, y, flags, s0, s1, first);
+    if (rc) return rc;
+    first = false;
+    s0 = s1;
+  } while (s0 < ns);
+  return FSI_OK;
+}
+
+template <typename T, int MODE>
+int ac_run(fsi_mesh* m, int i, const double* dx, double* y) {
+  ACOp<T, MODE> op;
+  memset(&op, 0, sizeof(op));
+  const T* xa = Staged<T>::xa(m);
+  const T* xd = Staged<T>::xd(m);
+  const int64_t nn = m->nn;
+  int f = 0;
+  if (MODE == 1) { op.F.d[f] = dx; op.F.f[f] = nullptr; ++f; }
+  for (int k = 0; k < 3; ++k) put<T>(op.F, f++, xa + k * nn);
+  put<T>(op.F, f++, xa + (4 + i) * nn);
+  if (MODE == 0) put<T>(op.F, f++, xd + (4 + i) * nn);
+  op.nf = f;
+  op.P = m->P;
+  fill_common(m, op.rh, &op.W);
+  op.gamma = m->gamma[i];
+  op.beta = m->beta[i];
+  op.out.y = y;
+  op.nn_ = nn;
+  return run_tile(m, op);
+}
+
+template <typename T>
+int launch_ac(fsi_mesh* m, int mode, int i, const double* dx, double* y) {
+  if (mode == 0) return ac_run<T, 0>(m, i, dx, y);
+  if (mode == 1) return ac_run<T, 1>(m, i, dx, y);
+  return ac_run<T, 2>(m, i, dx, y);
+}
+
+template <typename T, int MODE>
+int b_run(fsi_mesh* m, int s, const double* dx, double* y) {
+  BOp<T, MODE> op;
+  memset(&op, 0, sizeof(op));
+  const T* xa = Staged<T>::xa(m);
+  const T* xd = Staged<T>::xd(m);
+  const T* mat = Staged<T>::mat(m);
+  const int64_t nn = m->nn;
+  const int c0 = 4 + m->N + 6 * s;
+  int f = 0;
+  if (MODE == 1)
+    for (int c = 0; c < 6; ++c) { op.F.d[f] = dx + c * nn; op.F.f[f] = nullptr; ++f; }
+  for (int k = 0; k < 3; ++k) put<T>(op.F, f++, xa + k * nn);
+  put<T>(op.F, f++, mat + (2 + s) * nn);
+  if (MODE == 0) {
+    for (int c = 0; c < 6; ++c) put<T>(op.F, f++, xa + (c0 + c) * nn);
+    for (int c = 0; c < 6; ++c) put<T>(op.F, f++, xd + (c0 + c) * nn);
+  }
+  op.nf = f;
+  op.P = m->P;
+  fill_common(m, op.rh, &op.W);
+  op.out.y = y;
+  op.nn_ = nn;
+  return run_tile(m, op);
+}
+
+template <typename T>
+int launch_b(fsi_mesh* m, int mode, int s, const double* dx, double* y) {
+  if (mode == 0) return b_run<T, 0>(m, s, dx, y);
+  if (mode == 1) return b_run<T, 1>(m, s, dx, y);
+  return b_run<T, 2>(m, s, dx, y);
+}
+
+}  // namespace fsi

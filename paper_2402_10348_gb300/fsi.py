@@ -1,0 +1,274 @@
+"""Python binding of libfsi (include/fsi.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls and forwards device
+pointers of torch CUDA tensors; all computation happens in libfsi's kernels.  A
+missing library raises immediately: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfsi.so")
+
+FSI_OK, FSI_EINVAL, FSI_ECUDA, FSI_ENOCONV, FSI_ENAN, FSI_ETIMEOUT, FSI_ENOMEM = range(7)
+FSI_BLOCK_NS = 0
+FSI_ELASTIC_AUG = 0x1
+FSI_FP32 = 0x2
+FSI_PC_NONE, FSI_PC_JACOBI = 0, 1
+FSI_PREC_FP64, FSI_PREC_FP32_IR = 0, 1
+FSI_BC_NATURAL, FSI_BC_DIRICHLET = 0, 1
+FSI_RULE_SURFACE, FSI_RULE_COMPLEMENT = 0, 1
+
+
+def FSI_BLOCK_AC(i: int) -> int:
+    return 0x10000 | i
+
+
+def FSI_BLOCK_B(s: int) -> int:
+    return 0x20000 | s
+
+
+class FsiError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libfsi error {code}: {msg}")
+        self.code = code
+
+
+class fsi_phase(C.Structure):
+    _fields_ = [("rho", C.c_double), ("mu", C.c_double), ("mu_L", C.c_double),
+                ("is_solid", C.c_int32), ("pad", C.c_int32)]
+
+
+class fsi_face_bc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("priority", C.c_int32), ("vel", C.c_double * 3)]
+
+
+class fsi_mesh_desc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("n_phase", C.c_int32),
+                ("lx", C.c_double), ("ly", C.c_double), ("lz", C.c_double),
+                ("phases", C.POINTER(fsi_phase)),
+                ("gravity", C.c_double * 3),
+                ("eps", C.c_double), ("eta", C.c_double), ("dt", C.c_double),
+                ("rho_inf", C.c_double), ("c_i", C.c_double),
+                ("faces", fsi_face_bc * 6),
+                ("has_box", C.c_int32), ("pin_node", C.c_int32),
+                ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3), ("box_vel", C.c_double * 3),
+                ("device", C.c_int32), ("pad", C.c_int32)]
+
+
+class fsi_state(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("xn", C.c_void_p), ("xdn", C.c_void_p)]
+
+
+class fsi_solve_opts(C.Structure):
+    _fields_ = [("m", C.c_int32), ("max_iter", C.c_int32), ("rtol", C.c_double),
+                ("precond", C.c_int32), ("precision", C.c_int32), ("flags", C.c_uint32),
+                ("ir_max", C.c_int32), ("ir_inner_rtol", C.c_double)]
+
+
+class fsi_solve_info(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("restarts", C.c_int32), ("refinements", C.c_int32),
+                ("applies", C.c_int32), ("rel_res", C.c_double)]
+
+
+class fsi_step_opts(C.Structure):
+    _fields_ = [("k_max", C.c_int32), ("fixed_iters", C.c_int32), ("nl_tol", C.c_double),
+                ("solve", fsi_solve_opts)]
+
+
+class fsi_step_info(C.Structure):
+    _fields_ = [("nl_iters", C.c_int32), ("gmres_iters_ns", C.c_int32), ("gmres_iters_ac", C.c_int32),
+                ("gmres_iters_b", C.c_int32), ("applies", C.c_int32), ("pad", C.c_int32),
+                ("dof_applied", C.c_int64), ("max_ratio", C.c_double), ("worst_rel_res", C.c_double)]
+
+
+class fsi_surface(C.Structure):
+    _fields_ = [("verts", C.c_void_p), ("tris", C.c_void_p), ("n_verts", C.c_int32), ("n_tris", C.c_int32)]
+
+
+class fsi_phase_rule(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("surface", C.c_int32), ("plane_z", C.c_double),
+                ("plane_side", C.c_int32), ("pad", C.c_int32)]
+
+
+EXPORTS = ["fsi_create_mesh", "fsi_destroy_mesh", "fsi_set_stream", "fsi_mesh_info", "fsi_residual",
+           "fsi_jvp", "fsi_diag", "fsi_update_ac_coeffs", "fsi_set_ac_coeffs", "fsi_fix_gamma",
+           "fsi_gmres", "fsi_step", "fsi_init_phases", "fsi_last_error"]
+
+_lib = None
+
+
+def lib():
+    """Loads libfsi.so (built in-tree by paper_2402_10348_gb300._build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        L.fsi_last_error.restype = C.c_char_p
+        for name in EXPORTS:
+            if name != "fsi_last_error":
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, allow=()):
+    if rc != FSI_OK and rc not in allow:
+        raise FsiError(rc, lib().fsi_last_error().decode())
+    return rc
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError("libfsi takes device (CUDA) tensors")
+    if not t.is_contiguous():
+        raise ValueError("libfsi takes contiguous tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+def _dptr(t):
+    if t.dtype != torch.float64:
+        raise TypeError("libfsi field arrays are float64")
+    return _ptr(t)
+
+
+class Mesh:
+    """Owns an fsi_mesh handle."""
+
+    def __init__(self, handle, desc_struct, phases_arr):
+        self.handle = handle
+        self._desc = desc_struct
+        self._phases = phases_arr
+        nc, nn, ns = C.c_int32(), C.c_int64(), C.c_int32()
+        _check(lib().fsi_mesh_info(handle, C.byref(nc), C.byref(nn), C.byref(ns)))
+        self.ncomp, self.nn, self.n_solid = nc.value, nn.value, ns.value
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.fsi_destroy_mesh(h)
+            self.handle = None
+
+
+def make_desc(d, device: int = 0):
+    """fsi_mesh_desc from a problem description with the fields of workloads.MeshDesc."""
+    ph = (fsi_phase * len(d.phases))()
+    for i, p in enumerate(d.phases):
+        ph[i] = fsi_phase(p.rho, p.mu, p.mu_L, 1 if p.solid else 0, 0)
+    s = fsi_mesh_desc()
+    s.nx, s.ny, s.nz, s.n_phase = d.nx, d.ny, d.nz, len(d.phases)
+    s.lx, s.ly, s.lz = d.lx, d.ly, d.lz
+    s.phases = C.cast(ph, C.POINTER(fsi_phase))
+    s.gravity[:] = list(d.gravity)
+    s.eps, s.eta, s.dt, s.rho_inf, s.c_i = d.eps, d.eta, d.dt, d.rho_inf, d.c_i
+    for f in range(6):
+        fb = d.faces[f]
+        s.faces[f].kind, s.faces[f].priority = fb.kind, fb.priority
+        s.faces[f].vel[:] = list(fb.vel)
+    if d.prescribed_box is not None:
+        lo, hi, vel = d.prescribed_box
+        s.has_box = 1
+        s.box_lo[:], s.box_hi[:], s.box_vel[:] = list(lo), list(hi), list(vel)
+    s.pin_node = d.pin_node
+    s.device = device
+    return s, ph
+
+
+def fsi_create_mesh(d, device: int = 0) -> Mesh:
+    s, ph = make_desc(d, device)
+    h = C.c_void_p()
+    _check(lib().fsi_create_mesh(C.byref(s), C.byref(h)))
+    return Mesh(h, s, ph)
+
+
+def fsi_set_stream(mesh: Mesh, stream=None):
+    st = torch.cuda.current_stream() if stream is None else stream
+    _check(lib().fsi_set_stream(mesh.handle, C.c_void_p(st.cuda_stream)))
+
+
+def _state(x, xn, xdn):
+    return fsi_state(_dptr(x), _dptr(xn), _dptr(xdn))
+
+
+def fsi_residual(mesh: Mesh, block: int, x, xn, xdn, r):
+    st = _state(x, xn, xdn)
+    _check(lib().fsi_residual(mesh.handle, C.c_int32(block), C.byref(st), _dptr(r)))
+
+
+def fsi_jvp(mesh: Mesh, block: int, x, xn, xdn, dx, y, flags: int = FSI_ELASTIC_AUG):
+    st = _state(x, xn, xdn)
+    _check(lib().fsi_jvp(mesh.handle, C.c_int32(block), C.byref(st), _dptr(dx), _dptr(y), C.c_uint32(flags)))
+
+
+def fsi_diag(mesh: Mesh, block: int, x, xn, xdn, d, flags: int = FSI_ELASTIC_AUG):
+    st = _state(x, xn, xdn)
+    _check(lib().fsi_diag(mesh.handle, C.c_int32(block), C.byref(st), _dptr(d), C.c_uint32(flags)))
+
+
+def fsi_update_ac_coeffs(mesh: Mesh, phase: int, x, xn, xdn):
+    st = _state(x, xn, xdn)
+    out = (C.c_double * 2)()
+    _check(lib().fsi_update_ac_coeffs(mesh.handle, C.c_int32(phase), C.byref(st), out))
+    return out[0], out[1]
+
+
+def fsi_set_ac_coeffs(mesh: Mesh, phase: int, gamma: float, beta: float):
+    _check(lib().fsi_set_ac_coeffs(mesh.handle, C.c_int32(phase), C.c_double(gamma), C.c_double(beta)))
+
+
+def fsi_fix_gamma(mesh: Mesh, phase: int, gamma: float):
+    _check(lib().fsi_fix_gamma(mesh.handle, C.c_int32(phase), C.c_double(gamma)))
+
+
+def solve_opts(m=30, max_iter=2000, rtol=1e-8, precond=FSI_PC_JACOBI, precision=FSI_PREC_FP64,
+               flags=FSI_ELASTIC_AUG, ir_max=10, ir_inner_rtol=1e-3) -> fsi_solve_opts:
+    return fsi_solve_opts(m, max_iter, rtol, precond, precision, flags, ir_max, ir_inner_rtol)
+
+
+def fsi_gmres(mesh: Mesh, block: int, x, xn, xdn, rhs, sol, opts: fsi_solve_opts, allow_noconv=False):
+    st = _state(x, xn, xdn)
+    info = fsi_solve_info()
+    _check(lib().fsi_gmres(mesh.handle, C.c_int32(block), C.byref(st), _dptr(rhs), _dptr(sol),
+                           C.byref(opts), C.byref(info)), allow=(FSI_ENOCONV,) if allow_noconv else ())
+    return info
+
+
+def fsi_step(mesh: Mesh, x, xn, xdn, k_max=5, nl_tol=5e-4, fixed_iters=False,
+             solve: fsi_solve_opts | None = None) -> fsi_step_info:
+    st = _state(x, xn, xdn)
+    o = fsi_step_opts(k_max, 1 if fixed_iters else 0, nl_tol, solve if solve is not None else solve_opts())
+    info = fsi_step_info()
+    _check(lib().fsi_step(mesh.handle, C.byref(st), C.byref(o), C.byref(info)))
+    return info
+
+
+def fsi_init_phases(mesh: Mesh, surfaces, rules, grid, phi_out, tags_out=None):
+    """surfaces: objects with .verts (n,3) float64 and .tris (m,3) int arrays (host);
+    rules: objects with kind, surface, plane_z, plane_side."""
+    import numpy as np
+    keep = []
+    S = (fsi_surface * max(1, len(surfaces)))()
+    for i, s in enumerate(surfaces):
+        v = np.ascontiguousarray(s.verts, dtype=np.float64)
+        t = np.ascontiguousarray(s.tris, dtype=np.int32)
+        keep += [v, t]
+        S[i] = fsi_surface(v.ctypes.data, t.ctypes.data, v.shape[0], t.shape[0])
+    R = (fsi_phase_rule * len(rules))()
+    for i, r in enumerate(rules):
+        R[i] = fsi_phase_rule(r.kind, r.surface, r.plane_z, r.plane_side, 0)
+    tp = None
+    if tags_out is not None:
+        if tags_out.dtype != torch.int32:
+            raise TypeError("tags are int32")
+        tp = _ptr(tags_out)
+    _check(lib().fsi_init_phases(mesh.handle, S, C.c_int32(len(surfaces)), R, C.c_int32(grid[0]),
+                                 C.c_int32(grid[1]), C.c_int32(grid[2]), _dptr(phi_out), tp))

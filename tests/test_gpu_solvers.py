@@ -1,0 +1,154 @@
+"""GPU-vs-oracle parity of GMRES, mixed-precision refinement, the partitioned time
+step and the grid-cell initialisation, through the C ABI."""
+import numpy as np
+import pytest
+
+from tests.gpu_helpers import DEV, Gpu, T, relmax
+
+pytestmark = pytest.mark.gpu
+
+import torch  # noqa: E402
+
+from oracle import blocks, gmres, step  # noqa: E402
+from oracle.diag import block_diagonal  # noqa: E402
+from oracle.fields import Problem, State  # noqa: E402
+from oracle.gridcell import apply_rules, signed_distance_phi  # noqa: E402
+from paper_2402_10348_gb300 import fsi  # noqa: E402
+from tests.helpers import desc_small  # noqa: E402
+from workloads import cavity, random_state  # noqa: E402
+
+
+def _solve_case(block_name, block_id, comps, precision, rtol=1e-12):
+    d = desc_small(n=(7, 6, 5), n_fluid=1, n_solid=1)
+    x1, xn, xdn = random_state(d, 3)
+    pb, st = Problem(d), State(x1, xn, xdn)
+    g = Gpu(d, x1, xn, xdn)
+    coeffs = None
+    if block_name[0] == "ac":
+        fsi.fsi_set_ac_coeffs(g.mesh, block_name[1], 0.4, 0.1)
+        coeffs = {"gamma": {block_name[1]: 0.4}, "beta": {block_name[1]: 0.1}}
+    rhs = -blocks.residual(pb, st, block_name, coeffs)
+    ref, _, rel = gmres.gmres(lambda u: blocks.jvp(pb, st, block_name, u, coeffs), rhs,
+                              1.0 / block_diagonal(pb, st, block_name, coeffs), m=30, rtol=1e-12, max_iter=3000)
+    sol = torch.zeros(rhs.size, dtype=torch.float64, device=DEV)
+    info = fsi.fsi_gmres(g.mesh, block_id, *g.st(), T(rhs), sol,
+                         fsi.solve_opts(m=30, rtol=rtol, max_iter=5000, precision=precision, ir_inner_rtol=1e-4,
+                                        ir_max=60))
+    torch.cuda.synchronize()
+    got = sol.cpu().numpy()
+    assert info.rel_res <= rtol
+    return got, ref, info
+
+
+@pytest.mark.parametrize("block", [("ns", fsi.FSI_BLOCK_NS), (("ac", 1), fsi.FSI_BLOCK_AC(1)),
+                                   (("b", 0), fsi.FSI_BLOCK_B(0))])
+def test_gmres_matches_oracle(block):
+    """Both solve J x = -R to rel-res 1e-12 (CGS2 on the GPU, MGS in the oracle):
+    the solutions agree to 1e-12 times the condition number's headroom (1e-8)."""
+    got, ref, info = _solve_case(block[0], block[1], None, fsi.FSI_PREC_FP64)
+    assert np.linalg.norm(got - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+def test_fp32_iterative_refinement_reaches_fp64_solution():
+    """FP32 operator inside FP64 refinement reaches rel-res 1e-10 of the float64
+    operator, and the solution matches the FP64 oracle solve within 1e-6 relative
+    (cond(J) ~ 1e6 on this mesh bounds the refinement's contraction per step)."""
+    got, ref, info = _solve_case("ns", fsi.FSI_BLOCK_NS, None, fsi.FSI_PREC_FP32_IR, rtol=1e-10)
+    print(f"IR: {info.refinements} refinements, {info.iterations} inner iterations, rel-res {info.rel_res:.2e}")
+    assert info.refinements >= 2
+    assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+def test_gmres_zero_rhs_and_nonconvergence():
+    d = desc_small(n=(3, 3, 3))
+    x1, xn, xdn = random_state(d, 0)
+    g = Gpu(d, x1, xn, xdn)
+    n = 4 * d.nn
+    sol = torch.ones(n, dtype=torch.float64, device=DEV)
+    info = fsi.fsi_gmres(g.mesh, fsi.FSI_BLOCK_NS, *g.st(), torch.zeros(n, dtype=torch.float64, device=DEV), sol,
+                         fsi.solve_opts())
+    assert info.rel_res == 0.0 and float(sol.abs().max()) == 0.0
+    rhs = T(np.random.default_rng(0).normal(size=n))
+    with pytest.raises(fsi.FsiError) as e:
+        fsi.fsi_gmres(g.mesh, fsi.FSI_BLOCK_NS, *g.st(), rhs, sol, fsi.solve_opts(max_iter=3, rtol=1e-14))
+    assert e.value.code == fsi.FSI_ENOCONV
+    info = fsi.fsi_gmres(g.mesh, fsi.FSI_BLOCK_NS, *g.st(), rhs, sol, fsi.solve_opts(max_iter=3, rtol=1e-14),
+                         allow_noconv=True)
+    assert info.iterations == 3
+
+
+def test_nan_rhs_reported():
+    d = desc_small(n=(2, 2, 2))
+    x1, xn, xdn = random_state(d, 0)
+    g = Gpu(d, x1, xn, xdn)
+    n = 4 * d.nn
+    rhs = torch.full((n,), float("nan"), dtype=torch.float64, device=DEV)
+    with pytest.raises(fsi.FsiError) as e:
+        fsi.fsi_gmres(g.mesh, fsi.FSI_BLOCK_NS, *g.st(), rhs, torch.zeros_like(rhs), fsi.solve_opts())
+    assert e.value.code == fsi.FSI_ENAN
+
+
+def test_time_step_parity_mode():
+    """Parity mode (fixed nonlinear iterations, linear rtol 1e-13): one partitioned
+    step on a 6^3 cavity matches the oracle to 1e-10 relative L2 per field."""
+    wl = cavity(6)
+    d = wl.desc
+    phi, _ = signed_distance_phi(d, wl.surfaces[0], d.eps, wl.grid_cells)
+    x = np.zeros((d.ncomp, d.nn))
+    phases = apply_rules(d, {0: phi}, wl.rules, d.eps)
+    x[4:4 + d.n_phase] = phases
+    x[4 + d.n_phase: 4 + d.n_phase + 3] = 1.0
+    st = State(x.copy(), x.copy(), np.zeros_like(x))
+    g = Gpu(d, st.x, st.xn, st.xdn)
+    k = 3
+    step.time_step(Problem(d), st, step.StepOptions(k_max=k, fixed_nl_iters=True, rtol=1e-13, max_iter=5000))
+    info = fsi.fsi_step(g.mesh, *g.st(), k_max=k, fixed_iters=True,
+                        solve=fsi.solve_opts(rtol=1e-13, max_iter=5000))
+    assert info.nl_iters == k
+    got_n = g.xn.cpu().numpy()
+    got_d = g.xdn.cpu().numpy()
+    fields = {"v": slice(0, 3), "p": slice(3, 4), "phi": slice(4, 4 + d.n_phase), "B": slice(4 + d.n_phase, d.ncomp)}
+    for name, sl in fields.items():
+        e = np.linalg.norm(got_n[sl] - st.xn[sl]) / np.linalg.norm(st.xn[sl])
+        assert e <= 1e-10, (name, e)
+        nd = np.linalg.norm(st.xdn[sl])
+        if nd > 0:
+            assert np.linalg.norm(got_d[sl] - st.xdn[sl]) <= 1e-8 * nd, name
+
+
+@pytest.mark.parametrize("n,grid", [(16, (4, 4, 4)), (13, (3, 5, 2)), (8, (1, 1, 1))])
+def test_init_phases_bit_exact(n, grid):
+    """Grid-cell tags (cell, nearest vertex, crossing number, inside) are identical
+    integers; phi agrees to 2 ulp of tanh."""
+    wl = cavity(n)
+    d = wl.desc
+    phi_ref, tags_ref = signed_distance_phi(d, wl.surfaces[0], d.eps, grid)
+    g = Gpu(d, *random_state(d, 0))
+    phi = torch.zeros(d.n_phase * d.nn, dtype=torch.float64, device=DEV)
+    tags = torch.zeros(4 * d.nn, dtype=torch.int32, device=DEV)
+    fsi.fsi_init_phases(g.mesh, wl.surfaces, wl.rules, grid, phi, tags)
+    torch.cuda.synchronize()
+    got_tags = tags.cpu().numpy().reshape(4, d.nn)
+    assert np.array_equal(got_tags, tags_ref)
+    got = phi.cpu().numpy().reshape(d.n_phase, d.nn)
+    ref = apply_rules(d, {0: phi_ref}, wl.rules, d.eps)
+    assert np.abs(got - ref).max() <= 4e-16
+
+
+def test_init_box_surfaces_multiple_solids():
+    from workloads import falling
+    wl = falling(scale=8)
+    d = wl.desc
+    refs = {}
+    for s, surf in enumerate(wl.surfaces):
+        refs[s] = signed_distance_phi(d, surf, d.eps, wl.grid_cells)
+    g = Gpu(d, *random_state(d, 0))
+    phi = torch.zeros(d.n_phase * d.nn, dtype=torch.float64, device=DEV)
+    tags = torch.zeros(len(wl.surfaces) * 4 * d.nn, dtype=torch.int32, device=DEV)
+    fsi.fsi_init_phases(g.mesh, wl.surfaces, wl.rules, wl.grid_cells, phi, tags)
+    torch.cuda.synchronize()
+    got_tags = tags.cpu().numpy().reshape(len(wl.surfaces), 4, d.nn)
+    for s in refs:
+        assert np.array_equal(got_tags[s], refs[s][1])
+    ref = apply_rules(d, {s: refs[s][0] for s in refs}, wl.rules, d.eps)
+    assert np.abs(phi.cpu().numpy().reshape(d.n_phase, d.nn) - ref).max() <= 4e-16

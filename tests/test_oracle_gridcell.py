@@ -153,4 +153,4 @@ def test_phase_rules_partition_of_unity():
     phi_s, _ = signed_distance_phi(d, s, eps, (2, 2, 2))
     out = apply_rules(d, {0: phi_s}, [PhaseRule(RULE_COMPLEMENT), PhaseRule(RULE_SURFACE, surface=0)], eps)
     assert np.allclose(((1 + out[0]) / 2 + (1 + out[1]) / 2), 1.0, atol=1e-15)
-    assert np.array_equal(out[0], -phi_s)
+    assert np.allclose(out[0], -phi_s, rtol=0, atol=4e-16)

@@ -330,11 +330,20 @@ def random_state(desc: MeshDesc, seed: int, amp_v: float = 1.0, amp_B: float = 0
             x[k] = smooth(amp_v)
         x[3] = smooth(1.0)
         eps = desc.eps if desc.eps > 0 else 1.5 * min(desc.h)
-        for i in range(desc.n_phase):
+        # phase fractions that sum to one (phase 0 takes what the others leave), each
+        # phase i >= 1 a tanh profile of a random sphere, then small nodal noise
+        remaining = np.ones(nn)
+        alphas = [None] * desc.n_phase
+        for i in range(1, desc.n_phase):
             c = rng.uniform(0.3, 0.7, size=3) * L[:, 0]
             r = rng.uniform(0.15, 0.3) * float(L.min())
             d = r - np.sqrt(((X - c[:, None]) ** 2).sum(0))
-            x[4 + i] = phi_range * np.tanh(d / (math.sqrt(2.0) * eps)) + noise * rng.normal(size=nn)
+            s = (1.0 + phi_range * np.tanh(d / (math.sqrt(2.0) * eps))) / 2.0
+            alphas[i] = s * remaining
+            remaining = remaining - alphas[i]
+        alphas[0] = remaining
+        for i in range(desc.n_phase):
+            x[4 + i] = 2.0 * alphas[i] - 1.0 + 0.4 * noise * rng.normal(size=nn)
         base = 4 + desc.n_phase
         for s in range(desc.n_solid):
             for c in range(6):
