@@ -1,0 +1,381 @@
+"""Benchmark: partitioned time steps of the 64^3 lid-driven cavity (274,625 nodes,
+12 unknowns per node) through libfsi, on one GB300 per rank.
+
+A step is one full time step of the method (Section 2.5): predictor, nonlinear
+iterations of the NS, Allen-Cahn and B blocks (each a Newton step solved by
+Jacobi-preconditioned GMRES(30) to rel-res 1e-8), corrector.  The metric is the
+operator-apply throughput sustained inside those solves: the DoFs of every block
+residual and Jacobian-vector product the step evaluates, per second (GDoF/s);
+seconds per time step are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32ir|fp64]
+  python bench.py --impl reference ...   # the FP64 numpy oracle on the host cores
+
+Under torchrun each rank advances its own replica of the cavity (weak scaling, no
+data exchange); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "GDoF/s operator apply; s/timestep to rel-res 1e-8: learned-PC vs plain GMRES"
+UNIT = "GDoF/s"
+WORKLOAD = "cavity64: 3D lid-driven cavity, 64^3 Q1 hexes (274,625 nodes), elastic sphere R=0.2, N=2 phases, 1 solid"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="fsi", choices=["fsi", "reference"])
+    p.add_argument("--precision", default="fp32ir", choices=["fp32ir", "fp64"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Max over ranks (identity at world size 1)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value: float, world: int, device=None) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        out.update(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=reasons, samples=len(rows))
+        return out
+
+
+# ---------------------------------------------------------------- roofline data
+# Algorithmic float operations per element of one element evaluation (no halo
+# recomputation), counted from the arithmetic of the kernels' element functions
+# (see the count table in the design doc); multiply by the elements of one launch.
+def flops_per_element(kernel: str, n_solid: int) -> float:
+    """Per quadrature point: NS JVP 858 + 407 per solid (elastic linearization),
+    NS residual 635 + 167 per solid, AC JVP 247, B JVP 892; 8 points per element."""
+    per_qp = {"ns_jvp": 858 + 407 * n_solid, "ns_residual": 635 + 167 * n_solid,
+              "ac_jvp": 247, "b_jvp": 892}
+    for k, v in per_qp.items():
+        if kernel.startswith(k):
+            return 8.0 * v
+    return 0.0
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    pk = {}
+    if os.path.exists(path):
+        pk = json.load(open(path))
+    # float32 / float64 FMA peaks from unit counts and the maximum SM clock:
+    # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz; FP64: 152 x 2 DFMA/clk x 2 x 2.07 GHz
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    return {
+        "hbm_gbs": pk.get("hbm_gbs", 6800.0),
+        "hbm_src": "measured" if "hbm_gbs" in pk else "fallback",
+        "fp32_tflops": 152 * 128 * 2 * sm_mhz * 1e6 / 1e12,
+        "fp64_tflops": 152 * 2 * 2 * sm_mhz * 1e6 / 1e12,
+    }
+
+
+# ---------------------------------------------------------------- the GPU arm
+def initial_state(fsi, mesh, wl, torch, dev):
+    d = wl.desc
+    nn, nc = d.nn, d.ncomp
+    phi = torch.zeros(d.n_phase * nn, dtype=torch.float64, device=dev)
+    fsi.fsi_init_phases(mesh, wl.surfaces, wl.rules, wl.grid_cells, phi)
+    x = torch.zeros(nc * nn, dtype=torch.float64, device=dev)
+    x[4 * nn:(4 + d.n_phase) * nn] = phi
+    base = 4 + d.n_phase
+    for s in range(d.n_solid):
+        x[(base + 6 * s) * nn:(base + 6 * s + 3) * nn] = 1.0
+    return x, x.clone(), torch.zeros_like(x)
+
+
+def run_gpu(args):
+    import torch
+    from paper_2402_10348_gb300 import fsi
+    from workloads import cavity64
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    wl = cavity64()
+    d = wl.desc
+    mesh = fsi.fsi_create_mesh(d, device=local)
+    stream = torch.cuda.current_stream()
+    fsi.fsi_set_stream(mesh, stream)
+    prec = fsi.FSI_PREC_FP32_IR if args.precision == "fp32ir" else fsi.FSI_PREC_FP64
+    solve = fsi.solve_opts(m=30, rtol=1e-8, max_iter=4000, precision=prec, ir_inner_rtol=1e-3, ir_max=30)
+
+    x, xn, xdn = initial_state(fsi, mesh, wl, torch, dev)
+
+    def step():
+        return fsi.fsi_step(mesh, x, xn, xdn, k_max=wl.k_max, nl_tol=5e-4, solve=solve)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    fsi.fsi_profile(mesh, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    dof, infos = 0, []
+    for _ in range(args.steps):
+        inf = step()
+        dof += inf.dof_applied
+        infos.append(inf)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms_local = e0.elapsed_time(e1)
+    prof = fsi.fsi_profile_read(mesh)
+    fsi.fsi_profile(mesh, False)
+    clk = clocks.stop()
+    ms = reduce_max(ms_local, world, dev)
+    dof_all = reduce_sum(float(dof), world, dev)
+    seconds = ms / 1e3
+    value = dof_all / seconds / 1e9
+    launches = int(sum(v[0] for v in prof.values()))
+
+    # dominant kernel and its roofline
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    dname, (dlaunch, dms) = dom
+    pk = peaks()
+    roof = None
+    if flops_per_element(dname, d.n_solid) > 0 and dlaunch > 0:
+        per_launch_s = dms / dlaunch / 1e3
+        flops = flops_per_element(dname, d.n_solid) * d.ne
+        achieved = flops / per_launch_s / 1e12
+        peak = pk["fp32_tflops"] if dname.endswith("f32") else pk["fp64_tflops"]
+        roof = {"bound": "alu", "kernel": dname, "achieved": round(achieved, 3), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "avg_launch_us": round(per_launch_s * 1e6, 2), "launches": dlaunch,
+                "peak_src": "derived: 152 SMs x lanes x 2 x max SM clock"}
+    elif dlaunch > 0:
+        roof = {"bound": "hbm", "kernel": dname, "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": None, "traffic": None, "avg_launch_us": round(dms / dlaunch * 1e3, 2)}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(fsi, mesh, wl, torch, dev, stream, step_fn=lambda xs: fsi.fsi_step(
+            mesh, *xs, k_max=wl.k_max, nl_tol=5e-4, solve=solve), steps=max(1, min(args.steps, 2)), world=world)
+
+    line = {
+        "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == fsi.FSI_PREC_FP32_IR else "f64",
+        "precision": ("float32 operator applies inside float64 iterative refinement; float64 residuals, "
+                      "Gram-Schmidt, Hessenberg" if prec == fsi.FSI_PREC_FP32_IR else "float64 throughout"),
+        "data": "synthetic (seeded icosphere surface, initial phases by the grid-cell method)",
+        "config": {"workload": WORKLOAD, "nodes": d.nn, "dof_per_node": d.ncomp, "dt": d.dt,
+                   "nl_iters_max": wl.k_max, "gmres": "Jacobi GMRES(30) rtol 1e-8",
+                   "l2": "working set per step > L2 (Krylov basis 31 x 1.1M float64 = 272 MB per NS solve)",
+                   "parallelism": f"replicas x{world}"},
+        "s_per_timestep": round(ms / args.steps / 1e3, 5),
+        "step_stats": {"nl_iters": [i.nl_iters for i in infos],
+                       "gmres_iters_ns": [i.gmres_iters_ns for i in infos],
+                       "gmres_iters_ac": [i.gmres_iters_ac for i in infos],
+                       "gmres_iters_b": [i.gmres_iters_b for i in infos],
+                       "worst_rel_res": max(i.worst_rel_res for i in infos)},
+        "gpu_launches": launches,
+        "kernel_ms": {k: [v[0], round(v[1], 3)] for k, v in prof.items() if v[0] > 0},
+        "roofline": roof,
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_e2e(fsi, mesh, wl, torch, dev, stream, step_fn, steps, world):
+    """Same metric through the C ABI with the state in pinned HOST memory: every step
+    copies x^n, dx^n (and x^{n+1}) to the device, runs the step and copies the new
+    state back (the step's result)."""
+    d = wl.desc
+    n = d.ncomp * d.nn
+    host = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in range(3)]
+    xs = initial_state(fsi, mesh, wl, torch, dev)
+    for h, t in zip(host, xs):
+        h.copy_(t)
+    dev_bufs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(3)]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    dof = 0
+    for _ in range(steps):
+        for db, h in zip(dev_bufs, host):
+            db.copy_(h, non_blocking=True)
+        inf = step_fn(dev_bufs)
+        dof += inf.dof_applied
+        for db, h in zip(dev_bufs, host):
+            h.copy_(db, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = reduce_max(e0.elapsed_time(e1), world, dev)
+    dof = reduce_sum(float(dof), world, dev)
+    return {"value": round(dof / (ms / 1e3) / 1e9, 5), "unit": UNIT, "steps": steps,
+            "h2d_bytes_per_step": 3 * n * 8, "d2h_bytes_per_step": 3 * n * 8}
+
+
+# ---------------------------------------------------------------- the oracle on the host cores
+def _oracle_sample(nz_slab: int, seed: int = 0):
+    """A z-slab of the 64^3 cavity (same spacing, physics and a seeded state)."""
+    from workloads import cavity64, random_state
+    wl = cavity64()
+    d = wl.desc
+    d.nz = nz_slab
+    d.lz = nz_slab * (1.0 / 64.0)
+    x1, xn, xdn = random_state(d, seed)
+    return d, (x1, xn, xdn)
+
+
+def cpu_baseline(budget_s: float = 12.0):
+    """The oracle's NS Jacobian-vector product (the dominant apply of a step) on a
+    64 x 64 x 16-element slab of the workload, repeated for about budget_s."""
+    from oracle import ns
+    from oracle.fields import Problem, State
+    d, (x1, xn, xdn) = _oracle_sample(16)
+    pb, st = Problem(d), State(x1, xn, xdn)
+    dx = np.random.default_rng(1).normal(size=(4, d.nn))
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        ns.ns_jvp(pb, st, dx)
+        reps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(reps * 4 * d.nn / dt / 1e9, 7), "unit": UNIT, "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"{reps} float64 NS Jacobian-vector products on a 64x64x16-element slab of the 64^3 cavity "
+                      f"({4 * d.nn} DoF each, numpy; BLAS may use all {os.cpu_count()} cores), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import ns
+    from oracle.fields import Problem, State
+    d, (x1, xn, xdn) = _oracle_sample(4)
+    pb, st = Problem(d), State(x1, xn, xdn)
+    dx = np.random.default_rng(1).normal(size=(4, d.nn))
+    for _ in range(args.warmup):
+        ns.ns_jvp(pb, st, dx)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ns.ns_jvp(pb, st, dx)
+    dt = time.perf_counter() - t0
+    value = args.steps * 4 * d.nn / dt / 1e9
+    sample = (f"each step: one float64 NS Jacobian-vector product of the oracle on a 64x64x4-element slab "
+              f"of the 64^3 cavity ({4 * d.nn} DoF)")
+    line = {"metric": METRIC, "value": round(value, 7), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample}, "impl": "reference",
+            "cpu_baseline": {"value": round(value, 7), "unit": UNIT, "kind": "oracle", "cores": os.cpu_count(),
+                             "sample": sample},
+            "e2e": {"value": round(value, 7), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

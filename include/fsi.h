@@ -236,6 +236,21 @@ int fsi_init_phases(fsi_mesh* mesh, const fsi_surface* surfaces, int32_t n_surf,
                     const fsi_phase_rule* rules, int32_t gx, int32_t gy, int32_t gz,
                     double* phi_out, int32_t* tags_out);
 
+/* --------------------------------------------------------------- measurement
+ * (no counterpart in the paper: timing support for the benchmark)
+ * fsi_profile(mesh, 1) starts recording a CUDA event pair around every kernel the
+ * mesh launches (counters reset); fsi_profile(mesh, 0) stops.  Launch counts are
+ * kept whether or not events are recorded.  fsi_profile_read synchronises the
+ * stream and returns, per kernel class, the launches and the summed event time. */
+#define FSI_PROF_CLASSES 16
+typedef struct {
+  char name[24];
+  int64_t launches;
+  double ms;            /* summed device time between the event pair (0 if off) */
+} fsi_profile_entry;
+int fsi_profile(fsi_mesh* mesh, int32_t enable);
+int fsi_profile_read(fsi_mesh* mesh, fsi_profile_entry* out /* [FSI_PROF_CLASSES] */, int32_t* n_out);
+
 /* --------------------------------------------------------------- errors */
 const char* fsi_last_error(void);
 

@@ -20,6 +20,45 @@ int cuda_check(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? FSI_ENOMEM : FSI_ECUDA;
 }
 
+static const char* kProfNames[P_NCLS] = {
+    "stage", "ns_residual", "ns_jvp_f64", "ns_jvp_f32", "ns_diag", "ac_residual", "ac_jvp_f64", "ac_jvp_f32",
+    "ac_diag", "b_residual", "b_jvp_f64", "b_jvp_f32", "b_diag", "gamma_beta", "krylov_vector", "init"};
+constexpr int PROF_PAIRS = 4096;
+
+int prof_harvest(fsi_mesh* m) {
+  Profiler& p = m->prof;
+  if (p.used == 0) return FSI_OK;
+  FSI_CUDA(cudaEventSynchronize(p.ev[2 * (p.used - 1) + 1]));
+  for (int i = 0; i < p.used; ++i) {
+    float ms = 0.f;
+    FSI_CUDA(cudaEventElapsedTime(&ms, p.ev[2 * i], p.ev[2 * i + 1]));
+    p.ms[p.cls[i]] += ms;
+  }
+  p.used = 0;
+  return FSI_OK;
+}
+
+int prof_begin(fsi_mesh* m, int cls) {
+  Profiler& p = m->prof;
+  p.launches[cls]++;
+  if (!p.on) return FSI_OK;
+  if (p.used == PROF_PAIRS) {
+    int rc = prof_harvest(m);
+    if (rc) return rc;
+  }
+  p.cls[p.used] = cls;
+  FSI_CUDA(cudaEventRecord(p.ev[2 * p.used], m->stream));
+  return FSI_OK;
+}
+
+int prof_end(fsi_mesh* m, int cls) {
+  Profiler& p = m->prof;
+  if (!p.on) return FSI_OK;
+  FSI_CUDA(cudaEventRecord(p.ev[2 * p.used + 1], m->stream));
+  p.used++;
+  return FSI_OK;
+}
+
 void tile_grid(const fsi_mesh* m, dim3* grid) {
   const int ncx = (m->g.nx + 1 + OX - 1) / OX;
   const int ncy = (m->g.ny + 1 + OY - 1) / OY;
@@ -83,10 +122,10 @@ int stage(fsi_mesh* m, const fsi_state* st, bool fp32) {
     FSI_CUDA(cudaMalloc(&m->xd32, bytes / 2));
     FSI_CUDA(cudaMalloc(&m->mat32, sizeof(float) * (2 + m->ns) * m->nn));
   }
-  stage_kernel<<<vec_grid(m->nn), 256, 0, m->stream>>>(
-      st->x, st->xn, st->xdn, alpha1 ? nullptr : m->xa, m->xd, m->mat, fp32 ? m->xa32 : nullptr,
-      fp32 ? m->xd32 : nullptr, fp32 ? m->mat32 : nullptr, m->ncomp, m->nn, m->P, alpha1 ? 0 : 1);
-  FSI_CUDA(cudaGetLastError());
+  FSI_LAUNCH(m, P_STAGE,
+             stage_kernel<<<vec_grid(m->nn), 256, 0, m->stream>>>(
+                 st->x, st->xn, st->xdn, alpha1 ? nullptr : m->xa, m->xd, m->mat, fp32 ? m->xa32 : nullptr,
+                 fp32 ? m->xd32 : nullptr, fp32 ? m->mat32 : nullptr, m->ncomp, m->nn, m->P, alpha1 ? 0 : 1));
   m->staged_x = st->x;
   m->staged_xa = alpha1 ? st->x : m->xa;
   return FSI_OK;
@@ -284,7 +323,46 @@ int fsi_destroy_mesh(fsi_mesh* m) {
   cudaFree(m->wk);
   cudaFree(m->dinv);
   cudaFree(m->yvec);
+  cudaFree(m->partials_dot);
+  cudaFree(m->step_ws);
+  for (cudaEvent_t e : m->prof.ev) cudaEventDestroy(e);
   delete m;
+  return FSI_OK;
+}
+
+int fsi_profile(fsi_mesh* m, int32_t enable) {
+  if (!m) return set_error(FSI_EINVAL, "null mesh");
+  Profiler& p = m->prof;
+  if (enable) {
+    if (p.ev.empty()) {
+      p.ev.resize(2 * PROF_PAIRS);
+      p.cls.resize(PROF_PAIRS);
+      for (auto& e : p.ev) FSI_CUDA(cudaEventCreate(&e));
+    }
+    int rc = prof_harvest(m);
+    if (rc) return rc;
+    for (int c = 0; c < P_NCLS; ++c) { p.launches[c] = 0; p.ms[c] = 0.0; }
+    p.on = true;
+  } else {
+    int rc = prof_harvest(m);
+    if (rc) return rc;
+    p.on = false;
+  }
+  return FSI_OK;
+}
+
+int fsi_profile_read(fsi_mesh* m, fsi_profile_entry* out, int32_t* n_out) {
+  if (!m || !out) return set_error(FSI_EINVAL, "null argument");
+  FSI_CUDA(cudaStreamSynchronize(m->stream));
+  int rc = prof_harvest(m);
+  if (rc) return rc;
+  for (int c = 0; c < P_NCLS; ++c) {
+    memset(out[c].name, 0, sizeof(out[c].name));
+    strncpy(out[c].name, kProfNames[c], sizeof(out[c].name) - 1);
+    out[c].launches = m->prof.launches[c];
+    out[c].ms = m->prof.ms[c];
+  }
+  if (n_out) *n_out = P_NCLS;
   return FSI_OK;
 }
 

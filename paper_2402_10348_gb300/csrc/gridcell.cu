@@ -297,8 +297,7 @@ extern "C" int fsi_init_phases(fsi_mesh* m, const fsi_surface* surfs, int32_t n_
     FSI_CUDA(cudaMemcpyAsync(dT.p, S.tris, sizeof(int) * 3 * S.n_tris, cudaMemcpyHostToDevice, s));
     FSI_CUDA(cudaMemsetAsync(dcounts.p, 0, sizeof(int) * ncell, s));
     const int tb = 128, tg = (S.n_tris + tb - 1) / tb;
-    tri_ranges<<<tg, tb, 0, s>>>(dV.p, dT.p, S.n_tris, G, drange.p, dcounts.p);
-    FSI_CUDA(cudaGetLastError());
+    FSI_LAUNCH(m, P_INIT, tri_ranges<<<tg, tb, 0, s>>>(dV.p, dT.p, S.n_tris, G, drange.p, dcounts.p));
     FSI_CUDA(cudaMemcpyAsync(counts.data(), dcounts.p, sizeof(int) * ncell, cudaMemcpyDeviceToHost, s));
     FSI_CUDA(cudaStreamSynchronize(s));
     int64_t total = 0;
@@ -310,16 +309,13 @@ extern "C" int fsi_init_phases(fsi_mesh* m, const fsi_surface* surfs, int32_t n_
     FSI_CUDA(dlist.alloc((size_t)total));
     FSI_CUDA(cudaMemcpyAsync(doffs.p, offs.data(), sizeof(int) * ncell, cudaMemcpyHostToDevice, s));
     FSI_CUDA(cudaMemsetAsync(dcursor.p, 0, sizeof(int) * ncell, s));
-    tri_fill<<<tg, tb, 0, s>>>(drange.p, S.n_tris, G, doffs.p, dcursor.p, dlist.p);
-    FSI_CUDA(cudaGetLastError());
-    empty_cells<<<(ncell + 127) / 128, 128, 0, s>>>(dV.p, dT.p, drange.p, doffs.p, dcounts.p, dlist.p, G, dfirst.p,
-                                                   gmax, dcellx.p, derr.p);
-    FSI_CUDA(cudaGetLastError());
-    node_phi<<<(unsigned)((nn + 127) / 128), 128, 0, s>>>(dV.p, dT.p, drange.p, doffs.p, dcounts.p, dlist.p,
+    FSI_LAUNCH(m, P_INIT, tri_fill<<<tg, tb, 0, s>>>(drange.p, S.n_tris, G, doffs.p, dcursor.p, dlist.p));
+    FSI_LAUNCH(m, P_INIT, empty_cells<<<(ncell + 127) / 128, 128, 0, s>>>(dV.p, dT.p, drange.p, doffs.p, dcounts.p, dlist.p, G, dfirst.p,
+                                                   gmax, dcellx.p, derr.p));
+    FSI_LAUNCH(m, P_INIT, node_phi<<<(unsigned)((nn + 127) / 128), 128, 0, s>>>(dV.p, dT.p, drange.p, doffs.p, dcounts.p, dlist.p,
                                                           dcellx.p, G, phis.p + (int64_t)si * nn,
                                                           tags_out ? tags_out + (int64_t)si * 4 * nn : nullptr, nn,
-                                                          derr.p);
-    FSI_CUDA(cudaGetLastError());
+                                                          derr.p));
     FSI_CUDA(cudaStreamSynchronize(s));  // the surface buffers are freed at scope exit
   }
   std::vector<RuleDev> rd(m->N);
@@ -327,9 +323,8 @@ extern "C" int fsi_init_phases(fsi_mesh* m, const fsi_surface* surfs, int32_t n_
   DevBuf<RuleDev> drules;
   FSI_CUDA(drules.alloc(m->N));
   FSI_CUDA(cudaMemcpyAsync(drules.p, rd.data(), sizeof(RuleDev) * m->N, cudaMemcpyHostToDevice, s));
-  apply_rules_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(phis.p, drules.p, m->N, phi_out, nn, m->g.nx,
-                                                                   m->g.ny, m->g.hz, G.scale);
-  FSI_CUDA(cudaGetLastError());
+  FSI_LAUNCH(m, P_INIT, apply_rules_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(phis.p, drules.p, m->N, phi_out, nn, m->g.nx,
+                                                                   m->g.ny, m->g.hz, G.scale));
   int herr = 0;
   FSI_CUDA(cudaMemcpyAsync(&herr, derr.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   FSI_CUDA(cudaStreamSynchronize(s));

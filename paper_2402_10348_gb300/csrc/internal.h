@@ -9,6 +9,22 @@
 #include "../../include/fsi.h"
 #include "ops.cuh"
 
+namespace fsi {
+// Kernel classes of the event profiler (fsi_profile).
+enum ProfClass {
+  P_STAGE, P_NS_RES, P_NS_JVP64, P_NS_JVP32, P_NS_DIAG, P_AC_RES, P_AC_JVP64, P_AC_JVP32,
+  P_AC_DIAG, P_B_RES, P_B_JVP64, P_B_JVP32, P_B_DIAG, P_COEF, P_KRYLOV, P_INIT, P_NCLS
+};
+struct Profiler {
+  bool on = false;
+  int64_t launches[P_NCLS] = {};
+  double ms[P_NCLS] = {};
+  std::vector<cudaEvent_t> ev;  // pool of event pairs
+  std::vector<int> cls;         // class of each recorded pair
+  int used = 0;                 // pairs recorded since the last harvest
+};
+}  // namespace fsi
+
 struct fsi_mesh {
   int dev = 0;
   cudaStream_t stream = nullptr;
@@ -52,6 +68,7 @@ struct fsi_mesh {
   // counters (step info)
   int64_t applies = 0;
   int64_t dof_applied = 0;
+  fsi::Profiler prof;
 };
 
 namespace fsi {
@@ -101,5 +118,18 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& b, const double* rhs, double* x, c
 
 // tile launch geometry
 void tile_grid(const fsi_mesh* m, dim3* grid);
+
+// profiler: bracket every launch with prof_begin / prof_end (api.cu)
+int prof_begin(fsi_mesh* m, int cls);
+int prof_end(fsi_mesh* m, int cls);
+int prof_harvest(fsi_mesh* m);
+#define FSI_LAUNCH(m, cls, ...)                      \
+  do {                                               \
+    int _rc = fsi::prof_begin((m), (cls));           \
+    if (_rc) return _rc;                             \
+    __VA_ARGS__;                                     \
+    FSI_CUDA(cudaGetLastError());                    \
+    if ((_rc = fsi::prof_end((m), (cls)))) return _rc; \
+  } while (0)
 
 }  // namespace fsi

@@ -126,10 +126,8 @@ static int dot_to_device(fsi_mesh* m, const double* V, int64_t ldv, int k, const
                          int accumulate) {
   const int G = vgrid(n);
   dim3 grid(G, (k + DCH - 1) / DCH);
-  mdot_kernel<<<grid, VB, 0, m->stream>>>(V, ldv, k, w, n, m->partials_dot);
-  FSI_CUDA(cudaGetLastError());
-  sum_partials<<<k, VB, 0, m->stream>>>(m->partials_dot, G, out, accumulate);
-  FSI_CUDA(cudaGetLastError());
+  FSI_LAUNCH(m, P_KRYLOV, mdot_kernel<<<grid, VB, 0, m->stream>>>(V, ldv, k, w, n, m->partials_dot));
+  FSI_LAUNCH(m, P_KRYLOV, sum_partials<<<k, VB, 0, m->stream>>>(m->partials_dot, G, out, accumulate));
   return FSI_OK;
 }
 
@@ -143,23 +141,19 @@ int vec_dot(fsi_mesh* m, const double* a, const double* b, int64_t n, double* ou
 }
 
 int vec_axpy(fsi_mesh* m, double a, const double* x, double* y, int64_t n) {
-  axpby_kernel<<<vgrid(n), VB, 0, m->stream>>>(a, x, 1.0, y, n);
-  FSI_CUDA(cudaGetLastError());
+  FSI_LAUNCH(m, P_KRYLOV, axpby_kernel<<<vgrid(n), VB, 0, m->stream>>>(a, x, 1.0, y, n));
   return FSI_OK;
 }
 int vec_scale_copy(fsi_mesh* m, double a, const double* x, double* y, int64_t n) {
-  axpby_kernel<<<vgrid(n), VB, 0, m->stream>>>(a, x, 0.0, y, n);
-  FSI_CUDA(cudaGetLastError());
+  FSI_LAUNCH(m, P_KRYLOV, axpby_kernel<<<vgrid(n), VB, 0, m->stream>>>(a, x, 0.0, y, n));
   return FSI_OK;
 }
 int vec_mul(fsi_mesh* m, const double* a, const double* b, double* y, int64_t n) {
-  mul_kernel<<<vgrid(n), VB, 0, m->stream>>>(a, b, y, n);
-  FSI_CUDA(cudaGetLastError());
+  FSI_LAUNCH(m, P_KRYLOV, mul_kernel<<<vgrid(n), VB, 0, m->stream>>>(a, b, y, n));
   return FSI_OK;
 }
 int vec_recip(fsi_mesh* m, const double* a, double* y, int64_t n) {
-  recip_kernel<<<vgrid(n), VB, 0, m->stream>>>(a, y, n);
-  FSI_CUDA(cudaGetLastError());
+  FSI_LAUNCH(m, P_KRYLOV, recip_kernel<<<vgrid(n), VB, 0, m->stream>>>(a, y, n));
   return FSI_OK;
 }
 
@@ -222,14 +216,11 @@ static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double
       if ((rc = op_jvp(m, blk, z, w, flags))) return rc;
       // CGS2
       if ((rc = dot_to_device(m, V, n, j + 1, w, n, dev, 0))) return rc;
-      upd_kernel<<<vgrid(n), VB, 0, m->stream>>>(w, V, n, j + 1, dev, n, nullptr);
-      FSI_CUDA(cudaGetLastError());
+      FSI_LAUNCH(m, P_KRYLOV, upd_kernel<<<vgrid(n), VB, 0, m->stream>>>(w, V, n, j + 1, dev, n, nullptr));
       if ((rc = dot_to_device(m, V, n, j + 1, w, n, dev + 128, 0))) return rc;
       const int G = vgrid(n);
-      upd_kernel<<<G, VB, 0, m->stream>>>(w, V, n, j + 1, dev + 128, n, m->partials_dot);
-      FSI_CUDA(cudaGetLastError());
-      sum_partials<<<1, VB, 0, m->stream>>>(m->partials_dot, G, dev + 256, 0);
-      FSI_CUDA(cudaGetLastError());
+      FSI_LAUNCH(m, P_KRYLOV, upd_kernel<<<G, VB, 0, m->stream>>>(w, V, n, j + 1, dev + 128, n, m->partials_dot));
+      FSI_LAUNCH(m, P_KRYLOV, sum_partials<<<1, VB, 0, m->stream>>>(m->partials_dot, G, dev + 256, 0));
       FSI_CUDA(cudaMemcpyAsync(m->red_host, dev, sizeof(double) * 257, cudaMemcpyDeviceToHost, m->stream));
       FSI_CUDA(cudaStreamSynchronize(m->stream));
       const double* hh = m->red_host;
@@ -239,8 +230,7 @@ static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double
       const double hn = std::sqrt(hn2);
       Hij(j + 1, j) = hn;
       if (hn > 0.0) {
-        scale_by_norm<<<vgrid(n), VB, 0, m->stream>>>(w, dev + 256, n);
-        FSI_CUDA(cudaGetLastError());
+        FSI_LAUNCH(m, P_KRYLOV, scale_by_norm<<<vgrid(n), VB, 0, m->stream>>>(w, dev + 256, n));
       }
       for (int i = 0; i < j; ++i) {
         const double a = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
@@ -264,8 +254,7 @@ static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double
       y[i] = Hij(i, i) != 0.0 ? s / Hij(i, i) : 0.0;
     }
     FSI_CUDA(cudaMemcpyAsync(m->yvec, y.data(), sizeof(double) * jend, cudaMemcpyHostToDevice, m->stream));
-    combine_kernel<<<vgrid(n), VB, 0, m->stream>>>(x, m->dinv, V, n, jend, m->yvec, n);
-    FSI_CUDA(cudaGetLastError());
+    FSI_LAUNCH(m, P_KRYLOV, combine_kernel<<<vgrid(n), VB, 0, m->stream>>>(x, m->dinv, V, n, jend, m->yvec, n));
     // true residual r = b - A x
     if ((rc = op_jvp(m, blk, x, t, flags))) return rc;
     FSI_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, m->stream));
@@ -291,8 +280,7 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& blk, const double* rhs, double* x,
     if ((rc = op_diag(m, blk, m->wk + 3 * n, o.flags & ~FSI_FP32))) return rc;
     if ((rc = vec_recip(m, m->wk + 3 * n, m->dinv, n))) return rc;
   } else {
-    fill_kernel<<<vgrid(n), VB, 0, m->stream>>>(m->dinv, 1.0, n);
-    FSI_CUDA(cudaGetLastError());
+    FSI_LAUNCH(m, P_KRYLOV, fill_kernel<<<vgrid(n), VB, 0, m->stream>>>(m->dinv, 1.0, n));
   }
   fsi_solve_info inf{};
   double rel = 0.0;

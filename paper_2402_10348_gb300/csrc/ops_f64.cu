@@ -45,10 +45,9 @@ int op_coeffs(fsi_mesh* m, int i, double* gb) {
     m->n_partials = ncta;
   }
   op.partials = m->partials;
-  int rc = run_tile(m, op);
+  int rc = run_tile(m, op, P_COEF);
   if (rc) return rc;
-  coef_finalize<<<1, NTHREADS, 0, m->stream>>>(m->partials, ncta, m->P.eta, m->red);
-  FSI_CUDA(cudaGetLastError());
+  FSI_LAUNCH(m, P_COEF, coef_finalize<<<1, NTHREADS, 0, m->stream>>>(m->partials, ncta, m->P.eta, m->red));
   FSI_CUDA(cudaMemcpyAsync(m->red_host, m->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
   FSI_CUDA(cudaStreamSynchronize(m->stream));
   gb[0] = m->red_host[0];

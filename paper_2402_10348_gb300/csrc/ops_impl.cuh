@@ -34,7 +34,7 @@ inline void fill_common(const fsi_mesh* m, double rh[3], double* W) {
 }
 
 template <class Op>
-int run_tile(fsi_mesh* m, const Op& op) {
+int run_tile(fsi_mesh* m, const Op& op, int cls) {
   const size_t smem = tile_smem_bytes<Op>(op.nf);
   static size_t configured = 0;
   if (smem > configured) {
@@ -43,9 +43,20 @@ int run_tile(fsi_mesh* m, const Op& op) {
   }
   dim3 grid;
   tile_grid(m, &grid);
-  tile_kernel<Op><<<grid, NTHREADS, smem, m->stream>>>(op, m->g);
-  FSI_CUDA(cudaGetLastError());
+  FSI_LAUNCH(m, cls, tile_kernel<Op><<<grid, NTHREADS, smem, m->stream>>>(op, m->g));
   return FSI_OK;
+}
+
+template <typename T>
+constexpr int jvp_class(int kind) {
+  return kind == 0 ? (sizeof(T) == 8 ? P_NS_JVP64 : P_NS_JVP32)
+                   : (kind == 1 ? (sizeof(T) == 8 ? P_AC_JVP64 : P_AC_JVP32) : (sizeof(T) == 8 ? P_B_JVP64 : P_B_JVP32));
+}
+template <typename T, int MODE>
+constexpr int op_class(int kind) {
+  return MODE == 1 ? jvp_class<T>(kind)
+                   : (MODE == 0 ? (kind == 0 ? P_NS_RES : (kind == 1 ? P_AC_RES : P_B_RES))
+                                : (kind == 0 ? P_NS_DIAG : (kind == 1 ? P_AC_DIAG : P_B_DIAG)));
 }
 
 constexpr size_t SMEM_LIMIT = 232448;
@@ -97,7 +108,7 @@ int ns_pass(fsi_mesh* m, const double* dx, double* y, unsigned flags, int s0, in
   op.out.accumulate = first ? 0 : 1;
   op.out.dirichlet = first ? 1 : 0;
   op.nn_ = nn;
-  return run_tile(m, op);
+  return run_tile(m, op, op_class<T, MODE>(0));
 }
 
 template <typename T>
@@ -142,7 +153,7 @@ int ac_run(fsi_mesh* m, int i, const double* dx, double* y) {
   op.beta = m->beta[i];
   op.out.y = y;
   op.nn_ = nn;
-  return run_tile(m, op);
+  return run_tile(m, op, op_class<T, MODE>(1));
 }
 
 template <typename T>
@@ -175,7 +186,7 @@ int b_run(fsi_mesh* m, int s, const double* dx, double* y) {
   fill_common(m, op.rh, &op.W);
   op.out.y = y;
   op.nn_ = nn;
-  return run_tile(m, op);
+  return run_tile(m, op, op_class<T, MODE>(2));
 }
 
 template <typename T>

@@ -65,8 +65,8 @@ int fsi_step(fsi_mesh* m, fsi_state* st, const fsi_step_opts* o, fsi_step_info* 
   const bool fp32 = o->solve.precision == FSI_PREC_FP32_IR;
   fsi_step_info inf{};
   const int64_t a0 = m->applies, d0 = m->dof_applied;
-  predictor_kernel<<<grid_for(nn), 256, 0, m->stream>>>(st->x, st->xn, m->mask, m->vD, m->ncomp, nn);
-  FSI_CUDA(cudaGetLastError());
+  FSI_LAUNCH(m, P_STAGE,
+             predictor_kernel<<<grid_for(nn), 256, 0, m->stream>>>(st->x, st->xn, m->mask, m->vD, m->ncomp, nn));
   int rc;
   const int nblocks = 1 + m->N + m->ns;
   for (int k = 0; k < o->k_max; ++k) {
@@ -104,9 +104,9 @@ int fsi_step(fsi_mesh* m, fsi_state* st, const fsi_step_opts* o, fsi_step_info* 
     inf.max_ratio = max_ratio;
     if (!o->fixed_iters && max_ratio < o->nl_tol) break;
   }
-  corrector_kernel<<<grid_for(nn * m->ncomp), 256, 0, m->stream>>>(st->x, st->xn, st->xdn, m->P.dt, m->P.vs,
-                                                                   nn * m->ncomp);
-  FSI_CUDA(cudaGetLastError());
+  FSI_LAUNCH(m, P_STAGE,
+             corrector_kernel<<<grid_for(nn * m->ncomp), 256, 0, m->stream>>>(st->x, st->xn, st->xdn, m->P.dt,
+                                                                              m->P.vs, nn * m->ncomp));
   FSI_CUDA(cudaStreamSynchronize(m->stream));
   inf.applies = (int)(m->applies - a0);
   inf.dof_applied = m->dof_applied - d0;

@@ -95,9 +95,15 @@ class fsi_phase_rule(C.Structure):
                 ("plane_side", C.c_int32), ("pad", C.c_int32)]
 
 
+class fsi_profile_entry(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("ms", C.c_double)]
+
+
+FSI_PROF_CLASSES = 16
+
 EXPORTS = ["fsi_create_mesh", "fsi_destroy_mesh", "fsi_set_stream", "fsi_mesh_info", "fsi_residual",
            "fsi_jvp", "fsi_diag", "fsi_update_ac_coeffs", "fsi_set_ac_coeffs", "fsi_fix_gamma",
-           "fsi_gmres", "fsi_step", "fsi_init_phases", "fsi_last_error"]
+           "fsi_gmres", "fsi_step", "fsi_init_phases", "fsi_profile", "fsi_profile_read", "fsi_last_error"]
 
 _lib = None
 
@@ -272,3 +278,15 @@ def fsi_init_phases(mesh: Mesh, surfaces, rules, grid, phi_out, tags_out=None):
         tp = _ptr(tags_out)
     _check(lib().fsi_init_phases(mesh.handle, S, C.c_int32(len(surfaces)), R, C.c_int32(grid[0]),
                                  C.c_int32(grid[1]), C.c_int32(grid[2]), _dptr(phi_out), tp))
+
+
+def fsi_profile(mesh: Mesh, enable: bool):
+    _check(lib().fsi_profile(mesh.handle, C.c_int32(1 if enable else 0)))
+
+
+def fsi_profile_read(mesh: Mesh) -> dict:
+    """{kernel class: (launches, summed event ms)}; synchronises the mesh's stream."""
+    out = (fsi_profile_entry * FSI_PROF_CLASSES)()
+    n = C.c_int32()
+    _check(lib().fsi_profile_read(mesh.handle, out, C.byref(n)))
+    return {out[i].name.decode(): (out[i].launches, out[i].ms) for i in range(n.value)}
