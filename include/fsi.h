@@ -236,6 +236,27 @@ int fsi_init_phases(fsi_mesh* mesh, const fsi_surface* surfaces, int32_t n_surf,
                     const fsi_phase_rule* rules, int32_t gx, int32_t gy, int32_t gz,
                     double* phi_out, int32_t* tags_out);
 
+/* --------------------------------------------------------------- allocation-free variant
+ * (no counterpart in the paper.)  gamma and beta of one phase, as fsi_update_ac_coeffs
+ * computes them, for callers that cannot call cudaMalloc: code that must not
+ * synchronise the device (cudaMalloc and cudaFree may) and code inside a framework
+ * whose allocator owns all device memory.  It needs no mesh handle and allocates
+ * nothing: its per-CTA partial sums live in a file-scope __device__ array of the
+ * library, 512 KiB per device, held by every GPU that loads the library until the
+ * process exits.
+ *   v          device float64 [3][nn]: v^{n+alpha} (x^{n+1} when rho_inf = 0)
+ *   phi        device float64 [nn]:    phi^{n+alpha} of the phase
+ *   gamma_beta device float64 [2]:     written {gamma, beta} (stream-ordered)
+ *   stream     cudaStream_t (NULL = legacy default stream)
+ * Meshes needing more than 16384 per-CTA partial sums (about 37 M nodes) are
+ * rejected with FSI_EINVAL.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current: make that first call
+ * before any stream capture.  All calls share the one array, which keeps the last
+ * call's contents (every launch overwrites the slots it reads, so nothing has to
+ * start at zero); calls that overlap on the GPU race on it. */
+int fsi_gamma_beta_noalloc(int32_t nx, int32_t ny, int32_t nz, double lx, double ly, double lz, double eta,
+                           const double* v, const double* phi, double* gamma_beta, void* stream);
+
 /* --------------------------------------------------------------- measurement
  * (no counterpart in the paper: timing support for the benchmark)
  * fsi_profile(mesh, 1) starts recording a CUDA event pair around every kernel the

@@ -103,7 +103,8 @@ FSI_PROF_CLASSES = 16
 
 EXPORTS = ["fsi_create_mesh", "fsi_destroy_mesh", "fsi_set_stream", "fsi_mesh_info", "fsi_residual",
            "fsi_jvp", "fsi_diag", "fsi_update_ac_coeffs", "fsi_set_ac_coeffs", "fsi_fix_gamma",
-           "fsi_gmres", "fsi_step", "fsi_init_phases", "fsi_profile", "fsi_profile_read", "fsi_last_error"]
+           "fsi_gmres", "fsi_step", "fsi_init_phases", "fsi_gamma_beta_noalloc", "fsi_profile",
+           "fsi_profile_read", "fsi_last_error"]
 
 _lib = None
 
@@ -278,6 +279,15 @@ def fsi_init_phases(mesh: Mesh, surfaces, rules, grid, phi_out, tags_out=None):
         tp = _ptr(tags_out)
     _check(lib().fsi_init_phases(mesh.handle, S, C.c_int32(len(surfaces)), R, C.c_int32(grid[0]),
                                  C.c_int32(grid[1]), C.c_int32(grid[2]), _dptr(phi_out), tp))
+
+
+def fsi_gamma_beta_noalloc(nx, ny, nz, lx, ly, lz, eta, v, phi, gamma_beta, stream=None):
+    """gamma, beta of one phase written to the device tensor gamma_beta[2]; no allocation.
+    v: device float64 [3*nn] (v^{n+alpha}), phi: device float64 [nn] (phi^{n+alpha})."""
+    st = torch.cuda.current_stream() if stream is None else stream
+    _check(lib().fsi_gamma_beta_noalloc(C.c_int32(nx), C.c_int32(ny), C.c_int32(nz), C.c_double(lx),
+                                        C.c_double(ly), C.c_double(lz), C.c_double(eta), _dptr(v), _dptr(phi),
+                                        _dptr(gamma_beta), C.c_void_p(st.cuda_stream)))
 
 
 def fsi_profile(mesh: Mesh, enable: bool):
