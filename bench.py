@@ -185,7 +185,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     fsi.fsi_set_stream(mesh, stream)
     prec = fsi.FSI_PREC_FP32_IR if args.precision == "fp32ir" else fsi.FSI_PREC_FP64
-    solve = fsi.solve_opts(m=30, rtol=1e-8, max_iter=4000, precision=prec, ir_inner_rtol=1e-3, ir_max=30)
+    solve = fsi.solve_opts(m=64, rtol=1e-8, max_iter=3000, precision=prec, ir_inner_rtol=1e-3, ir_max=30)
 
     x, xn, xdn = initial_state(fsi, mesh, wl, torch, dev)
 
@@ -254,7 +254,7 @@ def run_gpu(args):
                       "Gram-Schmidt, Hessenberg" if prec == fsi.FSI_PREC_FP32_IR else "float64 throughout"),
         "data": "synthetic (seeded icosphere surface, initial phases by the grid-cell method)",
         "config": {"workload": WORKLOAD, "nodes": d.nn, "dof_per_node": d.ncomp, "dt": d.dt,
-                   "nl_iters_max": wl.k_max, "gmres": "Jacobi GMRES(30) rtol 1e-8",
+                   "nl_iters_max": wl.k_max, "gmres": "Jacobi GMRES(64) rtol 1e-8, stop on stagnation",
                    "l2": "working set per step > L2 (Krylov basis 31 x 1.1M float64 = 272 MB per NS solve)",
                    "parallelism": f"replicas x{world}"},
         "s_per_timestep": round(ms / args.steps / 1e3, 5),
@@ -262,7 +262,8 @@ def run_gpu(args):
                        "gmres_iters_ns": [i.gmres_iters_ns for i in infos],
                        "gmres_iters_ac": [i.gmres_iters_ac for i in infos],
                        "gmres_iters_b": [i.gmres_iters_b for i in infos],
-                       "worst_rel_res": max(i.worst_rel_res for i in infos)},
+                       "worst_rel_res": max(i.worst_rel_res for i in infos),
+                       "stalled_solves": [i.stalled_solves for i in infos]},
         "gpu_launches": launches,
         "kernel_ms": {k: [v[0], round(v[1], 3)] for k, v in prof.items() if v[0] > 0},
         "roofline": roof,

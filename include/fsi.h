@@ -167,6 +167,10 @@ typedef struct {
   int32_t refinements;  /* FP32_IR outer steps                                   */
   int32_t applies;      /* operator applies (all precisions)                     */
   double rel_res;       /* final ||b - A x|| / ||b|| (float64 operator)           */
+  int32_t stalled;      /* 1: stopped because a whole restart cycle reduced the
+                           true residual by less than 1 % (or an FP32_IR
+                           refinement by less than 10 %)                          */
+  int32_t pad;
 } fsi_solve_info;
 
 /* Solves J(st) x = rhs for one block by right-preconditioned restarted GMRES from
@@ -188,6 +192,7 @@ typedef struct {
   int32_t nl_iters;
   int32_t gmres_iters_ns, gmres_iters_ac, gmres_iters_b;
   int32_t applies;           /* operator applies (residuals and products)      */
+  int32_t stalled_solves;    /* block solves that stopped on stagnation        */
   int64_t dof_applied;       /* sum over applies of the block's DoF count      */
   double max_ratio;          /* last iteration's max ||dx_blk|| / ||x_blk||     */
   double worst_rel_res;      /* largest final linear relative residual         */
@@ -263,7 +268,7 @@ int fsi_gamma_beta_noalloc(int32_t nx, int32_t ny, int32_t nz, double lx, double
  * mesh launches (counters reset); fsi_profile(mesh, 0) stops.  Launch counts are
  * kept whether or not events are recorded.  fsi_profile_read synchronises the
  * stream and returns, per kernel class, the launches and the summed event time. */
-#define FSI_PROF_CLASSES 16
+#define FSI_PROF_CLASSES 20
 typedef struct {
   char name[24];
   int64_t launches;

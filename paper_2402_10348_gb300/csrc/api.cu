@@ -22,7 +22,8 @@ int cuda_check(cudaError_t e, const char* what) {
 
 static const char* kProfNames[P_NCLS] = {
     "stage", "ns_residual", "ns_jvp_f64", "ns_jvp_f32", "ns_diag", "ac_residual", "ac_jvp_f64", "ac_jvp_f32",
-    "ac_diag", "b_residual", "b_jvp_f64", "b_jvp_f32", "b_diag", "gamma_beta", "krylov_vector", "init"};
+    "ac_diag", "b_residual", "b_jvp_f64", "b_jvp_f32", "b_diag", "gamma_beta", "krylov_vector", "init",
+    "krylov_dot", "krylov_update", "krylov_scalar", "to_float"};
 constexpr int PROF_PAIRS = 4096;
 
 int prof_harvest(fsi_mesh* m) {
@@ -156,10 +157,19 @@ int op_residual(fsi_mesh* m, const BlockInfo& b, double* r) {
   return launch_b<double>(m, 0, b.index, nullptr, r);
 }
 
+__global__ void to_float_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) b[i] = (float)a[i];
+}
+
 int op_jvp(fsi_mesh* m, const BlockInfo& b, const double* dx, double* y, unsigned flags) {
   m->applies++;
   m->dof_applied += b.n;
   const bool f32 = flags & FSI_FP32;
+  if (f32) {  // float copy of the increment for the float32 kernels
+    if (!m->dx32) FSI_CUDA(cudaMalloc(&m->dx32, sizeof(float) * 6 * (size_t)m->nn));
+    FSI_LAUNCH(m, P_KRY_CONV, to_float_kernel<<<vec_grid(b.n), 256, 0, m->stream>>>(dx, m->dx32, b.n));
+  }
   if (b.kind == 0)
     return f32 ? launch_ns<float>(m, 1, dx, y, flags) : launch_ns<double>(m, 1, dx, y, flags);
   if (b.kind == 1)
@@ -325,6 +335,10 @@ int fsi_destroy_mesh(fsi_mesh* m) {
   cudaFree(m->yvec);
   cudaFree(m->partials_dot);
   cudaFree(m->step_ws);
+  cudaFree(m->kry_dev);
+  cudaFree(m->dx32);
+  if (m->kry_est) cudaFreeHost(m->kry_est);
+  for (cudaEvent_t e : m->kry_ev) cudaEventDestroy(e);
   for (cudaEvent_t e : m->prof.ev) cudaEventDestroy(e);
   delete m;
   return FSI_OK;

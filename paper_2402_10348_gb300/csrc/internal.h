@@ -13,7 +13,8 @@ namespace fsi {
 // Kernel classes of the event profiler (fsi_profile).
 enum ProfClass {
   P_STAGE, P_NS_RES, P_NS_JVP64, P_NS_JVP32, P_NS_DIAG, P_AC_RES, P_AC_JVP64, P_AC_JVP32,
-  P_AC_DIAG, P_B_RES, P_B_JVP64, P_B_JVP32, P_B_DIAG, P_COEF, P_KRYLOV, P_INIT, P_NCLS
+  P_AC_DIAG, P_B_RES, P_B_JVP64, P_B_JVP32, P_B_DIAG, P_COEF, P_KRYLOV, P_INIT, P_KRY_DOT, P_KRY_UPD,
+  P_KRY_SMALL, P_KRY_CONV, P_NCLS
 };
 struct Profiler {
   bool on = false;
@@ -44,6 +45,7 @@ struct fsi_mesh {
   float* xa32 = nullptr;    // float copies for FSI_FP32
   float* xd32 = nullptr;
   float* mat32 = nullptr;
+  float* dx32 = nullptr;     // float copy of a product's increment (FSI_FP32)
   const double* staged_x = nullptr;  // x^{n+1} of the last staging (p and Dirichlet rows)
   const double* staged_xa = nullptr; // the x^{n+alpha} array in use
   // coefficients
@@ -63,6 +65,9 @@ struct fsi_mesh {
   double* dinv = nullptr;    // [n]
   double* yvec = nullptr;    // [m+1] device
   double* partials_dot = nullptr;  // per-CTA partial dot products
+  void* kry_dev = nullptr;   // device Arnoldi/Givens state
+  double* kry_est = nullptr; // pinned host copies of the residual estimates
+  std::vector<cudaEvent_t> kry_ev;
   double* step_ws = nullptr; // [2][max block] time-step work vectors
   int64_t step_ws_n = 0;
   // counters (step info)

@@ -1,7 +1,29 @@
-// Krylov solver of libfsi: restarted right-preconditioned GMRES with classical
-// Gram-Schmidt applied twice (CGS2), Givens rotations on the host, float64 vectors;
-// optional float32 operator inside float64 iterative refinement.  Every reduction
-// is deterministic (fixed partition, fixed summation order).
+// Krylov solver of libfsi: restarted right-preconditioned GMRES(m) (the paper's
+// linear solver, Section 2.5) on float64 vectors, optionally with a float32 operator
+// inside float64 iterative refinement.
+//
+// Basis layout: the vectors V_0..V_m are stored chunk-interleaved, CH = 256
+// elements per chunk, all m+1 vectors of a chunk contiguous:
+//     V_i[j] = V[(j / CH) * (M1 * CH) + i * CH + j % CH],   M1 = slots per chunk.
+// A CTA of the projection kernels walks whole chunks, so it streams one contiguous
+// block of k x 2 KiB per chunk instead of k separate streams 8.8 MB apart (measured
+// 3.9 vs 2.7 TB/s read on GB300 for 33 vectors of the 64^3 NS block).
+//
+// Arnoldi step j (D = diag(dinv)):
+//   z = D V_j;  w = J z   (w: a contiguous work vector written by the operator)
+//   h = V^T w and |w|^2 in one pass over V_0..V_j      (mdot_kernel)
+//   w -= V h and |w|^2 in one pass                        (upd_kernel)
+//   if |w_new| < |w_old| / sqrt(2): once more (classical Gram-Schmidt with the DGKS
+//   re-orthogonalization test; the second pass is launched always and exits at once
+//   when the device-side flag says it is not needed)
+//   Givens rotation of the new Hessenberg column and the residual estimate on the
+//   device; V_{j+1} = w / |w| stored into its slot.
+// The host enqueues step j and only then waits for step j-1's residual estimate
+// (copied to pinned memory), so it never stalls the GPU between steps; at most one
+// step beyond convergence is computed and ignored.  The least-squares solution and
+// x += D V y are device kernels.  One host synchronisation per restart recomputes
+// the true residual b - A x.  All reductions use a fixed partition and a fixed
+// summation order (bit-reproducible).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -11,10 +33,28 @@
 
 namespace fsi {
 
-constexpr int VB = 256;          // threads per CTA of the vector kernels
-constexpr int DCH = 16;          // dot products per CTA pass
+constexpr int VB = 256;   // threads per CTA of the vector kernels
+constexpr int CH = 256;   // elements per basis chunk (one per thread)
+constexpr int DCH = 16;   // dot products per CTA pass
+constexpr int MMAX = 64;  // largest restart length
 
-static int vgrid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + VB * 8 - 1) / (VB * 8), 152 * 4)); }
+static int vgrid(int64_t n) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + VB * 4 - 1) / (VB * 4), 152 * 4));
+}
+static int cgrid(int64_t nch) { return (int)std::max<int64_t>(1, std::min<int64_t>(nch, 152 * 4)); }
+
+// device-resident Arnoldi/Givens state (inside fsi_mesh::kry_dev)
+struct KryDev {
+  double h[MMAX + 2];      // current column (pass 1), then the accumulated column
+  double h2[MMAX + 2];     // second pass
+  double H[(MMAX + 1) * MMAX];
+  double cs[MMAX], sn[MMAX], g[MMAX + 1], y[MMAX];
+  double nrm_old, nrm_new, nrm_fin;
+  double bnorm;
+  double est;              // |g_{j+1}| / |b|
+  int reorth;
+  int breakdown;
+};
 
 template <int K>
 __device__ __forceinline__ void block_reduce_store(double (&acc)[K], int kc, double* out, int stride) {
@@ -35,76 +75,183 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[K], int kc, dou
   }
 }
 
-// part[i*G + cta] = sum over the CTA's range of V_i . w,  i in [16*blockIdx.y, ...)
-__global__ void __launch_bounds__(VB) mdot_kernel(const double* __restrict__ V, int64_t ldv, int k,
-                                                  const double* __restrict__ w, int64_t n, double* part) {
+// --------------------------------------------------------- basis (chunked) kernels
+// part[(ib + i) * G + cta] = sum over the CTA's chunks of V_{ib+i} . w, i < KC,
+// ib = i0 + KC * blockIdx.y; with SELF the KC+1-th row is w . w (row i0 + KC).
+template <int KC, bool SELF>
+__global__ void __launch_bounds__(VB) mdot_kernel(const double* __restrict__ V, int M1, int i0,
+                                                  const double* __restrict__ w, int64_t n, double* part,
+                                                  const int* skip) {
+  if (skip && !*skip) return;
+  constexpr int NA = KC + (SELF ? 1 : 0);
   const int G = gridDim.x;
-  const int i0 = blockIdx.y * DCH;
-  const int kc = min(DCH, k - i0);
-  const int64_t per = (n + G - 1) / G;
-  const int64_t lo = blockIdx.x * per, hi = min(n, lo + per);
-  double acc[DCH];
+  const int ib = i0 + blockIdx.y * KC;
+  const int64_t nch = (n + CH - 1) / CH;
+  const int64_t per = (nch + G - 1) / G;
+  const int64_t c0 = blockIdx.x * per, c1 = min(nch, c0 + per);
+  double acc[NA > 0 ? NA : 1];
 #pragma unroll
-  for (int i = 0; i < DCH; ++i) acc[i] = 0.0;
-  for (int64_t j = lo + threadIdx.x; j < hi; j += VB) {
+  for (int i = 0; i < NA; ++i) acc[i] = 0.0;
+  for (int64_t c = c0; c < c1; ++c) {
+    const int64_t j = c * CH + threadIdx.x;
+    if (j >= n) break;
     const double wj = w[j];
+    const double* blk = V + c * (int64_t)M1 * CH + (int64_t)ib * CH + threadIdx.x;
 #pragma unroll
-    for (int i = 0; i < DCH; ++i)
-      if (i < kc) acc[i] += V[(int64_t)(i0 + i) * ldv + j] * wj;
+    for (int i = 0; i < KC; ++i) acc[i] += blk[i * CH] * wj;
+    if (SELF) acc[NA - 1] += wj * wj;
   }
-  block_reduce_store<DCH>(acc, kc, part + (int64_t)i0 * G + blockIdx.x, G);
+  block_reduce_store<(NA > 0 ? NA : 1)>(acc, NA, part + (int64_t)ib * G + blockIdx.x, G);
 }
 
-// out[i] = (accumulate ? out[i] : 0) + sum_c part[i*G + c]  (fixed order)
-__global__ void sum_partials(const double* __restrict__ part, int G, double* out, int accumulate) {
+// out[i] = sum_c part[i*G + c] (fixed order), i = blockIdx.x
+__global__ void sum_partials(const double* __restrict__ part, int G, double* out, const int* skip) {
+  if (skip && !*skip) return;
   const int i = blockIdx.x;
   double s = 0.0;
   for (int c = threadIdx.x; c < G; c += VB) s += part[(int64_t)i * G + c];
   double acc[1] = {s};
   __shared__ double res;
-  double* dst = &res;
-  block_reduce_store<1>(acc, 1, dst, 1);
+  block_reduce_store<1>(acc, 1, &res, 1);
   __syncthreads();
-  if (threadIdx.x == 0) out[i] = accumulate ? out[i] + res : res;
+  if (threadIdx.x == 0) out[i] = res;
 }
 
-// w -= sum_i h_i V_i ; optionally part[cta] = partial of |w|^2
-__global__ void __launch_bounds__(VB) upd_kernel(double* __restrict__ w, const double* __restrict__ V, int64_t ldv,
-                                                 int k, const double* __restrict__ h, int64_t n, double* part) {
-  __shared__ double hs[128];
+// sum_{i<k} hs_i V_i[j] for the element of this thread in chunk blk (8 loads in flight)
+__device__ __forceinline__ double lin_comb_chunk(const double* __restrict__ hs, const double* __restrict__ blk, int k) {
+  double p[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int i = 0;
+  for (; i + 8 <= k; i += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) p[u] += hs[i + u] * blk[(i + u) * CH];
+  }
+  for (; i < k; ++i) p[0] += hs[i] * blk[i * CH];
+  return ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+}
+
+// w -= sum_{i<k} h_i V_i ; part[cta] = partial of |w|^2   (w contiguous)
+__global__ void __launch_bounds__(VB) upd_kernel(double* __restrict__ w, const double* __restrict__ V, int M1, int k,
+                                                 const double* __restrict__ h, int64_t n, double* part,
+                                                 const int* skip) {
+  if (skip && !*skip) return;
+  __shared__ double hs[MMAX + 2];
   for (int i = threadIdx.x; i < k; i += VB) hs[i] = h[i];
   __syncthreads();
   const int G = gridDim.x;
-  const int64_t per = (n + G - 1) / G;
-  const int64_t lo = blockIdx.x * per, hi = min(n, lo + per);
+  const int64_t nch = (n + CH - 1) / CH;
+  const int64_t per = (nch + G - 1) / G;
+  const int64_t c0 = blockIdx.x * per, c1 = min(nch, c0 + per);
   double nrm[1] = {0.0};
-  for (int64_t j = lo + threadIdx.x; j < hi; j += VB) {
-    double s = w[j];
-    for (int i = 0; i < k; ++i) s -= hs[i] * V[(int64_t)i * ldv + j];
+  for (int64_t c = c0; c < c1; ++c) {
+    const int64_t j = c * CH + threadIdx.x;
+    if (j >= n) break;
+    const double s = w[j] - lin_comb_chunk(hs, V + c * (int64_t)M1 * CH + threadIdx.x, k);
     w[j] = s;
     nrm[0] += s * s;
   }
-  if (part) block_reduce_store<1>(nrm, 1, part + blockIdx.x, 1);
+  block_reduce_store<1>(nrm, 1, part + blockIdx.x, 1);
 }
 
-__global__ void scale_by_norm(double* w, const double* nrm2, int64_t n) {
-  const double s = 1.0 / sqrt(*nrm2);
-  for (int64_t j = blockIdx.x * (int64_t)VB + threadIdx.x; j < n; j += (int64_t)gridDim.x * VB) w[j] *= s;
+// V_slot[j] = src[j] * scale, scale = 1/sqrt(*n2) (n2 != null) or 1/K->nrm_fin
+__global__ void store_slot(double* __restrict__ V, int M1, int slot, const double* __restrict__ src, const double* n2,
+                           const KryDev* K, int64_t n) {
+  double s;
+  if (n2) {
+    s = 1.0 / sqrt(*n2);
+  } else {
+    const double nf = K->nrm_fin;
+    s = nf > 0.0 ? 1.0 / nf : 0.0;
+  }
+  for (int64_t j = blockIdx.x * (int64_t)VB + threadIdx.x; j < n; j += (int64_t)gridDim.x * VB)
+    V[(j / CH) * (int64_t)M1 * CH + (int64_t)slot * CH + (j % CH)] = src[j] * s;
+}
+
+// z = dinv * V_slot
+__global__ void precond_kernel(const double* __restrict__ V, int M1, int slot, const double* __restrict__ dinv,
+                               double* __restrict__ z, int64_t n) {
+  for (int64_t j = blockIdx.x * (int64_t)VB + threadIdx.x; j < n; j += (int64_t)gridDim.x * VB)
+    z[j] = dinv[j] * V[(j / CH) * (int64_t)M1 * CH + (int64_t)slot * CH + (j % CH)];
 }
 
 // x += dinv * sum_i y_i V_i
-__global__ void combine_kernel(double* __restrict__ x, const double* __restrict__ dinv, const double* __restrict__ V,
-                               int64_t ldv, int k, const double* __restrict__ y, int64_t n) {
-  __shared__ double ys[128];
-  for (int i = threadIdx.x; i < k; i += VB) ys[i] = y[i];
+__global__ void __launch_bounds__(VB) combine_kernel(double* __restrict__ x, const double* __restrict__ dinv,
+                                                     const double* __restrict__ V, int M1, int k, const KryDev* K,
+                                                     int64_t n) {
+  __shared__ double ys[MMAX];
+  for (int i = threadIdx.x; i < k; i += VB) ys[i] = K->y[i];
   __syncthreads();
-  for (int64_t j = blockIdx.x * (int64_t)VB + threadIdx.x; j < n; j += (int64_t)gridDim.x * VB) {
-    double s = 0.0;
-    for (int i = 0; i < k; ++i) s += ys[i] * V[(int64_t)i * ldv + j];
-    x[j] += dinv[j] * s;
+  const int64_t nch = (n + CH - 1) / CH;
+  for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
+    const int64_t j = c * CH + threadIdx.x;
+    if (j >= n) continue;
+    x[j] += dinv[j] * lin_comb_chunk(ys, V + c * (int64_t)M1 * CH + threadIdx.x, k);
   }
 }
 
+// --------------------------------------------------------- small device kernels
+// After pass 1: the column h[0..j], |w_old|^2 = h[j+1]; |w_new|^2 in nrm_new.
+__global__ void orth_decide(KryDev* K, int j) {
+  K->nrm_old = sqrt(K->h[j + 1]);
+  const double nn = sqrt(K->nrm_new);
+  K->reorth = (nn < K->nrm_old * 0.70710678118654752) ? 1 : 0;
+  K->nrm_fin = nn;
+}
+
+// After the (possible) second pass: fold h2 into h, rotate, update the estimate.
+__global__ void givens_kernel(KryDev* K, int j, int mm) {
+  if (K->reorth) {
+    for (int i = 0; i <= j; ++i) K->h[i] += K->h2[i];
+    K->nrm_fin = sqrt(K->nrm_new);
+  }
+  double* col = K->H;  // column j stored at H[i*mm + j]
+  for (int i = 0; i <= j; ++i) col[i * mm + j] = K->h[i];
+  const double hn = K->nrm_fin;
+  col[(j + 1) * mm + j] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double a = K->cs[i] * col[i * mm + j] + K->sn[i] * col[(i + 1) * mm + j];
+    col[(i + 1) * mm + j] = -K->sn[i] * col[i * mm + j] + K->cs[i] * col[(i + 1) * mm + j];
+    col[i * mm + j] = a;
+  }
+  const double den = hypot(col[j * mm + j], col[(j + 1) * mm + j]);
+  K->cs[j] = den > 0.0 ? col[j * mm + j] / den : 1.0;
+  K->sn[j] = den > 0.0 ? col[(j + 1) * mm + j] / den : 0.0;
+  col[j * mm + j] = den;
+  col[(j + 1) * mm + j] = 0.0;
+  K->g[j + 1] = -K->sn[j] * K->g[j];
+  K->g[j] = K->cs[j] * K->g[j];
+  K->est = fabs(K->g[j + 1]) / K->bnorm;
+  K->breakdown = (hn == 0.0 || den == 0.0 || !isfinite(hn)) ? 1 : 0;
+}
+
+// y = R^{-1} g for the first jend columns (back substitution).
+__global__ void lsq_kernel(KryDev* K, int jend, int mm) {
+  for (int i = jend - 1; i >= 0; --i) {
+    double s = K->g[i];
+    for (int k = i + 1; k < jend; ++k) s -= K->H[i * mm + k] * K->y[k];
+    const double d = K->H[i * mm + i];
+    K->y[i] = d != 0.0 ? s / d : 0.0;
+  }
+}
+
+// start of a cycle: g = (|r|, 0, ...)
+__global__ void cycle_start(KryDev* K, const double* rn2, int mm) {
+  const double b = sqrt(*rn2);
+  for (int i = 0; i <= mm; ++i) K->g[i] = 0.0;
+  K->g[0] = b;
+  K->nrm_fin = b;
+}
+
+// --------------------------------------------------------- contiguous vectors
+// part[cta] = partial of a . b over a contiguous range
+__global__ void __launch_bounds__(VB) dot_kernel(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
+                                                 double* part) {
+  const int G = gridDim.x;
+  const int64_t per = (n + G - 1) / G;
+  const int64_t lo = blockIdx.x * per, hi = min(n, lo + per);
+  double acc[1] = {0.0};
+  for (int64_t j = lo + threadIdx.x; j < hi; j += VB) acc[0] += a[j] * b[j];
+  block_reduce_store<1>(acc, 1, part + blockIdx.x, 1);
+}
 __global__ void axpby_kernel(double a, const double* __restrict__ x, double b, double* __restrict__ y, int64_t n) {
   for (int64_t j = blockIdx.x * (int64_t)VB + threadIdx.x; j < n; j += (int64_t)gridDim.x * VB) y[j] = a * x[j] + b * y[j];
 }
@@ -122,17 +269,70 @@ __global__ void fill_kernel(double* y, double v, int64_t n) {
 }
 
 // ---------------------------------------------------------------- host helpers
-static int dot_to_device(fsi_mesh* m, const double* V, int64_t ldv, int k, const double* w, int64_t n, double* out,
-                         int accumulate) {
+template <int R, bool SELF>
+static void launch_mdot(fsi_mesh* m, dim3 grid, const double* V, int M1, int i0, const double* w, int64_t n,
+                        const int* skip) {
+  mdot_kernel<R, SELF><<<grid, VB, 0, m->stream>>>(V, M1, i0, w, n, m->partials_dot, skip);
+}
+
+template <bool SELF>
+static void launch_mdot_rem(fsi_mesh* m, int rem, dim3 g1, const double* V, int M1, int i0, const double* w,
+                            int64_t n, const int* skip) {
+  switch (rem) {
+    case 0: launch_mdot<0, SELF>(m, g1, V, M1, i0, w, n, skip); break;
+    case 1: launch_mdot<1, SELF>(m, g1, V, M1, i0, w, n, skip); break;
+    case 2: launch_mdot<2, SELF>(m, g1, V, M1, i0, w, n, skip); break;
+    case 3: launch_mdot<3, SELF>(m, g1, V, M1, i0, w, n, skip); break;
+    case 4: launch_mdot<4, SELF>(m, g1, V, M1, i0, w, n, skip); break;
+    case 5: launch_mdot<5, SELF>(m, g1, V, M1, i0, w, n, skip); break;
+    case 6: launch_mdot<6, SELF>(m, g1, V, M1, i0, w, n, skip); break;
+    case 7: launch_mdot<7, SELF>(m, g1, V, M1, i0, w, n, skip); break;
+    case 8: launch_mdot<8, SELF>(m, g1, V, M1, i0, w, n, skip); break;
+    case 9: launch_mdot<9, SELF>(m, g1, V, M1, i0, w, n, skip); break;
+    case 10: launch_mdot<10, SELF>(m, g1, V, M1, i0, w, n, skip); break;
+    case 11: launch_mdot<11, SELF>(m, g1, V, M1, i0, w, n, skip); break;
+    case 12: launch_mdot<12, SELF>(m, g1, V, M1, i0, w, n, skip); break;
+    case 13: launch_mdot<13, SELF>(m, g1, V, M1, i0, w, n, skip); break;
+    case 14: launch_mdot<14, SELF>(m, g1, V, M1, i0, w, n, skip); break;
+    default: launch_mdot<15, SELF>(m, g1, V, M1, i0, w, n, skip); break;
+  }
+}
+
+// out[0..k) = V_i . w for the basis slots i < k; with self, out[k] = w . w.
+static int basis_dots(fsi_mesh* m, const double* V, int M1, int k, const double* w, int64_t n, double* out, bool self,
+                      const int* skip = nullptr) {
+  const int G = cgrid((n + CH - 1) / CH);
+  const int nfull = k / DCH, rem = k % DCH;
+  if (nfull)
+    FSI_LAUNCH(m, P_KRY_DOT, (launch_mdot<DCH, false>(m, dim3(G, nfull), V, M1, 0, w, n, skip)));
+  if (rem || self) {
+    if (self)
+      FSI_LAUNCH(m, P_KRY_DOT, (launch_mdot_rem<true>(m, rem, dim3(G, 1), V, M1, nfull * DCH, w, n, skip)));
+    else
+      FSI_LAUNCH(m, P_KRY_DOT, (launch_mdot_rem<false>(m, rem, dim3(G, 1), V, M1, nfull * DCH, w, n, skip)));
+  }
+  const int rows = k + (self ? 1 : 0);
+  FSI_LAUNCH(m, P_KRY_DOT, sum_partials<<<rows, VB, 0, m->stream>>>(m->partials_dot, G, out, skip));
+  return FSI_OK;
+}
+
+static int basis_update(fsi_mesh* m, double* w, const double* V, int M1, int k, const double* h, int64_t n,
+                        double* nrm_out, const int* skip = nullptr) {
+  const int G = cgrid((n + CH - 1) / CH);
+  FSI_LAUNCH(m, P_KRY_UPD, upd_kernel<<<G, VB, 0, m->stream>>>(w, V, M1, k, h, n, m->partials_dot, skip));
+  FSI_LAUNCH(m, P_KRY_UPD, sum_partials<<<1, VB, 0, m->stream>>>(m->partials_dot, G, nrm_out, skip));
+  return FSI_OK;
+}
+
+static int dot_dev(fsi_mesh* m, const double* a, const double* b, int64_t n, double* out) {
   const int G = vgrid(n);
-  dim3 grid(G, (k + DCH - 1) / DCH);
-  FSI_LAUNCH(m, P_KRYLOV, mdot_kernel<<<grid, VB, 0, m->stream>>>(V, ldv, k, w, n, m->partials_dot));
-  FSI_LAUNCH(m, P_KRYLOV, sum_partials<<<k, VB, 0, m->stream>>>(m->partials_dot, G, out, accumulate));
+  FSI_LAUNCH(m, P_KRY_DOT, dot_kernel<<<G, VB, 0, m->stream>>>(a, b, n, m->partials_dot));
+  FSI_LAUNCH(m, P_KRY_DOT, sum_partials<<<1, VB, 0, m->stream>>>(m->partials_dot, G, out, nullptr));
   return FSI_OK;
 }
 
 int vec_dot(fsi_mesh* m, const double* a, const double* b, int64_t n, double* out_host) {
-  int rc = dot_to_device(m, a, 0, 1, b, n, m->red, 0);
+  int rc = dot_dev(m, a, b, n, m->red);
   if (rc) return rc;
   FSI_CUDA(cudaMemcpyAsync(m->red_host, m->red, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
   FSI_CUDA(cudaStreamSynchronize(m->stream));
@@ -157,36 +357,46 @@ int vec_recip(fsi_mesh* m, const double* a, double* y, int64_t n) {
   return FSI_OK;
 }
 
+// basis: nch chunks x (mx + 1) slots x CH; wk: 7 contiguous work vectors
 static int ensure_krylov(fsi_mesh* m, int64_t n, int mm) {
-  if (m->kry_n >= n && m->kry_m >= mm) return FSI_OK;
+  if (m->kry_n >= n && m->kry_m >= mm && m->kry_dev) return FSI_OK;
   const int64_t nn = std::max(n, m->kry_n);
   const int mx = std::max(mm, m->kry_m);
   cudaFree(m->V);
   cudaFree(m->wk);
   cudaFree(m->dinv);
-  cudaFree(m->yvec);
   cudaFree(m->partials_dot);
-  m->V = m->wk = m->dinv = m->yvec = m->partials_dot = nullptr;
-  FSI_CUDA(cudaMalloc(&m->V, sizeof(double) * (size_t)(mx + 1) * nn));
-  FSI_CUDA(cudaMalloc(&m->wk, sizeof(double) * (size_t)6 * nn));
+  m->V = m->wk = m->dinv = m->partials_dot = nullptr;
+  const int64_t nch = (nn + CH - 1) / CH;
+  FSI_CUDA(cudaMalloc(&m->V, sizeof(double) * (size_t)nch * (mx + 1) * CH));
+  FSI_CUDA(cudaMalloc(&m->wk, sizeof(double) * (size_t)7 * nn));
   FSI_CUDA(cudaMalloc(&m->dinv, sizeof(double) * (size_t)nn));
-  FSI_CUDA(cudaMalloc(&m->yvec, sizeof(double) * 256));
-  FSI_CUDA(cudaMalloc(&m->partials_dot, sizeof(double) * (size_t)(mx + 1 + DCH) * 152 * 4));
+  FSI_CUDA(cudaMalloc(&m->partials_dot, sizeof(double) * (size_t)(MMAX + 2 + DCH) * 152 * 4));
+  if (!m->kry_dev) {
+    FSI_CUDA(cudaMalloc(&m->kry_dev, sizeof(KryDev)));
+    FSI_CUDA(cudaMallocHost(&m->kry_est, sizeof(double) * 2 * (MMAX + 1)));
+    m->kry_ev.resize(MMAX + 1);
+    for (auto& e : m->kry_ev) FSI_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
   m->kry_n = nn;
   m->kry_m = mx;
   return FSI_OK;
 }
 
 // One GMRES(m) solve A x = b from x = 0 with A = the block operator (flags) and the
-// right preconditioner diag(dinv).  Host-side Hessenberg least squares.
+// right preconditioner diag(dinv).
 static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double* x, int mm, double rtol,
-                      int max_iter, unsigned flags, int* iters, int* restarts, double* rel_out) {
+                      int max_iter, unsigned flags, int* iters, int* restarts, double* rel_out, int* stalled) {
   const int64_t n = blk.n;
+  const int M1 = m->kry_m + 1;
+  const int G = vgrid(n);
   double* V = m->V;
   double* r = m->wk;
   double* z = m->wk + n;
   double* t = m->wk + 2 * n;
-  double* dev = m->red;  // [0..127] h1, [128..255] h2, [256] nrm2
+  double* w = m->wk + 6 * n;
+  KryDev* K = static_cast<KryDev*>(m->kry_dev);
+  double* est = m->kry_est;  // pinned: [2*j] = estimate, [2*j+1] = breakdown flag
   FSI_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, m->stream));
   double bnorm2;
   int rc = vec_dot(m, b, b, n, &bnorm2);
@@ -194,74 +404,74 @@ static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double
   if (!std::isfinite(bnorm2)) return set_error(FSI_ENAN, "GMRES: right-hand side is not finite");
   const double bnorm = std::sqrt(bnorm2);
   *rel_out = 0.0;
+  *stalled = 0;
   if (bnorm == 0.0) return FSI_OK;
+  FSI_CUDA(cudaMemcpyAsync(&K->bnorm, &bnorm, sizeof(double), cudaMemcpyHostToDevice, m->stream));
   FSI_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, m->stream));
-  std::vector<double> H((mm + 1) * mm), cs(mm), sn(mm), g(mm + 1), y(mm);
-  auto Hij = [&](int i, int j) -> double& { return H[i * mm + j]; };
-  double rel = 1.0;
+  double rel = 1.0, cycle_rel = 1.0;
+  bool first_cycle = true;
   while (true) {
-    double beta2;
-    if ((rc = vec_dot(m, r, r, n, &beta2))) return rc;
+    // |r| on the device; the host needs it for the stopping and stall tests
+    if ((rc = dot_dev(m, r, r, n, m->red))) return rc;
+    FSI_CUDA(cudaMemcpyAsync(m->red_host, m->red, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    FSI_CUDA(cudaStreamSynchronize(m->stream));
+    const double beta2 = m->red_host[0];
     if (!std::isfinite(beta2)) return set_error(FSI_ENAN, "GMRES: residual is not finite");
-    const double beta = std::sqrt(beta2);
-    rel = beta / bnorm;
+    rel = std::sqrt(beta2) / bnorm;
     if (rel <= rtol || *iters >= max_iter) break;
-    if ((rc = vec_scale_copy(m, 1.0 / beta, r, V, n))) return rc;
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = beta;
+    if (!first_cycle && rel > 0.99 * cycle_rel) {
+      *stalled = 1;
+      break;
+    }
+    first_cycle = false;
+    cycle_rel = rel;
+    FSI_LAUNCH(m, P_KRY_SMALL, cycle_start<<<1, 1, 0, m->stream>>>(K, m->red, mm));
+    FSI_LAUNCH(m, P_KRYLOV, store_slot<<<G, VB, 0, m->stream>>>(V, M1, 0, r, m->red, K, n));
     int jend = 0;
-    for (int j = 0; j < mm; ++j) {
-      double* w = V + (int64_t)(j + 1) * n;
-      if ((rc = vec_mul(m, m->dinv, V + (int64_t)j * n, z, n))) return rc;
+    bool done = false;
+    const int jmax = std::min(mm, max_iter - *iters);
+    for (int j = 0; j < jmax && !done; ++j) {
+      FSI_LAUNCH(m, P_KRYLOV, precond_kernel<<<G, VB, 0, m->stream>>>(V, M1, j, m->dinv, z, n));
       if ((rc = op_jvp(m, blk, z, w, flags))) return rc;
-      // CGS2
-      if ((rc = dot_to_device(m, V, n, j + 1, w, n, dev, 0))) return rc;
-      FSI_LAUNCH(m, P_KRYLOV, upd_kernel<<<vgrid(n), VB, 0, m->stream>>>(w, V, n, j + 1, dev, n, nullptr));
-      if ((rc = dot_to_device(m, V, n, j + 1, w, n, dev + 128, 0))) return rc;
-      const int G = vgrid(n);
-      FSI_LAUNCH(m, P_KRYLOV, upd_kernel<<<G, VB, 0, m->stream>>>(w, V, n, j + 1, dev + 128, n, m->partials_dot));
-      FSI_LAUNCH(m, P_KRYLOV, sum_partials<<<1, VB, 0, m->stream>>>(m->partials_dot, G, dev + 256, 0));
-      FSI_CUDA(cudaMemcpyAsync(m->red_host, dev, sizeof(double) * 257, cudaMemcpyDeviceToHost, m->stream));
-      FSI_CUDA(cudaStreamSynchronize(m->stream));
-      const double* hh = m->red_host;
-      for (int i = 0; i <= j; ++i) Hij(i, j) = hh[i] + hh[128 + i];
-      const double hn2 = hh[256];
-      if (!std::isfinite(hn2)) return set_error(FSI_ENAN, "GMRES: Arnoldi vector is not finite");
-      const double hn = std::sqrt(hn2);
-      Hij(j + 1, j) = hn;
-      if (hn > 0.0) {
-        FSI_LAUNCH(m, P_KRYLOV, scale_by_norm<<<vgrid(n), VB, 0, m->stream>>>(w, dev + 256, n));
-      }
-      for (int i = 0; i < j; ++i) {
-        const double a = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
-        Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
-        Hij(i, j) = a;
-      }
-      const double den = std::hypot(Hij(j, j), Hij(j + 1, j));
-      cs[j] = den > 0.0 ? Hij(j, j) / den : 1.0;
-      sn[j] = den > 0.0 ? Hij(j + 1, j) / den : 0.0;
-      Hij(j, j) = den;
-      Hij(j + 1, j) = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
+      // pass 1: h = V^T w and |w|^2 (slot j+1 of h)
+      if ((rc = basis_dots(m, V, M1, j + 1, w, n, K->h, true))) return rc;
+      if ((rc = basis_update(m, w, V, M1, j + 1, K->h, n, &K->nrm_new))) return rc;
+      FSI_LAUNCH(m, P_KRY_SMALL, orth_decide<<<1, 1, 0, m->stream>>>(K, j));
+      // pass 2 only when the DGKS test asks for it
+      if ((rc = basis_dots(m, V, M1, j + 1, w, n, K->h2, false, &K->reorth))) return rc;
+      if ((rc = basis_update(m, w, V, M1, j + 1, K->h2, n, &K->nrm_new, &K->reorth))) return rc;
+      FSI_LAUNCH(m, P_KRY_SMALL, givens_kernel<<<1, 1, 0, m->stream>>>(K, j, mm));
+      FSI_LAUNCH(m, P_KRYLOV, store_slot<<<G, VB, 0, m->stream>>>(V, M1, j + 1, w, nullptr, K, n));
+      FSI_CUDA(cudaMemcpyAsync(est + 2 * j, &K->est, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+      FSI_CUDA(cudaMemcpyAsync(est + 2 * j + 1, &K->breakdown, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+      FSI_CUDA(cudaEventRecord(m->kry_ev[j], m->stream));
       ++*iters;
       jend = j + 1;
-      if (std::fabs(g[j + 1]) / bnorm <= rtol || *iters >= max_iter || hn == 0.0 || den == 0.0) break;
+      // look at the previous step while this one runs
+      if (j >= 1) {
+        FSI_CUDA(cudaEventSynchronize(m->kry_ev[j - 1]));
+        int bd = 0;
+        memcpy(&bd, est + 2 * (j - 1) + 1, sizeof(int));
+        const double e = est[2 * (j - 1)];
+        if (!std::isfinite(e)) return set_error(FSI_ENAN, "GMRES: Arnoldi vector is not finite");
+        if (e <= rtol || bd) {
+          jend = j;  // step j was computed for nothing
+          done = true;
+        }
+      }
     }
-    for (int i = jend - 1; i >= 0; --i) {
-      double s = g[i];
-      for (int k = i + 1; k < jend; ++k) s -= Hij(i, k) * y[k];
-      y[i] = Hij(i, i) != 0.0 ? s / Hij(i, i) : 0.0;
+    if (!done) {
+      FSI_CUDA(cudaEventSynchronize(m->kry_ev[jend - 1]));
+      if (!std::isfinite(est[2 * (jend - 1)])) return set_error(FSI_ENAN, "GMRES: Arnoldi vector is not finite");
     }
-    FSI_CUDA(cudaMemcpyAsync(m->yvec, y.data(), sizeof(double) * jend, cudaMemcpyHostToDevice, m->stream));
-    FSI_LAUNCH(m, P_KRYLOV, combine_kernel<<<vgrid(n), VB, 0, m->stream>>>(x, m->dinv, V, n, jend, m->yvec, n));
+    FSI_LAUNCH(m, P_KRY_SMALL, lsq_kernel<<<1, 1, 0, m->stream>>>(K, jend, mm));
+    FSI_LAUNCH(m, P_KRYLOV, combine_kernel<<<cgrid((n + CH - 1) / CH), VB, 0, m->stream>>>(x, m->dinv, V, M1, jend,
+                                                                                          K, n));
     // true residual r = b - A x
     if ((rc = op_jvp(m, blk, x, t, flags))) return rc;
     FSI_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, m->stream));
     if ((rc = vec_axpy(m, -1.0, t, r, n))) return rc;
     ++*restarts;
-    // make sure the host vector y is no longer needed before it is reused
-    FSI_CUDA(cudaStreamSynchronize(m->stream));
   }
   *rel_out = rel;
   return FSI_OK;
@@ -270,7 +480,7 @@ static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double
 int gmres_solve(fsi_mesh* m, const BlockInfo& blk, const double* rhs, double* x, const fsi_solve_opts& o,
                 fsi_solve_info* info) {
   const int mm = o.m;
-  if (mm < 1 || mm > 64) return set_error(FSI_EINVAL, "GMRES: restart length must be in 1..64");
+  if (mm < 1 || mm > MMAX) return set_error(FSI_EINVAL, "GMRES: restart length must be in 1..64");
   const int64_t n = blk.n;
   int rc = ensure_krylov(m, n, mm);
   if (rc) return rc;
@@ -285,7 +495,8 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& blk, const double* rhs, double* x,
   fsi_solve_info inf{};
   double rel = 0.0;
   if (o.precision == FSI_PREC_FP64) {
-    rc = gmres_core(m, blk, rhs, x, mm, o.rtol, o.max_iter, o.flags & ~FSI_FP32, &inf.iterations, &inf.restarts, &rel);
+    rc = gmres_core(m, blk, rhs, x, mm, o.rtol, o.max_iter, o.flags & ~FSI_FP32, &inf.iterations, &inf.restarts,
+                    &rel, &inf.stalled);
     if (rc) return rc;
   } else {
     // x = 0; r = rhs; repeat: solve A32 d = r; x += d; r = rhs - A64 x
@@ -295,13 +506,14 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& blk, const double* rhs, double* x,
     FSI_CUDA(cudaMemcpyAsync(r, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, m->stream));
     double b2;
     if ((rc = vec_dot(m, rhs, rhs, n, &b2))) return rc;
+    if (!std::isfinite(b2)) return set_error(FSI_ENAN, "IR: right-hand side is not finite");
     const double bnorm = std::sqrt(b2);
     rel = bnorm == 0.0 ? 0.0 : 1.0;
     for (int k = 0; k < std::max(1, o.ir_max) && rel > o.rtol; ++k) {
       double inner_rel;
-      // the inner solve needs its own right-hand side copy: gmres_core uses wk[0..3n)
-      rc = gmres_core(m, blk, r, d, mm, o.ir_inner_rtol, o.max_iter - inf.iterations,
-                      (o.flags | FSI_FP32), &inf.iterations, &inf.restarts, &inner_rel);
+      int inner_stalled;
+      rc = gmres_core(m, blk, r, d, mm, o.ir_inner_rtol, o.max_iter - inf.iterations, (o.flags | FSI_FP32),
+                      &inf.iterations, &inf.restarts, &inner_rel, &inner_stalled);
       if (rc) return rc;
       if ((rc = vec_axpy(m, 1.0, d, x, n))) return rc;
       if ((rc = op_jvp(m, blk, x, d, o.flags & ~FSI_FP32))) return rc;
@@ -310,9 +522,14 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& blk, const double* rhs, double* x,
       double r2;
       if ((rc = vec_dot(m, r, r, n, &r2))) return rc;
       if (!std::isfinite(r2)) return set_error(FSI_ENAN, "IR: residual is not finite");
+      const double prev = rel;
       rel = bnorm > 0.0 ? std::sqrt(r2) / bnorm : 0.0;
       inf.refinements = k + 1;
       if (inf.iterations >= o.max_iter) break;
+      if (rel > o.rtol && rel > 0.9 * prev) {
+        inf.stalled = 1;
+        break;
+      }
     }
   }
   inf.rel_res = rel;

@@ -31,6 +31,14 @@ constexpr int MAXP = 16;   // phases
 constexpr int MAXS = 16;   // solids
 constexpr int MAXF = 40;   // staged fields per kernel
 
+// Resident 256-thread CTAs per SM the register budget is cut for (one: a cap of
+// 128 registers spills and measured slower for the float32 NS product).
+#ifndef FSI_MINB_F32
+#define FSI_MINB_F32 1
+#endif
+template <typename T>
+struct MinBlocks { static constexpr int value = sizeof(T) == 4 ? FSI_MINB_F32 : 1; };
+
 struct Phys {
   double dt, alpha, alpha_m, vs, c_mass, c_el, c_i, eps, eta;
   double Gd[3], GG, trG;
@@ -40,17 +48,19 @@ struct Phys {
   int solid_phase[MAXS];
 };
 
-// Nodal field sources for staging: exactly one of d/f is non-null per field.
+// Nodal field sources for staging: a float64 kernel reads d[], a float32 kernel f[]
+// (every staged field of a kernel has the kernel's compute type).
 struct Fields {
   const double* d[MAXF];
   const float* f[MAXF];
 };
 
 template <typename T>
-__device__ __forceinline__ T ld_field(const Fields& F, int i, int64_t n) {
-  const float* pf = F.f[i];
-  return pf ? T(pf[n]) : T(F.d[i][n]);
-}
+__device__ __forceinline__ const T* field_ptr(const Fields& F, int i);
+template <>
+__device__ __forceinline__ const double* field_ptr<double>(const Fields& F, int i) { return F.d[i]; }
+template <>
+__device__ __forceinline__ const float* field_ptr<float>(const Fields& F, int i) { return F.f[i]; }
 
 // symmetric storage order [11, 22, 33, 12, 23, 13]
 __host__ __device__ constexpr int sym_k(int c) { return c < 3 ? c : (c == 3 ? 0 : (c == 4 ? 1 : 0)); }
@@ -76,6 +86,7 @@ template <typename TT, int MODE>  // MODE 0: residual, 1: JVP, 2: diagonal
 struct NSOp {
   using T = TT;
   static constexpr int NC = 4;
+  static constexpr int MINB = MinBlocks<TT>::value;
   Fields F;
   int nf;           // staged field count
   int s0, s1;       // solids in this pass
@@ -85,7 +96,7 @@ struct NSOp {
   double rh[3], W;
   OutDesc out;
 
-  __device__ __forceinline__ T field(int f, int64_t n) const { return ld_field<T>(F, f, n); }
+  __device__ __forceinline__ const T* fptr(int f) const { return field_ptr<T>(F, f); }
   using Red = NoRed;
   __device__ __forceinline__ void begin_cta(Red&) const {}
   __device__ __forceinline__ void end_cta(Red&) const {}
@@ -324,6 +335,7 @@ template <typename TT, int MODE>
 struct ACOp {
   using T = TT;
   static constexpr int NC = 1;
+  static constexpr int MINB = MinBlocks<TT>::value;
   Fields F;
   int nf;
   Phys P;
@@ -332,7 +344,7 @@ struct ACOp {
   OutDesc out;
   int64_t nn_;
 
-  __device__ __forceinline__ T field(int f, int64_t n) const { return ld_field<T>(F, f, n); }
+  __device__ __forceinline__ const T* fptr(int f) const { return field_ptr<T>(F, f); }
   using Red = NoRed;
   __device__ __forceinline__ void begin_cta(Red&) const {}
   __device__ __forceinline__ void end_cta(Red&) const {}
@@ -406,6 +418,7 @@ template <typename TT, int MODE>
 struct BOp {
   using T = TT;
   static constexpr int NC = 6;
+  static constexpr int MINB = MinBlocks<TT>::value;
   Fields F;
   int nf;
   Phys P;
@@ -413,7 +426,7 @@ struct BOp {
   OutDesc out;
   int64_t nn_;
 
-  __device__ __forceinline__ T field(int f, int64_t n) const { return ld_field<T>(F, f, n); }
+  __device__ __forceinline__ const T* fptr(int f) const { return field_ptr<T>(F, f); }
   using Red = NoRed;
   __device__ __forceinline__ void begin_cta(Red&) const {}
   __device__ __forceinline__ void end_cta(Red&) const {}
@@ -503,6 +516,7 @@ struct BOp {
 struct CoefOp {
   using T = double;
   static constexpr int NC = 2;
+  static constexpr int MINB = 1;
   Fields F;
   int nf;
   double rh[3], W;
@@ -511,7 +525,7 @@ struct CoefOp {
   const double* phi_node;  // nodal phi^{n+alpha}
   struct Red { double sv2, nband, sFp, ssF; };
 
-  __device__ __forceinline__ double field(int f, int64_t n) const { return ld_field<double>(F, f, n); }
+  __device__ __forceinline__ const double* fptr(int f) const { return F.d[f]; }
   __device__ __forceinline__ void begin_cta(Red& r) const { r.sv2 = r.nband = r.sFp = r.ssF = 0.0; }
 
   __device__ void element(const Corners<double>& cr, const ElemCtx& ec, double (&c)[NC][8], Red& red) const {

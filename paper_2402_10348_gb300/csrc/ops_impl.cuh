@@ -61,11 +61,19 @@ constexpr int op_class(int kind) {
 
 constexpr size_t SMEM_LIMIT = 232448;
 
+// The increment of a product: float64 kernels read dx itself, float32 kernels the
+// float copy the caller made (m->dx32, same layout).
+template <typename T>
+inline void put_dx(Fields& F, int i, const fsi_mesh* m, const double* dx, int64_t off) {
+  if constexpr (sizeof(T) == 4) put<float>(F, i, m->dx32 + off);
+  else put<double>(F, i, dx + off);
+}
+
 template <typename T>
 inline int solids_per_pass(int nf_fixed) {
-  // 2 planes x (nf_fixed + 7 s) fields + 4 x 8 x 256 contributions
-  const size_t fixed = sizeof(T) * (size_t)(2 * nf_fixed * PP + 4 * 8 * NTHREADS);
-  const size_t per = sizeof(T) * (size_t)(2 * 7 * PP);
+  // 3 ring slots x (nf_fixed + 7 s) fields + 4 x 8 x 256 contributions
+  const size_t fixed = sizeof(T) * (size_t)(3 * nf_fixed * PP + 4 * 8 * NTHREADS);
+  const size_t per = sizeof(T) * (size_t)(3 * 7 * PP);
   if (fixed >= SMEM_LIMIT) return 0;
   return (int)((SMEM_LIMIT - fixed) / per);
 }
@@ -81,7 +89,7 @@ int ns_pass(fsi_mesh* m, const double* dx, double* y, unsigned flags, int s0, in
   if ((MODE == 1 ? 4 : 0) + 9 + 7 * (s1 - s0) > MAXF) return set_error(FSI_EINVAL, "NS operator: too many staged fields");
   int f = 0;
   if (MODE == 1) {
-    for (int k = 0; k < 4; ++k) { op.F.d[f] = dx + k * nn; op.F.f[f] = nullptr; ++f; }
+    for (int k = 0; k < 4; ++k) put_dx<T>(op.F, f++, m, dx, k * nn);
   }
   for (int k = 0; k < 3; ++k) put<T>(op.F, f++, xa + k * nn);   // v
   put<T>(op.F, f++, xa + 3 * nn);                                 // p^{n+1}
@@ -142,7 +150,7 @@ int ac_run(fsi_mesh* m, int i, const double* dx, double* y) {
   const T* xd = Staged<T>::xd(m);
   const int64_t nn = m->nn;
   int f = 0;
-  if (MODE == 1) { op.F.d[f] = dx; op.F.f[f] = nullptr; ++f; }
+  if (MODE == 1) put_dx<T>(op.F, f++, m, dx, 0);
   for (int k = 0; k < 3; ++k) put<T>(op.F, f++, xa + k * nn);
   put<T>(op.F, f++, xa + (4 + i) * nn);
   if (MODE == 0) put<T>(op.F, f++, xd + (4 + i) * nn);
@@ -174,7 +182,7 @@ int b_run(fsi_mesh* m, int s, const double* dx, double* y) {
   const int c0 = 4 + m->N + 6 * s;
   int f = 0;
   if (MODE == 1)
-    for (int c = 0; c < 6; ++c) { op.F.d[f] = dx + c * nn; op.F.f[f] = nullptr; ++f; }
+    for (int c = 0; c < 6; ++c) put_dx<T>(op.F, f++, m, dx, c * nn);
   for (int k = 0; k < 3; ++k) put<T>(op.F, f++, xa + k * nn);
   put<T>(op.F, f++, mat + (2 + s) * nn);
   if (MODE == 0) {

@@ -152,14 +152,31 @@ struct ElemCtx {
   bool owned;  // this CTA is the one that counts the element in reductions
 };
 
+// cp.async of one element (4 or 8 bytes) global -> shared; src_bytes = 0 writes zeros.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool valid) {
+  const unsigned saddr = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  const int sz = valid ? (int)sizeof(T) : 0;
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(saddr), "l"(src), "r"(sz) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(saddr), "l"(src), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Node planes live in a ring of three shared-memory slots: while layer ez is
+// computed from the planes ez and ez+1, the copies of plane ez+2 are in flight.
+__host__ __device__ constexpr int plane_slot(int kz) { return ((kz % 3) + 3) % 3; }
+
 template <class Op>
-__global__ void __launch_bounds__(NTHREADS, 1) tile_kernel(const __grid_constant__ Op op, const Geom g) {
+__global__ void __launch_bounds__(NTHREADS, Op::MINB) tile_kernel(const __grid_constant__ Op op, const Geom g) {
   using T = typename Op::T;
   constexpr int NC = Op::NC;
   const int NS = op.nf;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* planes = reinterpret_cast<T*>(smem_raw);       // [2][NS][PP]
-  T* contrib = planes + 2 * NS * PP;                // [NC*8][NTHREADS]
+  T* planes = reinterpret_cast<T*>(smem_raw);       // [3][NS][PP]
+  T* contrib = planes + 3 * NS * PP;                // [NC*8][NTHREADS]
 
   const int t = threadIdx.x;
   const int tx = t % TX, ty = t / TX;
@@ -178,23 +195,31 @@ __global__ void __launch_bounds__(NTHREADS, 1) tile_kernel(const __grid_constant
   typename Op::Red red;
   op.begin_cta(red);
 
-  auto load_plane = [&](int kz, int slot) {
-    T* dst = planes + slot * NS * PP;
+  // issue the copies of node plane kz (all staged fields) into its ring slot
+  auto issue_plane = [&](int kz) {
+    T* dst = planes + plane_slot(kz) * NS * PP;
     for (int idx = t; idx < PP; idx += NTHREADS) {
       const int lx = idx % PX, ly = idx / PX;
       const int gi = i0 - 1 + lx, gj = j0 - 1 + ly;
       const bool ok = kz >= 0 && kz <= g.nz && gi >= 0 && gi <= g.nx && gj >= 0 && gj <= g.ny;
       const int64_t n = ok ? (int64_t)gi + (int64_t)(g.nx + 1) * ((int64_t)gj + (int64_t)(g.ny + 1) * kz) : 0;
-#pragma unroll
-      for (int f = 0; f < NS; ++f) dst[f * PP + idx] = ok ? op.field(f, n) : T(0);
+      for (int f = 0; f < NS; ++f) {
+        const T* src = op.fptr(f);
+        cp_async_elem(dst + f * PP + idx, src + n, ok);
+      }
     }
   };
 
   const int ez_begin = k0 - 1, ez_end = k0 + g.zc - 1;  // inclusive
-  load_plane(ez_begin, ez_begin & 1);
+  issue_plane(ez_begin);
+  cp_async_commit();
+  issue_plane(ez_begin + 1);
+  cp_async_commit();
   for (int ez = ez_begin; ez <= ez_end; ++ez) {
-    load_plane(ez + 1, (ez + 1) & 1);
-    __syncthreads();
+    if (ez + 2 <= ez_end + 1) issue_plane(ez + 2);
+    cp_async_commit();  // possibly empty: keeps one group per iteration
+    cp_async_wait_1();  // this thread's copies of planes ez, ez+1 have landed
+    __syncthreads();    // ... and everybody's
     {
       T c[NC][8];
 #pragma unroll
@@ -203,8 +228,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tile_kernel(const __grid_constant
         for (int a = 0; a < 8; ++a) c[q][a] = T(0);
       if (exy_ok && ez >= 0 && ez < g.nz) {
         Corners<T> cr;
-        cr.lo = planes + (ez & 1) * NS * PP;
-        cr.hi = planes + ((ez + 1) & 1) * NS * PP;
+        cr.lo = planes + plane_slot(ez) * NS * PP;
+        cr.hi = planes + plane_slot(ez + 1) * NS * PP;
         cr.off = ty * PX + tx;
         ElemCtx ec{ex, ey, ez, exy_owned && ez >= k0};
         op.element(cr, ec, c, red);
@@ -214,6 +239,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tile_kernel(const __grid_constant
 #pragma unroll
         for (int a = 0; a < 8; ++a) contrib[(q * 8 + a) * NTHREADS + t] = c[q][a];
     }
+    // every read of plane ez is done after this barrier: the next iteration may
+    // refill its slot with plane ez+3
     __syncthreads();
     if (node_thread) {
       const int e00 = ty * TX + tx;  // element (tx, ty) has this node as corner (1,1)
@@ -239,7 +266,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tile_kernel(const __grid_constant
 #pragma unroll
       for (int q = 0; q < NC; ++q) carry[q] = upper[q];
     }
-    __syncthreads();
+    // the contributions are rewritten only after the next iteration's first barrier
   }
   op.end_cta(red);
 }
@@ -247,7 +274,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tile_kernel(const __grid_constant
 template <class Op>
 inline size_t tile_smem_bytes(int nf) {
   using T = typename Op::T;
-  return sizeof(T) * (size_t)(2 * nf * PP + Op::NC * 8 * NTHREADS);
+  return sizeof(T) * (size_t)(3 * nf * PP + Op::NC * 8 * NTHREADS);
 }
 
 struct NoRed {};

@@ -72,7 +72,7 @@ class fsi_solve_opts(C.Structure):
 
 class fsi_solve_info(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("restarts", C.c_int32), ("refinements", C.c_int32),
-                ("applies", C.c_int32), ("rel_res", C.c_double)]
+                ("applies", C.c_int32), ("rel_res", C.c_double), ("stalled", C.c_int32), ("pad", C.c_int32)]
 
 
 class fsi_step_opts(C.Structure):
@@ -82,7 +82,7 @@ class fsi_step_opts(C.Structure):
 
 class fsi_step_info(C.Structure):
     _fields_ = [("nl_iters", C.c_int32), ("gmres_iters_ns", C.c_int32), ("gmres_iters_ac", C.c_int32),
-                ("gmres_iters_b", C.c_int32), ("applies", C.c_int32), ("pad", C.c_int32),
+                ("gmres_iters_b", C.c_int32), ("applies", C.c_int32), ("stalled_solves", C.c_int32),
                 ("dof_applied", C.c_int64), ("max_ratio", C.c_double), ("worst_rel_res", C.c_double)]
 
 
@@ -99,7 +99,7 @@ class fsi_profile_entry(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("ms", C.c_double)]
 
 
-FSI_PROF_CLASSES = 16
+FSI_PROF_CLASSES = 20
 
 EXPORTS = ["fsi_create_mesh", "fsi_destroy_mesh", "fsi_set_stream", "fsi_mesh_info", "fsi_residual",
            "fsi_jvp", "fsi_diag", "fsi_update_ac_coeffs", "fsi_set_ac_coeffs", "fsi_fix_gamma",
