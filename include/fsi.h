@@ -273,6 +273,9 @@ typedef struct {
   char name[24];
   int64_t launches;
   double ms;            /* summed device time between the event pair (0 if off) */
+  double bytes;         /* summed algorithmic DRAM bytes of the launches (vector
+                           kernels: the vectors the algorithm reads and writes
+                           once; 0 for classes that do not declare them)          */
 } fsi_profile_entry;
 int fsi_profile(fsi_mesh* mesh, int32_t enable);
 int fsi_profile_read(fsi_mesh* mesh, fsi_profile_entry* out /* [FSI_PROF_CLASSES] */, int32_t* n_out);

@@ -355,7 +355,7 @@ int fsi_profile(fsi_mesh* m, int32_t enable) {
     }
     int rc = prof_harvest(m);
     if (rc) return rc;
-    for (int c = 0; c < P_NCLS; ++c) { p.launches[c] = 0; p.ms[c] = 0.0; }
+    for (int c = 0; c < P_NCLS; ++c) { p.launches[c] = 0; p.ms[c] = 0.0; p.bytes[c] = 0.0; }
     p.on = true;
   } else {
     int rc = prof_harvest(m);
@@ -375,6 +375,7 @@ int fsi_profile_read(fsi_mesh* m, fsi_profile_entry* out, int32_t* n_out) {
     strncpy(out[c].name, kProfNames[c], sizeof(out[c].name) - 1);
     out[c].launches = m->prof.launches[c];
     out[c].ms = m->prof.ms[c];
+    out[c].bytes = m->prof.bytes[c];
   }
   if (n_out) *n_out = P_NCLS;
   return FSI_OK;

@@ -20,6 +20,7 @@ struct Profiler {
   bool on = false;
   int64_t launches[P_NCLS] = {};
   double ms[P_NCLS] = {};
+  double bytes[P_NCLS] = {};   // algorithmic HBM bytes declared by the launch sites
   std::vector<cudaEvent_t> ev;  // pool of event pairs
   std::vector<int> cls;         // class of each recorded pair
   int used = 0;                 // pairs recorded since the last harvest
@@ -127,6 +128,7 @@ void tile_grid(const fsi_mesh* m, dim3* grid);
 // profiler: bracket every launch with prof_begin / prof_end (api.cu)
 int prof_begin(fsi_mesh* m, int cls);
 int prof_end(fsi_mesh* m, int cls);
+inline void prof_bytes(fsi_mesh* m, int cls, double b) { m->prof.bytes[cls] += b; }
 int prof_harvest(fsi_mesh* m);
 #define FSI_LAUNCH(m, cls, ...)                      \
   do {                                               \

@@ -41,7 +41,9 @@ constexpr int MMAX = 64;  // largest restart length
 static int vgrid(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((n + VB * 4 - 1) / (VB * 4), 152 * 4));
 }
-static int cgrid(int64_t nch) { return (int)std::max<int64_t>(1, std::min<int64_t>(nch, 152 * 4)); }
+// two CTAs per SM: each streams enough chunks to amortise its end-of-kernel
+// reduction of up to 16 sums (the reduction dominated at four CTAs per SM)
+static int cgrid(int64_t nch) { return (int)std::max<int64_t>(1, std::min<int64_t>(nch, 152 * 2)); }
 
 // device-resident Arnoldi/Givens state (inside fsi_mesh::kry_dev)
 struct KryDev {
@@ -374,7 +376,7 @@ static int ensure_krylov(fsi_mesh* m, int64_t n, int mm) {
   FSI_CUDA(cudaMalloc(&m->partials_dot, sizeof(double) * (size_t)(MMAX + 2 + DCH) * 152 * 4));
   if (!m->kry_dev) {
     FSI_CUDA(cudaMalloc(&m->kry_dev, sizeof(KryDev)));
-    FSI_CUDA(cudaMallocHost(&m->kry_est, sizeof(double) * 2 * (MMAX + 1)));
+    FSI_CUDA(cudaMallocHost(&m->kry_est, sizeof(double) * 3 * (MMAX + 1)));
     m->kry_ev.resize(MMAX + 1);
     for (auto& e : m->kry_ev) FSI_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
@@ -396,7 +398,7 @@ static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double
   double* t = m->wk + 2 * n;
   double* w = m->wk + 6 * n;
   KryDev* K = static_cast<KryDev*>(m->kry_dev);
-  double* est = m->kry_est;  // pinned: [2*j] = estimate, [2*j+1] = breakdown flag
+  double* est = m->kry_est;  // pinned: [3j] estimate, [3j+1] breakdown flag, [3j+2] second pass ran
   FSI_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, m->stream));
   double bnorm2;
   int rc = vec_dot(m, b, b, n, &bnorm2);
@@ -427,32 +429,37 @@ static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double
     cycle_rel = rel;
     FSI_LAUNCH(m, P_KRY_SMALL, cycle_start<<<1, 1, 0, m->stream>>>(K, m->red, mm));
     FSI_LAUNCH(m, P_KRYLOV, store_slot<<<G, VB, 0, m->stream>>>(V, M1, 0, r, m->red, K, n));
-    int jend = 0;
+    int jend = 0, enq = 0;
     bool done = false;
     const int jmax = std::min(mm, max_iter - *iters);
+    const double vb = 8.0 * (double)n;  // bytes of one vector
     for (int j = 0; j < jmax && !done; ++j) {
       FSI_LAUNCH(m, P_KRYLOV, precond_kernel<<<G, VB, 0, m->stream>>>(V, M1, j, m->dinv, z, n));
       if ((rc = op_jvp(m, blk, z, w, flags))) return rc;
       // pass 1: h = V^T w and |w|^2 (slot j+1 of h)
       if ((rc = basis_dots(m, V, M1, j + 1, w, n, K->h, true))) return rc;
       if ((rc = basis_update(m, w, V, M1, j + 1, K->h, n, &K->nrm_new))) return rc;
+      prof_bytes(m, P_KRY_DOT, (j + 2) * vb);   // j+1 basis vectors and w read once
+      prof_bytes(m, P_KRY_UPD, (j + 3) * vb);   // j+1 basis vectors and w read, w written
       FSI_LAUNCH(m, P_KRY_SMALL, orth_decide<<<1, 1, 0, m->stream>>>(K, j));
       // pass 2 only when the DGKS test asks for it
       if ((rc = basis_dots(m, V, M1, j + 1, w, n, K->h2, false, &K->reorth))) return rc;
       if ((rc = basis_update(m, w, V, M1, j + 1, K->h2, n, &K->nrm_new, &K->reorth))) return rc;
       FSI_LAUNCH(m, P_KRY_SMALL, givens_kernel<<<1, 1, 0, m->stream>>>(K, j, mm));
       FSI_LAUNCH(m, P_KRYLOV, store_slot<<<G, VB, 0, m->stream>>>(V, M1, j + 1, w, nullptr, K, n));
-      FSI_CUDA(cudaMemcpyAsync(est + 2 * j, &K->est, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
-      FSI_CUDA(cudaMemcpyAsync(est + 2 * j + 1, &K->breakdown, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+      FSI_CUDA(cudaMemcpyAsync(est + 3 * j, &K->est, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+      FSI_CUDA(cudaMemcpyAsync(est + 3 * j + 1, &K->breakdown, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+      FSI_CUDA(cudaMemcpyAsync(est + 3 * j + 2, &K->reorth, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
       FSI_CUDA(cudaEventRecord(m->kry_ev[j], m->stream));
       ++*iters;
       jend = j + 1;
+      enq = j + 1;
       // look at the previous step while this one runs
       if (j >= 1) {
         FSI_CUDA(cudaEventSynchronize(m->kry_ev[j - 1]));
         int bd = 0;
-        memcpy(&bd, est + 2 * (j - 1) + 1, sizeof(int));
-        const double e = est[2 * (j - 1)];
+        memcpy(&bd, est + 3 * (j - 1) + 1, sizeof(int));
+        const double e = est[3 * (j - 1)];
         if (!std::isfinite(e)) return set_error(FSI_ENAN, "GMRES: Arnoldi vector is not finite");
         if (e <= rtol || bd) {
           jend = j;  // step j was computed for nothing
@@ -460,9 +467,15 @@ static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double
         }
       }
     }
-    if (!done) {
-      FSI_CUDA(cudaEventSynchronize(m->kry_ev[jend - 1]));
-      if (!std::isfinite(est[2 * (jend - 1)])) return set_error(FSI_ENAN, "GMRES: Arnoldi vector is not finite");
+    FSI_CUDA(cudaEventSynchronize(m->kry_ev[enq - 1]));
+    if (!done && !std::isfinite(est[3 * (jend - 1)])) return set_error(FSI_ENAN, "GMRES: Arnoldi vector is not finite");
+    for (int j = 0; j < enq; ++j) {  // the second passes that ran
+      int ro = 0;
+      memcpy(&ro, est + 3 * j + 2, sizeof(int));
+      if (ro) {
+        prof_bytes(m, P_KRY_DOT, (j + 2) * vb);
+        prof_bytes(m, P_KRY_UPD, (j + 3) * vb);
+      }
     }
     FSI_LAUNCH(m, P_KRY_SMALL, lsq_kernel<<<1, 1, 0, m->stream>>>(K, jend, mm));
     FSI_LAUNCH(m, P_KRYLOV, combine_kernel<<<cgrid((n + CH - 1) / CH), VB, 0, m->stream>>>(x, m->dinv, V, M1, jend,

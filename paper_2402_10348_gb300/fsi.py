@@ -96,7 +96,7 @@ class fsi_phase_rule(C.Structure):
 
 
 class fsi_profile_entry(C.Structure):
-    _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("ms", C.c_double)]
+    _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("ms", C.c_double), ("bytes", C.c_double)]
 
 
 FSI_PROF_CLASSES = 20
@@ -299,4 +299,4 @@ def fsi_profile_read(mesh: Mesh) -> dict:
     out = (fsi_profile_entry * FSI_PROF_CLASSES)()
     n = C.c_int32()
     _check(lib().fsi_profile_read(mesh.handle, out, C.byref(n)))
-    return {out[i].name.decode(): (out[i].launches, out[i].ms) for i in range(n.value)}
+    return {out[i].name.decode(): (out[i].launches, out[i].ms, out[i].bytes) for i in range(n.value)}
