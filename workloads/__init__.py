@@ -358,3 +358,18 @@ def random_state(desc: MeshDesc, seed: int, amp_v: float = 1.0, amp_B: float = 0
 
 def random_vector(n: int, seed: int) -> np.ndarray:
     return np.random.default_rng(seed).normal(size=n)
+
+
+def he_normal_weights(fan: list, seed: int, last_scale: float = 0.1) -> np.ndarray:
+    """Seeded initial weights for a stack of 3x3x3 convolutions.
+
+    `fan` lists (out channels, in channels) per convolution in storage order; each
+    convolution gets co*ci*27 normal draws with std sqrt(2 / (27 ci)) (He et al. 2015),
+    the last one scaled by `last_scale` so that an untrained network starts close to
+    zero output."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for k, (co, ci) in enumerate(fan):
+        std = math.sqrt(2.0 / (27 * ci)) * (last_scale if k == len(fan) - 1 else 1.0)
+        parts.append(rng.normal(scale=std, size=co * ci * 27))
+    return np.concatenate(parts)
