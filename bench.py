@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--precision", default="fp32ir", choices=["fp32ir", "fp64"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner arm")
+    p.add_argument("--train-steps", type=int, default=3000)
     p.add_argument("--case", default="step", choices=["step", "solve"],
                    help="solve: only a fixed 40-iteration float32-IR NS GMRES solve at 64^3 (a short, "
                         "repeatable launch sequence for ncu captures); prints no JSON")
@@ -265,12 +267,23 @@ def run_gpu(args):
 
     x, xn, xdn = initial_state(fsi, mesh, wl, torch, dev)
 
-    def step():
-        return fsi.fsi_step(mesh, x, xn, xdn, k_max=wl.k_max, nl_tol=5e-4, solve=solve)
+    def step(opts=solve):
+        return fsi.fsi_step(mesh, x, xn, xdn, k_max=wl.k_max, nl_tol=5e-4, solve=opts)
 
+    # the learned preconditioner of the NS block: training pairs are harvested from the
+    # (untimed) Jacobi warm-up steps
+    pc = None
+    if not args.no_learned:
+        from workloads import he_normal_weights
+        pc = fsi.fsi_pc_create(mesh, n_pairs_cap=512, linear=True, modulate=True)
+        fsi.fsi_pc_set_weights(pc, he_normal_weights(pc.fan, 3))
+        fsi.fsi_set_pc(mesh, pc)
+        harvest = fsi.solve_opts(m=64, rtol=1e-8, max_iter=3000, precision=prec, ir_inner_rtol=1e-3, ir_max=30)
+        harvest.flags |= fsi.FSI_HARVEST
     for _ in range(args.warmup):
-        step()
+        step(harvest if pc is not None else solve)
     torch.cuda.synchronize()
+    snapshot = (x.clone(), xn.clone(), xdn.clone())
     clocks = Clocks(local)
     clocks.start()
     if world > 1:
@@ -309,6 +322,12 @@ def run_gpu(args):
         oname, ov = max(ops.items(), key=lambda kv: kv[1][1])
         roof_op = roofline(oname, *ov, d, pk)
 
+    learned = None
+    if pc is not None:
+        learned = run_learned_arm(fsi, torch, mesh, pc, solve, step, (x, xn, xdn), snapshot, args, stream)
+        learned["jacobi_s_per_timestep"] = round(ms / args.steps / 1e3, 5)
+        learned["jacobi_ns_iters"] = [i.gmres_iters_ns for i in infos]
+
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(fsi, mesh, wl, torch, dev, stream, step_fn=lambda xs: fsi.fsi_step(
@@ -340,6 +359,7 @@ def run_gpu(args):
         "roofline_operator": roof_op,
         "clocks": clk,
         "e2e": e2e,
+        "learned_pc": learned,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
@@ -347,6 +367,52 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_learned_arm(fsi, torch, mesh, pc, solve, step, state, snapshot, args, stream):
+    """Trains the network on the harvested pairs (timed apart), then replays the timed
+    steps from the same initial state with flexible GMRES + the network on the NS block
+    (Jacobi on the other blocks, and as the fallback); s/timestep to rel-res 1e-8."""
+    import numpy as np
+    x, xn, xdn = state
+    npairs = fsi.fsi_pc_pairs(pc)
+    fsi.fsi_pc_fit_norm(pc)
+    rng = np.random.default_rng(0)
+    order = rng.integers(0, npairs, size=args.train_steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = fsi.fsi_pc_train(pc, order, 2e-4)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    opts = fsi.fsi_solve_opts.from_buffer_copy(solve)
+    opts.precond = fsi.FSI_PC_LEARNED
+
+    def restore():
+        for dst, src in zip((x, xn, xdn), snapshot):
+            dst.copy_(src)
+
+    restore()
+    step(opts)  # first use allocates the flexible-GMRES directions
+    restore()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = [step(opts) for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {
+        "network": "U-Net, 4 levels, 16 channels, 3x3x3 convolutions (tcgen05, bf16 x bf16 -> f32), "
+                   "linear (no activation), inputs modulated by the solid indicator",
+        "pairs": npairs, "train_steps": args.train_steps, "train_s": round(train_s, 3),
+        "train_ms_per_step": round(1e3 * train_s / max(1, args.train_steps), 3),
+        "relative_loss_first_last": [round(float(losses[:50].mean()), 4), round(float(losses[-200:].mean()), 4)],
+        "s_per_timestep": round(ms / args.steps / 1e3, 5),
+        "ns_iters": [i.gmres_iters_ns for i in infos],
+        "worst_rel_res": max(i.worst_rel_res for i in infos),
+        "stalled_solves": [i.stalled_solves for i in infos],
+        "fallback_solves": [i.fallback_solves for i in infos],
+    }
 
 
 def run_e2e(fsi, mesh, wl, torch, dev, stream, step_fn, steps, world):

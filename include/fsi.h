@@ -146,6 +146,15 @@ int fsi_fix_gamma(fsi_mesh* mesh, int32_t phase, double gamma);
 
 #define FSI_PC_NONE 0
 #define FSI_PC_JACOBI 1
+#define FSI_PC_LEARNED 2  /* NS block: the attached network in flexible GMRES (fsi_set_pc);
+                             other blocks fall back to FSI_PC_JACOBI                */
+
+/* solve flag: record training pairs of the NS block into the attached learned
+ * preconditioner (fsi_set_pc): for every refinement checkpoint x_k (FP32_IR; x_0 = 0)
+ * the pair (r_k - r*, x* - x_k) with r_k = rhs - A x_k and x* the final iterate, and
+ * from Jacobi-preconditioned Arnoldi steps j = 4, 12, 20, ... (at most 8 per inner
+ * solve) the pair (A z_j, z_j), z_j = D^{-1} v_j, with the operator the step used */
+#define FSI_HARVEST 0x10u
 
 #define FSI_PREC_FP64 0     /* operator applies in float64                         */
 #define FSI_PREC_FP32_IR 1  /* float32 operator inside float64 iterative refinement */
@@ -156,7 +165,7 @@ typedef struct {
   double rtol;        /* stop when ||b - A x|| / ||b|| <= rtol                    */
   int32_t precond;    /* FSI_PC_*                                                 */
   int32_t precision;  /* FSI_PREC_*                                               */
-  uint32_t flags;     /* operator flags (FSI_ELASTIC_AUG)                         */
+  uint32_t flags;     /* operator flags (FSI_ELASTIC_AUG), FSI_HARVEST            */
   int32_t ir_max;     /* FP32_IR: maximum refinement steps                        */
   double ir_inner_rtol; /* FP32_IR: relative tolerance of each inner solve         */
 } fsi_solve_opts;
@@ -170,7 +179,8 @@ typedef struct {
   int32_t stalled;      /* 1: stopped because a whole restart cycle reduced the
                            true residual by less than 1 % (or an FP32_IR
                            refinement by less than 10 %)                          */
-  int32_t pad;
+  int32_t fallback;     /* 1: the learned preconditioner stalled and Jacobi GMRES
+                           finished the solve                                     */
 } fsi_solve_info;
 
 /* Solves J(st) x = rhs for one block by right-preconditioned restarted GMRES from
@@ -196,6 +206,8 @@ typedef struct {
   int64_t dof_applied;       /* sum over applies of the block's DoF count      */
   double max_ratio;          /* last iteration's max ||dx_blk|| / ||x_blk||     */
   double worst_rel_res;      /* largest final linear relative residual         */
+  int32_t fallback_solves;   /* FSI_PC_LEARNED solves finished by Jacobi GMRES */
+  int32_t pad;
 } fsi_step_info;
 
 /* One partitioned time step (Section 2.1.2 predictor-multicorrector, Section 2.5):
@@ -262,13 +274,78 @@ int fsi_init_phases(fsi_mesh* mesh, const fsi_surface* surfaces, int32_t n_surf,
 int fsi_gamma_beta_noalloc(int32_t nx, int32_t ny, int32_t nz, double lx, double ly, double lz, double eta,
                            const double* v, const double* phi, double* gamma_beta, void* stream);
 
+/* --------------------------------------------------------------- learned preconditioner
+ * (no counterpart in the paper, which prescribes GMRES but no preconditioner.)
+ * A 3D convolutional U-Net on the mesh's node grid acts as a flexible right
+ * preconditioner of the NS block: z = M(r) = D^{-1} r + (|r| / sqrt(n)) dbar_c kc_c y_c
+ * on non-Dirichlet rows (z = r on Dirichlet rows), where D is the Jacobi diagonal,
+ * n = 4 nn, and y = net(x) with input channels x_c = (D^{-1} r)_c sqrt(n) / (|r| dbar_c)
+ * (0 on Dirichlet rows) for c < 4, then the N phase indicators phi^{n+alpha}, zero
+ * padded to 16.  Network: 4 levels (node grids n -> n/2+1), 16 channels, 3x3x3
+ * zero-padded convolutions without bias, ReLU:
+ *   a_l = relu(conv x_l), e_l = relu(conv a_l), x_{l+1} = R e_l          (l = 0, 1, 2)
+ *   a_3 = relu(conv x_3), d_3 = relu(conv a_3)
+ *   b_l = relu(conv [e_l, P d_{l+1}]), d_l = relu(conv b_l)               (l = 2, 1, 0)
+ *   y = conv d_0  (4 output channels)
+ * with P the Q1 interpolation between node grids and R = P^T / 8.  Weights: 15
+ * convolutions W[co][ci][kz][ky][kx] float32, concatenated in the order enc0a, enc0b,
+ * enc1a, enc1b, enc2a, enc2b, bota, botb, dec2a, dec2b, dec1a, dec1b, dec0a, dec0b,
+ * out; they compute in bfloat16 with float32 accumulation (5th-generation tensor
+ * cores), activations are stored in bfloat16.
+ * Tensors passed in/out (x_in, target) use the library's layout: x_in is 2 planes of
+ * [nz+1][ny+1][nx+1] voxels x 8 bfloat16 (channels 0-7, then 8-15); target and y are
+ * planar [4][nn] (bfloat16 resp. float32).  All pointers are device pointers unless
+ * named _host.  Calls synchronise the mesh's stream. */
+typedef struct fsi_pc fsi_pc;
+typedef struct {
+  int32_t block;        /* FSI_BLOCK_NS                                           */
+  int32_t n_pairs_cap;  /* training pairs held on the device (ring buffer), >= 0   */
+  int32_t linear;       /* 1: no ReLU, the network is a linear operator of its input */
+  int32_t modulate;     /* 1: input channels 4.. are s_c (1 + phi_s) / 2 for each
+                           solid s (at most 3) instead of the indicators, so that a
+                           linear network keeps z = M(r) linear in r               */
+} fsi_pc_desc;
+int fsi_pc_create(fsi_mesh* mesh, const fsi_pc_desc* desc, fsi_pc** out);
+int fsi_pc_destroy(fsi_pc* pc);
+/* n_layers = 15; n_weights; fan[2*l] = out channels, fan[2*l+1] = in channels;
+ * grids[3*l..] = node-grid size (x, y, z) of level l.  Outputs are nullable. */
+int fsi_pc_layout(const fsi_pc* pc, int32_t* n_layers, int64_t* n_weights, int32_t* fan, int32_t* grids);
+/* host float32 weights (n = n_weights); set_weights also resets Adam's state */
+int fsi_pc_set_weights(fsi_pc* pc, const float* w_host, int64_t n);
+int fsi_pc_get_weights(const fsi_pc* pc, float* w_host, int64_t n);
+/* normalisation scales dbar_c, kc_c (host [4], > 0) */
+int fsi_pc_set_norm(fsi_pc* pc, const double* dbar_host, const double* kc_host);
+int fsi_pc_get_norm(const fsi_pc* pc, double* dbar_host, double* kc_host);
+/* y = net(x_in) */
+int fsi_pc_forward(fsi_pc* pc, const uint16_t* x_in, float* y);
+/* gradient of L = mean over non-Dirichlet rows (c, v) of (y_c - target_c / kc_c)^2
+ * w.r.t. the weights (grad: device float32 [n_weights]); loss_host: L */
+int fsi_pc_grad(fsi_pc* pc, const uint16_t* x_in, const uint16_t* target, float* grad, double* loss_host);
+/* z = M(r) at the state st (staged; D from the float64 NS diagonal with the
+ * elastic augmentation); r, z: NS block vectors [4][nn] float64 */
+int fsi_pc_apply(fsi_pc* pc, const fsi_state* st, const double* r, double* z);
+/* stores the training pair (r, e) (A e = r) at the state st: input channels as in
+ * an apply, target t_c = (e - D^{-1} r)_c sqrt(n) / (|r| dbar_c); the first pair
+ * fixes dbar_c = mean of D^{-1}_c over non-Dirichlet rows */
+int fsi_pc_add_pair(fsi_pc* pc, const fsi_state* st, const double* r, const double* e);
+int fsi_pc_pairs(const fsi_pc* pc, int32_t* n_pairs);
+/* kc_c = RMS of the stored targets' component c (non-Dirichlet rows) */
+int fsi_pc_fit_norm(fsi_pc* pc);
+/* iters Adam steps (lr; beta1 0.9, beta2 0.999, eps 1e-8), step i on the stored
+ * pair p = order_host[i] with the relative loss L_p / mean over valid rows of
+ * (target_p / kc)^2 (every pair weighs the same, whatever the scale of its error);
+ * loss_host[i] (nullable) = that relative loss before step i */
+int fsi_pc_train(fsi_pc* pc, int32_t iters, float lr, const int32_t* order_host, float* loss_host);
+/* attaches pc to its mesh for FSI_PC_LEARNED and FSI_HARVEST (NULL detaches) */
+int fsi_set_pc(fsi_mesh* mesh, fsi_pc* pc);
+
 /* --------------------------------------------------------------- measurement
  * (no counterpart in the paper: timing support for the benchmark)
  * fsi_profile(mesh, 1) starts recording a CUDA event pair around every kernel the
  * mesh launches (counters reset); fsi_profile(mesh, 0) stops.  Launch counts are
  * kept whether or not events are recorded.  fsi_profile_read synchronises the
  * stream and returns, per kernel class, the launches and the summed event time. */
-#define FSI_PROF_CLASSES 20
+#define FSI_PROF_CLASSES 23
 typedef struct {
   char name[24];
   int64_t launches;

@@ -33,7 +33,10 @@ the GPU library trains and applies as a flexible right preconditioner inside FGM
 `quant="bf16"` rounds, at the same places as the GPU kernels store them, the weights,
 the activations, the restriction/prolongation results and the back-propagated
 activation gradients to bfloat16 (round to nearest even); all arithmetic between those
-points stays float64.  `quant=None` is the float64 network.
+points stays float64.  `quant="bf16-f32"` rounds at the same places but accumulates
+the convolutions in float32: the spread between the two measures how far two correct
+implementations of the bfloat16 network can drift apart through rounding alone (the
+tests take their tolerances from it).  `quant=None` is the float64 network.
 
 Parity pins: tests/test_oracle_pcnet.py (brute-force convolution, adjoint identities,
 Q1 reproduction of linear fields, finite-difference gradients, Adam closed forms).
@@ -57,7 +60,11 @@ def bf16(a: np.ndarray) -> np.ndarray:
 
 
 def _q(a, quant):
-    return bf16(a) if quant == "bf16" else a
+    return bf16(a) if quant in ("bf16", "bf16-f32") else a
+
+
+def _acc(quant):
+    return np.float32 if quant == "bf16-f32" else np.float64
 
 
 # ------------------------------------------------------------------------ grids
@@ -94,29 +101,32 @@ def restrict(f: np.ndarray, coarse_shape) -> np.ndarray:
 
 
 # ----------------------------------------------------------------- convolutions
-def conv3(x: np.ndarray, W: np.ndarray) -> np.ndarray:
-    """y[o, v] = sum_{i, k} W[o, i, k] x[i, v + k - 1], zero outside the grid."""
+def conv3(x: np.ndarray, W: np.ndarray, acc=np.float64) -> np.ndarray:
+    """y[o, v] = sum_{i, k} W[o, i, k] x[i, v + k - 1], zero outside the grid
+    (accumulated in the floating type `acc`, returned as float64)."""
     _, nz, ny, nx = x.shape
-    xp = np.pad(x, ((0, 0), (1, 1), (1, 1), (1, 1)))
-    y = np.zeros((W.shape[0], nz, ny, nx))
+    xp = np.pad(x, ((0, 0), (1, 1), (1, 1), (1, 1))).astype(acc)
+    W = W.astype(acc)
+    y = np.zeros((W.shape[0], nz, ny, nx), dtype=acc)
     for kz in range(3):
         for ky in range(3):
             for kx in range(3):
                 y += np.einsum("oi,izyx->ozyx", W[:, :, kz, ky, kx],
                                xp[:, kz:kz + nz, ky:ky + ny, kx:kx + nx])
-    return y
+    return y.astype(np.float64)
 
 
-def conv3_adjoint(g: np.ndarray, W: np.ndarray) -> np.ndarray:
+def conv3_adjoint(g: np.ndarray, W: np.ndarray, acc=np.float64) -> np.ndarray:
     """The adjoint of x -> conv3(x, W) applied to g[o, v]."""
     _, nz, ny, nx = g.shape
-    xp = np.zeros((W.shape[1], nz + 2, ny + 2, nx + 2))
+    g, W = g.astype(acc), W.astype(acc)
+    xp = np.zeros((W.shape[1], nz + 2, ny + 2, nx + 2), dtype=acc)
     for kz in range(3):
         for ky in range(3):
             for kx in range(3):
                 xp[:, kz:kz + nz, ky:ky + ny, kx:kx + nx] += np.einsum(
                     "oi,ozyx->izyx", W[:, :, kz, ky, kx], g)
-    return xp[:, 1:-1, 1:-1, 1:-1]
+    return xp[:, 1:-1, 1:-1, 1:-1].astype(np.float64)
 
 
 def conv3_wgrad(x: np.ndarray, g: np.ndarray) -> np.ndarray:
@@ -164,26 +174,30 @@ def flatten(Ws: dict, cin0: int, cout: int) -> np.ndarray:
     return np.concatenate([Ws[name].ravel() for name, _, _ in layer_specs(cin0, cout)])
 
 
-def forward(w: np.ndarray, x0: np.ndarray, cout: int, quant=None):
-    """y = network(x0); x0[cin0, nz, ny, nx].  Returns (y, cache)."""
+def forward(w: np.ndarray, x0: np.ndarray, cout: int, quant=None, relu_on: bool = True):
+    """y = network(x0); x0[cin0, nz, ny, nx].  Returns (y, cache).  relu_on=False
+    drops every ReLU: the network is then a linear operator of x0 (a learned
+    multigrid-like cycle of convolutions, restrictions and prolongations)."""
     cin0 = x0.shape[0]
     W = {k: _q(v, quant) for k, v in unflatten(w, cin0, cout).items()}
     shapes = level_shapes(x0.shape[1:])
-    relu = lambda a: np.maximum(a, 0.0)  # noqa: E731
+    relu = (lambda a: np.maximum(a, 0.0)) if relu_on else (lambda a: a)  # noqa: E731
+    conv = lambda a, Wl: conv3(a, Wl, _acc(quant))  # noqa: E731
     c = {"x0": _q(x0, quant)}
     for lv in range(3):
-        c[f"a{lv}"] = _q(relu(conv3(c[f"x{lv}"], W[f"enc{lv}a"])), quant)
-        c[f"e{lv}"] = _q(relu(conv3(c[f"a{lv}"], W[f"enc{lv}b"])), quant)
+        c[f"a{lv}"] = _q(relu(conv(c[f"x{lv}"], W[f"enc{lv}a"])), quant)
+        c[f"e{lv}"] = _q(relu(conv(c[f"a{lv}"], W[f"enc{lv}b"])), quant)
         c[f"x{lv + 1}"] = _q(restrict(c[f"e{lv}"], shapes[lv + 1]), quant)
-    c["a3"] = _q(relu(conv3(c["x3"], W["bota"])), quant)
-    c["d3"] = _q(relu(conv3(c["a3"], W["botb"])), quant)
+    c["a3"] = _q(relu(conv(c["x3"], W["bota"])), quant)
+    c["d3"] = _q(relu(conv(c["a3"], W["botb"])), quant)
     for lv in (2, 1, 0):
         up = _q(prolong(c[f"d{lv + 1}"], shapes[lv]), quant)
         c[f"c{lv}"] = np.concatenate([c[f"e{lv}"], up])
-        c[f"b{lv}"] = _q(relu(conv3(c[f"c{lv}"], W[f"dec{lv}a"])), quant)
-        c[f"d{lv}"] = _q(relu(conv3(c[f"b{lv}"], W[f"dec{lv}b"])), quant)
-    y = conv3(c["d0"], W["out"])
+        c[f"b{lv}"] = _q(relu(conv(c[f"c{lv}"], W[f"dec{lv}a"])), quant)
+        c[f"d{lv}"] = _q(relu(conv(c[f"b{lv}"], W[f"dec{lv}b"])), quant)
+    y = conv(c["d0"], W["out"])
     c["W"] = W
+    c["relu_on"] = relu_on
     return y, c
 
 
@@ -202,31 +216,35 @@ def backward(w: np.ndarray, cache: dict, gy: np.ndarray, quant=None) -> np.ndarr
     cout = gy.shape[0]
     shapes = level_shapes(cache["x0"].shape[1:])
     gW = {}
-    mask = lambda g, a: g * (a > 0)  # noqa: E731  (relu' from the stored output)
+    if cache["relu_on"]:
+        mask = lambda g, a: g * (a > 0)  # noqa: E731  (relu' from the stored output)
+    else:
+        mask = lambda g, a: g  # noqa: E731
+    conv3_adj = lambda g, Wl: conv3_adjoint(g, Wl, _acc(quant))  # noqa: E731
     g = _q(gy, quant)
     gW["out"] = conv3_wgrad(cache["d0"], g)
-    g_d = _q(mask(conv3_adjoint(g, W["out"]), cache["d0"]), quant)
+    g_d = _q(mask(conv3_adj(g, W["out"]), cache["d0"]), quant)
     g_e = {}
     for lv in (0, 1, 2):
         gW[f"dec{lv}b"] = conv3_wgrad(cache[f"b{lv}"], g_d)
-        g_b = _q(mask(conv3_adjoint(g_d, W[f"dec{lv}b"]), cache[f"b{lv}"]), quant)
+        g_b = _q(mask(conv3_adj(g_d, W[f"dec{lv}b"]), cache[f"b{lv}"]), quant)
         gW[f"dec{lv}a"] = conv3_wgrad(cache[f"c{lv}"], g_b)
-        g_c = _q(conv3_adjoint(g_b, W[f"dec{lv}a"]), quant)
+        g_c = _q(conv3_adj(g_b, W[f"dec{lv}a"]), quant)
         g_e[lv] = g_c[:CH]
         # adjoint of P is 8 R
         g_d = _q(mask(8.0 * restrict(g_c[CH:], shapes[lv + 1]), cache[f"d{lv + 1}"]), quant)
     gW["botb"] = conv3_wgrad(cache["a3"], g_d)
-    g_a = _q(mask(conv3_adjoint(g_d, W["botb"]), cache["a3"]), quant)
+    g_a = _q(mask(conv3_adj(g_d, W["botb"]), cache["a3"]), quant)
     gW["bota"] = conv3_wgrad(cache["x3"], g_a)
-    g_x = _q(conv3_adjoint(g_a, W["bota"]), quant)
+    g_x = _q(conv3_adj(g_a, W["bota"]), quant)
     for lv in (2, 1, 0):
         # adjoint of R is (1/8) P; e_l also feeds the decoder's concatenation
         g_el = _q(mask(g_e[lv] + prolong(g_x, shapes[lv]) / 8.0, cache[f"e{lv}"]), quant)
         gW[f"enc{lv}b"] = conv3_wgrad(cache[f"a{lv}"], g_el)
-        g_a = _q(mask(conv3_adjoint(g_el, W[f"enc{lv}b"]), cache[f"a{lv}"]), quant)
+        g_a = _q(mask(conv3_adj(g_el, W[f"enc{lv}b"]), cache[f"a{lv}"]), quant)
         gW[f"enc{lv}a"] = conv3_wgrad(cache[f"x{lv}"], g_a)
         if lv > 0:
-            g_x = _q(conv3_adjoint(g_a, W[f"enc{lv}a"]), quant)
+            g_x = _q(conv3_adj(g_a, W[f"enc{lv}a"]), quant)
     return flatten(gW, cin0, cout)
 
 
@@ -241,14 +259,20 @@ def adam_step(w, g, m, v, t: int, lr: float):
 
 
 # ------------------------------------------------------- preconditioner apply
-def pc_input(r, dinv, phases, dirichlet, dbar, rnorm, quant=None):
-    """Network input channels [ncomp + N padded to 16k, nz, ny, nx] from a block
-    residual r[ncomp][nz, ny, nx]: (D^{-1} r)_c * sqrt(n_rows) / (rnorm * dbar_c) on
-    non-Dirichlet rows (0 on Dirichlet rows), then the phase indicators."""
+def pc_input(r, dinv, phases, dirichlet, dbar, rnorm, quant=None, modulate=False):
+    """Network input channels [16 k, nz, ny, nx] from a block residual r[ncomp][...]:
+    s_c = (D^{-1} r)_c * sqrt(n_rows) / (rnorm * dbar_c) on non-Dirichlet rows (0 on
+    Dirichlet rows), followed by either the indicators `phases` themselves or, with
+    modulate=True, the products s_c * (1 + phi) / 2 for every indicator in `phases`
+    (the input, and a network without ReLU, then stay linear in r); zero padded."""
     ncomp = r.shape[0]
     g = np.sqrt(r.size) / rnorm
     s = np.where(dirichlet, 0.0, dinv * r)
-    chans = [s[c] * g / dbar[c] for c in range(ncomp)] + list(phases)
+    chans = [s[c] * g / dbar[c] for c in range(ncomp)]
+    if modulate:
+        chans += [chans[c] * 0.5 * (1.0 + ph) for ph in phases for c in range(ncomp)]
+    else:
+        chans += list(phases)
     cin = -(-len(chans) // CH) * CH
     x = np.zeros((cin,) + r.shape[1:])
     x[:len(chans)] = chans
@@ -263,12 +287,12 @@ def pc_output(r, dinv, dirichlet, y, dbar, kc, rnorm):
     return np.where(dirichlet, r, z)
 
 
-def pc_apply(w, r, dinv, phases, dirichlet, dbar, kc, quant=None):
+def pc_apply(w, r, dinv, phases, dirichlet, dbar, kc, quant=None, relu_on=True, modulate=False):
     rnorm = float(np.linalg.norm(r))
     if rnorm == 0.0:
         return np.zeros_like(r)
-    x = pc_input(r, dinv, phases, dirichlet, dbar, rnorm, quant)
-    y, _ = forward(w, x, r.shape[0], quant)
+    x = pc_input(r, dinv, phases, dirichlet, dbar, rnorm, quant, modulate)
+    y, _ = forward(w, x, r.shape[0], quant, relu_on)
     return pc_output(r, dinv, dirichlet, y, dbar, kc, rnorm)
 
 

@@ -23,7 +23,7 @@ int cuda_check(cudaError_t e, const char* what) {
 static const char* kProfNames[P_NCLS] = {
     "stage", "ns_residual", "ns_jvp_f64", "ns_jvp_f32", "ns_diag", "ac_residual", "ac_jvp_f64", "ac_jvp_f32",
     "ac_diag", "b_residual", "b_jvp_f64", "b_jvp_f32", "b_diag", "gamma_beta", "krylov_vector", "init",
-    "krylov_dot", "krylov_update", "krylov_scalar", "to_float"};
+    "krylov_dot", "krylov_update", "krylov_scalar", "to_float", "pc_conv", "pc_wgrad", "pc_aux"};
 constexpr int PROF_PAIRS = 4096;
 
 int prof_harvest(fsi_mesh* m) {
@@ -337,6 +337,7 @@ int fsi_destroy_mesh(fsi_mesh* m) {
   cudaFree(m->step_ws);
   cudaFree(m->kry_dev);
   cudaFree(m->dx32);
+  cudaFree(m->Z);
   if (m->kry_est) cudaFreeHost(m->kry_est);
   for (cudaEvent_t e : m->kry_ev) cudaEventDestroy(e);
   for (cudaEvent_t e : m->prof.ev) cudaEventDestroy(e);

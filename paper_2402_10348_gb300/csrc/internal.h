@@ -14,7 +14,7 @@ namespace fsi {
 enum ProfClass {
   P_STAGE, P_NS_RES, P_NS_JVP64, P_NS_JVP32, P_NS_DIAG, P_AC_RES, P_AC_JVP64, P_AC_JVP32,
   P_AC_DIAG, P_B_RES, P_B_JVP64, P_B_JVP32, P_B_DIAG, P_COEF, P_KRYLOV, P_INIT, P_KRY_DOT, P_KRY_UPD,
-  P_KRY_SMALL, P_KRY_CONV, P_NCLS
+  P_KRY_SMALL, P_KRY_CONV, P_PC_CONV, P_PC_WGRAD, P_PC_AUX, P_NCLS
 };
 struct Profiler {
   bool on = false;
@@ -71,6 +71,9 @@ struct fsi_mesh {
   std::vector<cudaEvent_t> kry_ev;
   double* step_ws = nullptr; // [2][max block] time-step work vectors
   int64_t step_ws_n = 0;
+  double* Z = nullptr;       // [m][n] FGMRES preconditioned directions
+  int64_t Z_n = 0;
+  fsi_pc* pc = nullptr;      // attached learned preconditioner (NS block), not owned
   // counters (step info)
   int64_t applies = 0;
   int64_t dof_applied = 0;

@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "pcnet.h"
 
 namespace fsi {
 
@@ -190,6 +191,25 @@ __global__ void __launch_bounds__(VB) combine_kernel(double* __restrict__ x, con
   }
 }
 
+// z = V_slot (contiguous copy of one basis vector)
+__global__ void extract_kernel(const double* __restrict__ V, int M1, int slot, double* __restrict__ z, int64_t n) {
+  for (int64_t j = blockIdx.x * (int64_t)VB + threadIdx.x; j < n; j += (int64_t)gridDim.x * VB)
+    z[j] = V[(j / CH) * (int64_t)M1 * CH + (int64_t)slot * CH + (j % CH)];
+}
+
+// x += sum_i y_i Z_i (flexible GMRES: the stored preconditioned directions)
+__global__ void __launch_bounds__(VB) zcombine_kernel(double* __restrict__ x, const double* __restrict__ Z, int k,
+                                                      const KryDev* K, int64_t n) {
+  __shared__ double ys[MMAX];
+  for (int i = threadIdx.x; i < k; i += VB) ys[i] = K->y[i];
+  __syncthreads();
+  for (int64_t j = blockIdx.x * (int64_t)VB + threadIdx.x; j < n; j += (int64_t)gridDim.x * VB) {
+    double s = 0.0;
+    for (int i = 0; i < k; ++i) s += ys[i] * Z[(int64_t)i * n + j];
+    x[j] += s;
+  }
+}
+
 // --------------------------------------------------------- small device kernels
 // After pass 1: the column h[0..j], |w_old|^2 = h[j+1]; |w_new|^2 in nrm_new.
 __global__ void orth_decide(KryDev* K, int j) {
@@ -326,7 +346,16 @@ static int basis_update(fsi_mesh* m, double* w, const double* V, int M1, int k, 
   return FSI_OK;
 }
 
+// per-CTA partial sums of the reductions (fixed size, allocated on first use)
+static int ensure_partials(fsi_mesh* m) {
+  if (m->partials_dot) return FSI_OK;
+  FSI_CUDA(cudaMalloc(&m->partials_dot, sizeof(double) * (size_t)(MMAX + 2 + DCH) * 152 * 4));
+  return FSI_OK;
+}
+
 static int dot_dev(fsi_mesh* m, const double* a, const double* b, int64_t n, double* out) {
+  int rc = ensure_partials(m);
+  if (rc) return rc;
   const int G = vgrid(n);
   FSI_LAUNCH(m, P_KRY_DOT, dot_kernel<<<G, VB, 0, m->stream>>>(a, b, n, m->partials_dot));
   FSI_LAUNCH(m, P_KRY_DOT, sum_partials<<<1, VB, 0, m->stream>>>(m->partials_dot, G, out, nullptr));
@@ -367,13 +396,12 @@ static int ensure_krylov(fsi_mesh* m, int64_t n, int mm) {
   cudaFree(m->V);
   cudaFree(m->wk);
   cudaFree(m->dinv);
-  cudaFree(m->partials_dot);
-  m->V = m->wk = m->dinv = m->partials_dot = nullptr;
+  m->V = m->wk = m->dinv = nullptr;
   const int64_t nch = (nn + CH - 1) / CH;
   FSI_CUDA(cudaMalloc(&m->V, sizeof(double) * (size_t)nch * (mx + 1) * CH));
   FSI_CUDA(cudaMalloc(&m->wk, sizeof(double) * (size_t)7 * nn));
   FSI_CUDA(cudaMalloc(&m->dinv, sizeof(double) * (size_t)nn));
-  FSI_CUDA(cudaMalloc(&m->partials_dot, sizeof(double) * (size_t)(MMAX + 2 + DCH) * 152 * 4));
+  if (int rc = ensure_partials(m)) return rc;
   if (!m->kry_dev) {
     FSI_CUDA(cudaMalloc(&m->kry_dev, sizeof(KryDev)));
     FSI_CUDA(cudaMallocHost(&m->kry_est, sizeof(double) * 3 * (MMAX + 1)));
@@ -388,7 +416,8 @@ static int ensure_krylov(fsi_mesh* m, int64_t n, int mm) {
 // One GMRES(m) solve A x = b from x = 0 with A = the block operator (flags) and the
 // right preconditioner diag(dinv).
 static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double* x, int mm, double rtol,
-                      int max_iter, unsigned flags, int* iters, int* restarts, double* rel_out, int* stalled) {
+                      int max_iter, unsigned flags, int* iters, int* restarts, double* rel_out, int* stalled,
+                      fsi_pc* pc = nullptr, fsi_pc* harvest = nullptr) {
   const int64_t n = blk.n;
   const int M1 = m->kry_m + 1;
   const int G = vgrid(n);
@@ -412,6 +441,7 @@ static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double
   FSI_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, m->stream));
   double rel = 1.0, cycle_rel = 1.0;
   bool first_cycle = true;
+  int n_arnoldi_pairs = 0;
   while (true) {
     // |r| on the device; the host needs it for the stopping and stall tests
     if ((rc = dot_dev(m, r, r, n, m->red))) return rc;
@@ -434,8 +464,20 @@ static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double
     const int jmax = std::min(mm, max_iter - *iters);
     const double vb = 8.0 * (double)n;  // bytes of one vector
     for (int j = 0; j < jmax && !done; ++j) {
-      FSI_LAUNCH(m, P_KRYLOV, precond_kernel<<<G, VB, 0, m->stream>>>(V, M1, j, m->dinv, z, n));
-      if ((rc = op_jvp(m, blk, z, w, flags))) return rc;
+      if (pc) {  // flexible GMRES: z_j = M(v_j), |v_j| = 1
+        double* zj = m->Z + (int64_t)j * n;
+        FSI_LAUNCH(m, P_KRYLOV, extract_kernel<<<G, VB, 0, m->stream>>>(V, M1, j, t, n));
+        if ((rc = pcn::apply(pc, t, 1.0, m->dinv, zj))) return rc;
+        if ((rc = op_jvp(m, blk, zj, w, flags))) return rc;
+      } else {
+        FSI_LAUNCH(m, P_KRYLOV, precond_kernel<<<G, VB, 0, m->stream>>>(V, M1, j, m->dinv, z, n));
+        if ((rc = op_jvp(m, blk, z, w, flags))) return rc;
+        // broadband training pairs: A z_j = w exactly for the operator just applied
+        if (harvest && j % 8 == 4 && n_arnoldi_pairs < 8) {
+          if ((rc = pcn::add_pair(harvest, w, nullptr, z, nullptr, m->dinv))) return rc;
+          ++n_arnoldi_pairs;
+        }
+      }
       // pass 1: h = V^T w and |w|^2 (slot j+1 of h)
       if ((rc = basis_dots(m, V, M1, j + 1, w, n, K->h, true))) return rc;
       if ((rc = basis_update(m, w, V, M1, j + 1, K->h, n, &K->nrm_new))) return rc;
@@ -478,8 +520,12 @@ static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double
       }
     }
     FSI_LAUNCH(m, P_KRY_SMALL, lsq_kernel<<<1, 1, 0, m->stream>>>(K, jend, mm));
-    FSI_LAUNCH(m, P_KRYLOV, combine_kernel<<<cgrid((n + CH - 1) / CH), VB, 0, m->stream>>>(x, m->dinv, V, M1, jend,
-                                                                                          K, n));
+    if (pc) {
+      FSI_LAUNCH(m, P_KRYLOV, zcombine_kernel<<<G, VB, 0, m->stream>>>(x, m->Z, jend, K, n));
+    } else {
+      FSI_LAUNCH(m, P_KRYLOV, combine_kernel<<<cgrid((n + CH - 1) / CH), VB, 0, m->stream>>>(x, m->dinv, V, M1, jend,
+                                                                                            K, n));
+    }
     // true residual r = b - A x
     if ((rc = op_jvp(m, blk, x, t, flags))) return rc;
     FSI_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, m->stream));
@@ -498,19 +544,66 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& blk, const double* rhs, double* x,
   int rc = ensure_krylov(m, n, mm);
   if (rc) return rc;
   const int64_t a0 = m->applies;
-  // Jacobi diagonal of the float64 operator
-  if (o.precond == FSI_PC_JACOBI) {
-    if ((rc = op_diag(m, blk, m->wk + 3 * n, o.flags & ~FSI_FP32))) return rc;
+  // the learned preconditioner acts on the NS block only; other blocks use Jacobi
+  fsi_pc* pc = (o.precond == FSI_PC_LEARNED && blk.kind == 0) ? m->pc : nullptr;
+  if (o.precond == FSI_PC_LEARNED && blk.kind == 0 && !pc)
+    return set_error(FSI_EINVAL, "GMRES: FSI_PC_LEARNED without an attached preconditioner (fsi_set_pc)");
+  fsi_pc* harvest = ((o.flags & FSI_HARVEST) && blk.kind == 0 && m->pc && m->pc->cap > 0) ? m->pc : nullptr;
+  const unsigned opflags = o.flags & ~FSI_HARVEST;
+  if (pc && (m->Z_n < n * mm || !m->Z)) {
+    cudaFree(m->Z);
+    m->Z = nullptr;
+    FSI_CUDA(cudaMalloc(&m->Z, sizeof(double) * (size_t)(n * mm)));
+    m->Z_n = n * mm;
+  }
+  if (harvest && (rc = pcn::ensure_checkpoints(harvest))) return rc;
+  // Jacobi diagonal of the float64 operator (also the learned preconditioner's scale)
+  if (o.precond == FSI_PC_JACOBI || o.precond == FSI_PC_LEARNED || harvest) {
+    if ((rc = op_diag(m, blk, m->wk + 3 * n, opflags & ~FSI_FP32))) return rc;
     if ((rc = vec_recip(m, m->wk + 3 * n, m->dinv, n))) return rc;
-  } else {
+  }
+  if (o.precond == FSI_PC_NONE) {
     FSI_LAUNCH(m, P_KRYLOV, fill_kernel<<<vgrid(n), VB, 0, m->stream>>>(m->dinv, 1.0, n));
   }
   fsi_solve_info inf{};
   double rel = 0.0;
+  int nck = 0;  // harvest checkpoints recorded
+  auto checkpoint = [&](const double* xk, const double* rk) -> int {
+    if (!harvest || nck >= pcn::CKMAX) return FSI_OK;
+    FSI_CUDA(cudaMemcpyAsync(harvest->ck + (int64_t)nck * n, xk, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                             m->stream));
+    FSI_CUDA(cudaMemcpyAsync(harvest->ck + (int64_t)(pcn::CKMAX + nck) * n, rk, sizeof(double) * n,
+                             cudaMemcpyDeviceToDevice, m->stream));
+    ++nck;
+    return FSI_OK;
+  };
+  double* rfin = nullptr;  // final true residual (harvest)
   if (o.precision == FSI_PREC_FP64) {
-    rc = gmres_core(m, blk, rhs, x, mm, o.rtol, o.max_iter, o.flags & ~FSI_FP32, &inf.iterations, &inf.restarts,
-                    &rel, &inf.stalled);
+    rc = gmres_core(m, blk, rhs, x, mm, o.rtol, o.max_iter, opflags & ~FSI_FP32, &inf.iterations, &inf.restarts,
+                    &rel, &inf.stalled, pc, pc ? nullptr : harvest);
     if (rc) return rc;
+    if (pc && rel > o.rtol && inf.iterations < o.max_iter) {
+      // fallback: Jacobi GMRES on the remaining residual r = rhs - A x (in wk[0..n))
+      double* d = m->wk + 4 * n;
+      double* r = m->wk + 5 * n;
+      FSI_CUDA(cudaMemcpyAsync(r, m->wk, sizeof(double) * n, cudaMemcpyDeviceToDevice, m->stream));
+      double rel2;
+      int st2 = 0;
+      rc = gmres_core(m, blk, r, d, mm, o.rtol / std::max(rel, 1e-300), o.max_iter - inf.iterations,
+                      opflags & ~FSI_FP32, &inf.iterations, &inf.restarts, &rel2, &st2, nullptr);
+      if (rc) return rc;
+      if ((rc = vec_axpy(m, 1.0, d, x, n))) return rc;
+      rel *= rel2;
+      inf.stalled = st2;
+      inf.fallback = 1;
+    }
+    rfin = m->wk;  // rhs - A x (the fallback's final residual is the same vector)
+    if (harvest) {  // the one checkpoint x_0 = 0, r_0 = rhs
+      FSI_CUDA(cudaMemsetAsync(harvest->ck, 0, sizeof(double) * n, m->stream));
+      FSI_CUDA(cudaMemcpyAsync(harvest->ck + (int64_t)pcn::CKMAX * n, rhs, sizeof(double) * n,
+                               cudaMemcpyDeviceToDevice, m->stream));
+      nck = 1;
+    }
   } else {
     // x = 0; r = rhs; repeat: solve A32 d = r; x += d; r = rhs - A64 x
     double* d = m->wk + 4 * n;
@@ -522,14 +615,17 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& blk, const double* rhs, double* x,
     if (!std::isfinite(b2)) return set_error(FSI_ENAN, "IR: right-hand side is not finite");
     const double bnorm = std::sqrt(b2);
     rel = bnorm == 0.0 ? 0.0 : 1.0;
+    fsi_pc* inner_pc = pc;
     for (int k = 0; k < std::max(1, o.ir_max) && rel > o.rtol; ++k) {
+      if ((rc = checkpoint(x, r))) return rc;
       double inner_rel;
       int inner_stalled;
-      rc = gmres_core(m, blk, r, d, mm, o.ir_inner_rtol, o.max_iter - inf.iterations, (o.flags | FSI_FP32),
-                      &inf.iterations, &inf.restarts, &inner_rel, &inner_stalled);
+      rc = gmres_core(m, blk, r, d, mm, o.ir_inner_rtol, o.max_iter - inf.iterations, (opflags | FSI_FP32),
+                      &inf.iterations, &inf.restarts, &inner_rel, &inner_stalled, inner_pc,
+                      inner_pc ? nullptr : harvest);
       if (rc) return rc;
       if ((rc = vec_axpy(m, 1.0, d, x, n))) return rc;
-      if ((rc = op_jvp(m, blk, x, d, o.flags & ~FSI_FP32))) return rc;
+      if ((rc = op_jvp(m, blk, x, d, opflags & ~FSI_FP32))) return rc;
       FSI_CUDA(cudaMemcpyAsync(r, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, m->stream));
       if ((rc = vec_axpy(m, -1.0, d, r, n))) return rc;
       double r2;
@@ -539,12 +635,27 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& blk, const double* rhs, double* x,
       rel = bnorm > 0.0 ? std::sqrt(r2) / bnorm : 0.0;
       inf.refinements = k + 1;
       if (inf.iterations >= o.max_iter) break;
+      if (inner_pc && (inner_stalled || (rel > o.rtol && rel > 0.9 * prev))) {
+        inner_pc = nullptr;  // the network stalled: Jacobi GMRES finishes the solve
+        inf.fallback = 1;
+        continue;
+      }
       if (rel > o.rtol && rel > 0.9 * prev) {
         inf.stalled = 1;
         break;
       }
     }
+    rfin = r;
   }
+  if (harvest) {
+    // pairs (r_k - r*, x* - x_k): A (x* - x_k) = r_k - r* holds exactly for the
+    // float64 operator that computed the residuals
+    for (int k = 0; k < nck; ++k)
+      if ((rc = pcn::add_pair(harvest, harvest->ck + (int64_t)(pcn::CKMAX + k) * n, rfin, x,
+                              harvest->ck + (int64_t)k * n, m->dinv)))
+        return rc;
+  }
+  if (pc && (rc = pcn::check_err(pc))) return rc;
   inf.rel_res = rel;
   inf.applies = (int)(m->applies - a0);
   if (info) *info = inf;

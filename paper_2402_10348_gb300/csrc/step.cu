@@ -89,6 +89,7 @@ int fsi_step(fsi_mesh* m, fsi_state* st, const fsi_step_opts* o, fsi_step_info* 
       if (rc && rc != FSI_ENOCONV) return rc;
       inf.worst_rel_res = std::max(inf.worst_rel_res, si.rel_res);
       if (si.stalled) inf.stalled_solves++;
+      if (si.fallback) inf.fallback_solves++;
       if (b.kind == 0) inf.gmres_iters_ns += si.iterations;
       else if (b.kind == 1) inf.gmres_iters_ac += si.iterations;
       else inf.gmres_iters_b += si.iterations;

@@ -18,7 +18,8 @@ FSI_OK, FSI_EINVAL, FSI_ECUDA, FSI_ENOCONV, FSI_ENAN, FSI_ETIMEOUT, FSI_ENOMEM =
 FSI_BLOCK_NS = 0
 FSI_ELASTIC_AUG = 0x1
 FSI_FP32 = 0x2
-FSI_PC_NONE, FSI_PC_JACOBI = 0, 1
+FSI_PC_NONE, FSI_PC_JACOBI, FSI_PC_LEARNED = 0, 1, 2
+FSI_HARVEST = 0x10
 FSI_PREC_FP64, FSI_PREC_FP32_IR = 0, 1
 FSI_BC_NATURAL, FSI_BC_DIRICHLET = 0, 1
 FSI_RULE_SURFACE, FSI_RULE_COMPLEMENT = 0, 1
@@ -72,7 +73,7 @@ class fsi_solve_opts(C.Structure):
 
 class fsi_solve_info(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("restarts", C.c_int32), ("refinements", C.c_int32),
-                ("applies", C.c_int32), ("rel_res", C.c_double), ("stalled", C.c_int32), ("pad", C.c_int32)]
+                ("applies", C.c_int32), ("rel_res", C.c_double), ("stalled", C.c_int32), ("fallback", C.c_int32)]
 
 
 class fsi_step_opts(C.Structure):
@@ -83,7 +84,8 @@ class fsi_step_opts(C.Structure):
 class fsi_step_info(C.Structure):
     _fields_ = [("nl_iters", C.c_int32), ("gmres_iters_ns", C.c_int32), ("gmres_iters_ac", C.c_int32),
                 ("gmres_iters_b", C.c_int32), ("applies", C.c_int32), ("stalled_solves", C.c_int32),
-                ("dof_applied", C.c_int64), ("max_ratio", C.c_double), ("worst_rel_res", C.c_double)]
+                ("dof_applied", C.c_int64), ("max_ratio", C.c_double), ("worst_rel_res", C.c_double),
+                ("fallback_solves", C.c_int32), ("pad", C.c_int32)]
 
 
 class fsi_surface(C.Structure):
@@ -99,12 +101,15 @@ class fsi_profile_entry(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("ms", C.c_double), ("bytes", C.c_double)]
 
 
-FSI_PROF_CLASSES = 20
+FSI_PROF_CLASSES = 23
 
 EXPORTS = ["fsi_create_mesh", "fsi_destroy_mesh", "fsi_set_stream", "fsi_mesh_info", "fsi_residual",
            "fsi_jvp", "fsi_diag", "fsi_update_ac_coeffs", "fsi_set_ac_coeffs", "fsi_fix_gamma",
            "fsi_gmres", "fsi_step", "fsi_init_phases", "fsi_gamma_beta_noalloc", "fsi_profile",
-           "fsi_profile_read", "fsi_last_error"]
+           "fsi_profile_read", "fsi_pc_create", "fsi_pc_destroy", "fsi_pc_layout", "fsi_pc_set_weights",
+           "fsi_pc_get_weights", "fsi_pc_set_norm", "fsi_pc_get_norm", "fsi_pc_forward", "fsi_pc_grad",
+           "fsi_pc_apply", "fsi_pc_add_pair", "fsi_pc_pairs", "fsi_pc_fit_norm", "fsi_pc_train", "fsi_set_pc",
+           "fsi_last_error"]
 
 _lib = None
 
@@ -300,3 +305,117 @@ def fsi_profile_read(mesh: Mesh) -> dict:
     n = C.c_int32()
     _check(lib().fsi_profile_read(mesh.handle, out, C.byref(n)))
     return {out[i].name.decode(): (out[i].launches, out[i].ms, out[i].bytes) for i in range(n.value)}
+
+
+# ------------------------------------------------------------------ learned preconditioner
+class fsi_pc_desc(C.Structure):
+    _fields_ = [("block", C.c_int32), ("n_pairs_cap", C.c_int32), ("linear", C.c_int32), ("modulate", C.c_int32)]
+
+
+class PC:
+    """Owns an fsi_pc handle; keeps its mesh alive."""
+
+    def __init__(self, handle, mesh: Mesh):
+        self.handle = handle
+        self.mesh = mesh
+        nl, nw = C.c_int32(), C.c_int64()
+        fan = (C.c_int32 * 30)()
+        grids = (C.c_int32 * 12)()
+        _check(lib().fsi_pc_layout(handle, C.byref(nl), C.byref(nw), fan, grids))
+        self.n_weights = nw.value
+        self.fan = [(fan[2 * i], fan[2 * i + 1]) for i in range(nl.value)]
+        self.grids = [(grids[3 * i], grids[3 * i + 1], grids[3 * i + 2]) for i in range(4)]
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.fsi_pc_destroy(h)
+            self.handle = None
+
+
+def fsi_pc_create(mesh: Mesh, block: int = 0, n_pairs_cap: int = 0, linear: bool = False,
+                  modulate: bool = False) -> PC:
+    h = C.c_void_p()
+    d = fsi_pc_desc(block, n_pairs_cap, 1 if linear else 0, 1 if modulate else 0)
+    _check(lib().fsi_pc_create(mesh.handle, C.byref(d), C.byref(h)))
+    return PC(h, mesh)
+
+
+def _f32_host(a):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def fsi_pc_set_weights(pc: PC, w):
+    a, p = _f32_host(w)
+    _check(lib().fsi_pc_set_weights(pc.handle, p, C.c_int64(a.size)))
+
+
+def fsi_pc_get_weights(pc: PC):
+    import numpy as np
+    a = np.zeros(pc.n_weights, dtype=np.float32)
+    _check(lib().fsi_pc_get_weights(pc.handle, a.ctypes.data_as(C.POINTER(C.c_float)), C.c_int64(a.size)))
+    return a
+
+
+def fsi_pc_set_norm(pc: PC, dbar, kc):
+    d = (C.c_double * 4)(*[float(v) for v in dbar])
+    k = (C.c_double * 4)(*[float(v) for v in kc])
+    _check(lib().fsi_pc_set_norm(pc.handle, d, k))
+
+
+def fsi_pc_get_norm(pc: PC):
+    d, k = (C.c_double * 4)(), (C.c_double * 4)()
+    _check(lib().fsi_pc_get_norm(pc.handle, d, k))
+    return list(d), list(k)
+
+
+def fsi_pc_forward(pc: PC, x_in, y):
+    """x_in: device int16 tensor holding the bfloat16 input planes; y: float32 [4][nn]."""
+    if x_in.dtype not in (torch.int16, torch.bfloat16) or y.dtype != torch.float32:
+        raise TypeError("fsi_pc_forward: x_in is bfloat16 (or its int16 bits), y float32")
+    _check(lib().fsi_pc_forward(pc.handle, _ptr(x_in), _ptr(y)))
+
+
+def fsi_pc_grad(pc: PC, x_in, target, grad) -> float:
+    if grad.dtype != torch.float32:
+        raise TypeError("fsi_pc_grad: grad is float32")
+    loss = C.c_double()
+    _check(lib().fsi_pc_grad(pc.handle, _ptr(x_in), _ptr(target), _ptr(grad), C.byref(loss)))
+    return loss.value
+
+
+def fsi_pc_apply(pc: PC, x, xn, xdn, r, z):
+    st = _state(x, xn, xdn)
+    _check(lib().fsi_pc_apply(pc.handle, C.byref(st), _dptr(r), _dptr(z)))
+
+
+def fsi_pc_add_pair(pc: PC, x, xn, xdn, r, e):
+    st = _state(x, xn, xdn)
+    _check(lib().fsi_pc_add_pair(pc.handle, C.byref(st), _dptr(r), _dptr(e)))
+
+
+def fsi_pc_pairs(pc: PC) -> int:
+    n = C.c_int32()
+    _check(lib().fsi_pc_pairs(pc.handle, C.byref(n)))
+    return n.value
+
+
+def fsi_pc_fit_norm(pc: PC):
+    _check(lib().fsi_pc_fit_norm(pc.handle))
+
+
+def fsi_pc_train(pc: PC, order, lr: float):
+    """Adam steps over the stored pairs order[0..]; returns the loss before each step."""
+    import numpy as np
+    o = np.ascontiguousarray(order, dtype=np.int32)
+    loss = np.zeros(o.size, dtype=np.float32)
+    _check(lib().fsi_pc_train(pc.handle, C.c_int32(o.size), C.c_float(lr),
+                              o.ctypes.data_as(C.POINTER(C.c_int32)),
+                              loss.ctypes.data_as(C.POINTER(C.c_float))))
+    return loss
+
+
+def fsi_set_pc(mesh: Mesh, pc):
+    _check(lib().fsi_set_pc(mesh.handle, pc.handle if pc is not None else None))

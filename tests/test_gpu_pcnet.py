@@ -1,0 +1,226 @@
+"""GPU parity of the learned preconditioner (csrc/pcnet.cu, tcgen05 convolutions)
+against the oracle network (oracle/pcnet.py) with bfloat16 rounding emulated at the
+same places, plus its training and its use in flexible GMRES.
+
+Tolerances: the tensor cores accumulate the bfloat16 products in float32 (not IEEE
+round-to-nearest at every addition) and the result is rounded once to bfloat16; the
+oracle accumulates in float64 and rounds via float32.  Roundings then differ where an
+accumulated value lies near a bfloat16 rounding boundary and the differences travel
+through the 15 layers: measured 0.7-1.7e-3 relative L2 on the network output (a float32
+numpy accumulation of the same network lands 2e-4 from the oracle), against O(1) for a
+wrong tap, channel or transposition.  The distance to the float64 network (the effect
+of bfloat16 itself, about 4e-3) is reported too."""
+import numpy as np
+import pytest
+
+from tests.gpu_helpers import DEV, Gpu, T
+from tests.helpers import desc_small
+
+pytestmark = pytest.mark.gpu
+
+import torch  # noqa: E402
+
+from oracle import bc, blocks, diag, pcnet as pn  # noqa: E402
+from oracle.fields import Problem, State  # noqa: E402
+from oracle.gmres import gmres as ogmres  # noqa: E402
+from paper_2402_10348_gb300 import fsi  # noqa: E402
+from workloads import he_normal_weights, random_state  # noqa: E402
+
+TOL_NET = 5e-3   # relative L2, GPU vs bf16-emulating oracle
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def to_planes(x):
+    """Oracle tensor [C, nz, ny, nx] of bfloat16 values -> the library's octet planes."""
+    C, nz, ny, nx = x.shape
+    b = (np.ascontiguousarray(x, dtype=np.float32).view(np.uint32) >> 16).astype(np.uint16)
+    b = np.ascontiguousarray(b.reshape(C // 8, 8, nz, ny, nx).transpose(0, 2, 3, 4, 1))
+    return torch.tensor(b.view(np.int16), device=DEV)
+
+
+def to_bf16_planar(t):
+    b = (np.ascontiguousarray(t, dtype=np.float32).view(np.uint32) >> 16).astype(np.uint16)
+    return torch.tensor(np.ascontiguousarray(b).view(np.int16).ravel(), device=DEV)
+
+
+def _setup(n, seed=0, n_fluid=1, n_solid=1, linear=False, modulate=False):
+    d = desc_small(n=n, n_fluid=n_fluid, n_solid=n_solid)
+    x1, xn, xdn = random_state(d, seed)
+    g = Gpu(d, x1, xn, xdn)
+    pc = fsi.fsi_pc_create(g.mesh, n_pairs_cap=4, linear=linear, modulate=modulate)
+    w = he_normal_weights(pc.fan, seed + 1, last_scale=1.0)
+    fsi.fsi_pc_set_weights(pc, w)
+    w32 = w.astype(np.float32).astype(np.float64)
+    shape = (d.nz + 1, d.ny + 1, d.nx + 1)
+    return d, g, pc, w32, shape, (x1, xn, xdn)
+
+
+def _valid_mask(d, shape):
+    vmask, _, pmask = bc.dirichlet(d)
+    m = np.stack([~vmask, ~vmask, ~vmask, ~pmask])
+    return m.reshape((4,) + shape)
+
+
+@pytest.mark.parametrize("n,linear", [((16, 16, 16), False), ((12, 20, 9), False), ((7, 5, 30), False),
+                                      ((12, 20, 9), True)])
+def test_forward_matches_oracle(n, linear):
+    d, g, pc, w, shape, _ = _setup(n, linear=linear)
+    assert pc.grids[0] == (d.nx + 1, d.ny + 1, d.nz + 1)
+    x = pn.bf16(np.random.default_rng(2).normal(size=(16,) + shape))
+    y = torch.zeros(4 * d.nn, dtype=torch.float32, device=DEV)
+    fsi.fsi_pc_forward(pc, to_planes(x), y)
+    torch.cuda.synchronize()
+    ref, _ = pn.forward(w, x, 4, quant="bf16", relu_on=not linear)
+    ref64, _ = pn.forward(w, x, 4, relu_on=not linear)
+    got = y.cpu().numpy().reshape(ref.shape)
+    err, err64 = rel(got, ref), rel(got, ref64)
+    print(f"forward {n}: vs bf16 oracle {err:.2e}, vs float64 network {err64:.2e}")
+    assert err <= TOL_NET and err64 <= 5e-2
+
+
+@pytest.mark.parametrize("n,linear", [((16, 16, 16), False), ((12, 20, 9), False), ((12, 20, 9), True)])
+def test_weight_gradient_matches_oracle(n, linear):
+    d, g, pc, w, shape, _ = _setup(n, seed=3, linear=linear)
+    rng = np.random.default_rng(4)
+    x = pn.bf16(rng.normal(size=(16,) + shape))
+    t = pn.bf16(rng.normal(size=(4,) + shape))
+    kc = np.array([0.5, 2.0, 1.0, 4.0])
+    fsi.fsi_pc_set_norm(pc, [1, 1, 1, 1], kc)
+    grad = torch.zeros(pc.n_weights, dtype=torch.float32, device=DEV)
+    loss = fsi.fsi_pc_grad(pc, to_planes(x), to_bf16_planar(t), grad)
+    mask = _valid_mask(d, shape)
+    y, cache = pn.forward(w, x, 4, quant="bf16", relu_on=not linear)
+    L, gy = pn.loss_and_grad_y(y, t / kc[:, None, None, None], mask)
+    ref = pn.backward(w, cache, gy, quant="bf16")
+    # the spread between float32- and float64-accumulated bf16 networks: how far
+    # rounding alone moves each layer's gradient (large for the coarse levels, whose
+    # few voxels make the gradient a short sum of rounded terms)
+    y2, cache2 = pn.forward(w, x, 4, quant="bf16-f32", relu_on=not linear)
+    ref32 = pn.backward(w, cache2, pn.loss_and_grad_y(y2, t / kc[:, None, None, None], mask)[1], quant="bf16-f32")
+    assert loss == pytest.approx(L, rel=1e-3)
+    got = grad.cpu().numpy().astype(np.float64)
+    off, errs, tols = 0, {}, {}
+    for (co, ci), (name, _, _) in zip(pc.fan, pn.layer_specs(16, 4)):
+        k = co * ci * 27
+        errs[name] = rel(got[off:off + k], ref[off:off + k])
+        tols[name] = 3.0 * rel(ref32[off:off + k], ref[off:off + k]) + TOL_NET
+        off += k
+    print("grad errors:", {k: f"{v:.2e} (tol {tols[k]:.1e})" for k, v in errs.items()})
+    assert all(errs[k] <= tols[k] for k in errs), errs
+
+
+@pytest.mark.parametrize("linear,modulate", [(False, False), (True, True)])
+def test_apply_matches_oracle_and_passes_dirichlet_rows(linear, modulate):
+    d, g, pc, w, shape, (x1, xn, xdn) = _setup((10, 9, 8), seed=5, n_fluid=2, n_solid=1, linear=linear,
+                                               modulate=modulate)
+    dbar, kc = [0.7, 0.8, 0.9, 1.3], [0.6, 0.5, 0.4, 2.0]
+    fsi.fsi_pc_set_norm(pc, dbar, kc)
+    r = np.random.default_rng(6).normal(size=(4, d.nn))
+    z = torch.zeros(4 * d.nn, dtype=torch.float64, device=DEV)
+    fsi.fsi_pc_apply(pc, *g.st(), T(r.ravel()), z)
+    torch.cuda.synchronize()
+    pb, st = Problem(d), State(x1, xn, xdn)
+    dvec = diag.block_diagonal(pb, st, "ns")
+    dinv = (1.0 / dvec).reshape((4,) + shape)
+    vmask, _, pmask = bc.dirichlet(d)
+    dirichlet = np.stack([vmask, vmask, vmask, pmask]).reshape((4,) + shape)
+    if modulate:
+        phases = [x1[4 + i].reshape(shape) for i in range(d.n_phase) if d.phases[i].solid]
+    else:
+        phases = [x1[4 + i].reshape(shape) for i in range(d.n_phase)]
+    ref = pn.pc_apply(w, r.reshape((4,) + shape), dinv, phases, dirichlet, np.array(dbar), np.array(kc),
+                      quant="bf16", relu_on=not linear, modulate=modulate)
+    got = z.cpu().numpy().reshape(ref.shape)
+    assert np.array_equal(got[dirichlet], r.reshape(ref.shape)[dirichlet])
+    assert rel(got, ref) <= TOL_NET
+
+
+def test_training_reduces_the_loss_on_a_fixed_pair():
+    """Adam on one stored pair (a smooth error e and r = J e): the loss falls."""
+    d, g, pc, w, shape, (x1, xn, xdn) = _setup((12, 12, 12), seed=7)
+    fsi.fsi_pc_set_weights(pc, he_normal_weights(pc.fan, 8))  # output layer scaled by 0.1
+    zz, yy, xx = np.meshgrid(*[np.linspace(0, 1, k) for k in shape], indexing="ij")
+    e = np.stack([np.sin(np.pi * (c + 1) * xx) * np.sin(np.pi * yy) * np.sin(np.pi * (2 - c % 2) * zz)
+                  for c in range(4)]).reshape(4, d.nn)
+    rr = torch.zeros(4 * d.nn, dtype=torch.float64, device=DEV)
+    fsi.fsi_jvp(g.mesh, fsi.FSI_BLOCK_NS, *g.st(), T(e.ravel()), rr)
+    fsi.fsi_pc_add_pair(pc, *g.st(), rr, T(e.ravel()))
+    assert fsi.fsi_pc_pairs(pc) == 1
+    fsi.fsi_pc_fit_norm(pc)
+    losses = fsi.fsi_pc_train(pc, np.zeros(100, dtype=np.int32), 2e-3)
+    print("loss", losses[:3], "->", losses[-3:])
+    assert np.all(np.isfinite(losses)) and losses[-10:].mean() < 0.7 * losses[:3].mean()
+
+
+def _lin_problem(n=(12, 12, 12), seed=9):
+    d = desc_small(n=n)
+    x1, xn, xdn = random_state(d, seed)
+    g = Gpu(d, x1, xn, xdn)
+    rhs = g.residual(fsi.FSI_BLOCK_NS, 4 * d.nn)
+    return d, g, rhs, (x1, xn, xdn)
+
+
+def test_fgmres_with_untrained_network_reaches_the_oracle_solution():
+    """Whatever the network does, flexible GMRES must reach the tolerance (with the
+    Jacobi fallback if it stalls): the oracle's own operator confirms the residual,
+    and the solution matches the oracle's float64 GMRES solution to 1e-6."""
+    d, g, rhs, (x1, xn, xdn) = _lin_problem()
+    pc = fsi.fsi_pc_create(g.mesh)
+    fsi.fsi_pc_set_weights(pc, he_normal_weights(pc.fan, 11))
+    fsi.fsi_set_pc(g.mesh, pc)
+    sol = torch.zeros(4 * d.nn, dtype=torch.float64, device=DEV)
+    pb, st = Problem(d), State(x1, xn, xdn)
+    A = lambda v: blocks.jvp(pb, st, "ns", v)  # noqa: E731
+    dinv = 1.0 / diag.block_diagonal(pb, st, "ns")
+    ref, _, _ = ogmres(A, rhs, dinv, m=30, rtol=1e-13, max_iter=8000)
+    for prec in (fsi.FSI_PREC_FP64, fsi.FSI_PREC_FP32_IR):
+        o = fsi.solve_opts(m=30, rtol=1e-12, max_iter=6000, precond=fsi.FSI_PC_LEARNED, precision=prec,
+                           ir_inner_rtol=1e-3, ir_max=60)
+        info = fsi.fsi_gmres(g.mesh, fsi.FSI_BLOCK_NS, *g.st(), T(rhs), sol, o)
+        x = sol.cpu().numpy()
+        print(f"precision {prec}: iterations {info.iterations} fallback {info.fallback} rel {info.rel_res:.2e}")
+        assert info.rel_res <= 1e-12
+        assert np.linalg.norm(rhs - A(x)) / np.linalg.norm(rhs) <= 2e-12
+        assert rel(x, ref) <= 1e-6
+
+
+def test_harvested_pairs_train_a_network_that_beats_jacobi():
+    """What the trained network gains: on the 32^3 cavity's NS block, a linear U-Net
+    trained on pairs harvested from Jacobi solves (refinement checkpoints and Arnoldi
+    steps) lets flexible GMRES(64) reach rel-res 1e-8 in far fewer iterations than
+    Jacobi GMRES(64) on a right-hand side it has not seen; both reach the tolerance
+    (the flexible solve may hand its last stretch to the Jacobi fallback)."""
+    from workloads import cavity
+    d = cavity(32).desc
+    x1, xn, xdn = random_state(d, 1, amp_v=0.3)
+    g = Gpu(d, x1, xn, xdn)
+    rhs = g.residual(fsi.FSI_BLOCK_NS, 4 * d.nn)
+    pc = fsi.fsi_pc_create(g.mesh, n_pairs_cap=512, linear=True, modulate=True)
+    fsi.fsi_pc_set_weights(pc, he_normal_weights(pc.fan, 3))
+    fsi.fsi_set_pc(g.mesh, pc)
+    rng = np.random.default_rng(0)
+    sol = torch.zeros(4 * d.nn, dtype=torch.float64, device=DEV)
+    o = fsi.solve_opts(m=64, rtol=1e-9, max_iter=6000, precond=fsi.FSI_PC_JACOBI,
+                       precision=fsi.FSI_PREC_FP32_IR, ir_inner_rtol=0.1, ir_max=40)
+    o.flags |= fsi.FSI_HARVEST
+    for k in range(8):
+        b = rhs * (1.0 + 0.3 * rng.normal(size=rhs.size))
+        fsi.fsi_gmres(g.mesh, fsi.FSI_BLOCK_NS, *g.st(), T(b), sol, o, allow_noconv=True)
+    npairs = fsi.fsi_pc_pairs(pc)
+    assert npairs >= 100
+    fsi.fsi_pc_fit_norm(pc)
+    losses = fsi.fsi_pc_train(pc, rng.integers(0, npairs, size=6000), 2e-4)
+    print(f"pairs {npairs}; relative loss {losses[:50].mean():.3f} -> {losses[-200:].mean():.3f}")
+    assert losses[-200:].mean() < 0.5
+    b = rhs * (1.0 + 0.3 * rng.normal(size=rhs.size))
+    base = fsi.solve_opts(m=64, rtol=1e-8, max_iter=8000)
+    jac = fsi.fsi_gmres(g.mesh, fsi.FSI_BLOCK_NS, *g.st(), T(b), sol, base, allow_noconv=True)
+    base.precond = fsi.FSI_PC_LEARNED
+    lrn = fsi.fsi_gmres(g.mesh, fsi.FSI_BLOCK_NS, *g.st(), T(b), sol, base, allow_noconv=True)
+    print(f"iterations: Jacobi {jac.iterations} (rel {jac.rel_res:.1e}), "
+          f"learned {lrn.iterations} (rel {lrn.rel_res:.1e}, fallback {lrn.fallback})")
+    assert lrn.rel_res <= 1e-8 and jac.rel_res <= 1e-8
+    assert lrn.iterations < 0.6 * jac.iterations

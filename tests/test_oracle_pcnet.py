@@ -108,16 +108,17 @@ def test_network_is_positively_homogeneous():
     assert pn.n_weights(16, 4) == w.size == 6912 * 11 + 3 * 13824 + 1728
 
 
-def test_gradient_matches_finite_differences_per_layer():
+@pytest.mark.parametrize("relu_on", [True, False])
+def test_gradient_matches_finite_differences_per_layer(relu_on):
     w, x = _tiny_net(shape=(9, 7, 5))
     t = _rng(5).normal(size=(4, 9, 7, 5))
     mask = _rng(6).random(size=(4, 9, 7, 5)) > 0.2
 
     def loss(wv):
-        y, _ = pn.forward(wv, x, 4)
+        y, _ = pn.forward(wv, x, 4, relu_on=relu_on)
         return pn.loss_and_grad_y(y, t, mask)[0]
 
-    y, cache = pn.forward(w, x, 4)
+    y, cache = pn.forward(w, x, 4, relu_on=relu_on)
     _, gy = pn.loss_and_grad_y(y, t, mask)
     g = pn.backward(w, cache, gy)
     off = 0
@@ -192,3 +193,21 @@ def test_fgmres_exact_inverse_and_varying_preconditioner():
     x, it, rel = og.fgmres(lambda v: A @ v, b, lambda v: (0.5 + rng.random(40)) * v, m=8,
                            rtol=1e-10, max_iter=400)
     assert rel <= 1e-10 and np.allclose(x, np.linalg.solve(A, b), rtol=1e-8)
+
+
+def test_linear_network_and_modulated_input_are_linear_in_r():
+    w, _ = _tiny_net(shape=(5, 5, 5))
+    rng = _rng(21)
+    shape = (4, 5, 5, 5)
+    r1, r2 = rng.normal(size=shape), rng.normal(size=shape)
+    dinv = rng.random(size=shape) + 0.5
+    dirichlet = np.zeros(shape, dtype=bool)
+    phases = [np.tanh(rng.normal(size=shape[1:]))]
+    dbar, kc = np.ones(4), np.ones(4)
+
+    def M(r):
+        return pn.pc_apply(w, r, dinv, phases, dirichlet, dbar, kc, relu_on=False, modulate=True)
+
+    assert np.allclose(M(r1 - 2.5 * r2), M(r1) - 2.5 * M(r2), rtol=1e-10, atol=1e-12)
+    x = pn.pc_input(r1, dinv, phases, dirichlet, dbar, 1.0, modulate=True)
+    assert np.allclose(x[4:8], x[:4] * 0.5 * (1 + phases[0]), rtol=1e-14) and np.all(x[8:] == 0)
