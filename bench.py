@@ -327,6 +327,8 @@ def run_gpu(args):
         learned = run_learned_arm(fsi, torch, mesh, pc, solve, step, (x, xn, xdn), snapshot, args, stream)
         learned["jacobi_s_per_timestep"] = round(ms / args.steps / 1e3, 5)
         learned["jacobi_ns_iters"] = [i.gmres_iters_ns for i in infos]
+        learned["jacobi_nl_iters"] = [i.nl_iters for i in infos]
+        learned["jacobi_max_ratio"] = [i.max_ratio for i in infos]
 
     e2e = None
     if not args.no_e2e:
@@ -408,7 +410,9 @@ def run_learned_arm(fsi, torch, mesh, pc, solve, step, state, snapshot, args, st
         "train_ms_per_step": round(1e3 * train_s / max(1, args.train_steps), 3),
         "relative_loss_first_last": [round(float(losses[:50].mean()), 4), round(float(losses[-200:].mean()), 4)],
         "s_per_timestep": round(ms / args.steps / 1e3, 5),
+        "nl_iters": [i.nl_iters for i in infos],
         "ns_iters": [i.gmres_iters_ns for i in infos],
+        "max_ratio": [i.max_ratio for i in infos],
         "worst_rel_res": max(i.worst_rel_res for i in infos),
         "stalled_solves": [i.stalled_solves for i in infos],
         "fallback_solves": [i.fallback_solves for i in infos],

@@ -304,6 +304,10 @@ typedef struct {
   int32_t modulate;     /* 1: input channels 4.. are s_c (1 + phi_s) / 2 for each
                            solid s (at most 3) instead of the indicators, so that a
                            linear network keeps z = M(r) linear in r               */
+  int32_t smooth;       /* 1: the output y is replaced by P R y before it is added
+                           (its high-frequency part, where the bfloat16 rounding
+                           noise sits, is dropped)                                  */
+  int32_t pad;
 } fsi_pc_desc;
 int fsi_pc_create(fsi_mesh* mesh, const fsi_pc_desc* desc, fsi_pc** out);
 int fsi_pc_destroy(fsi_pc* pc);

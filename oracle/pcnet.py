@@ -279,21 +279,28 @@ def pc_input(r, dinv, phases, dirichlet, dbar, rnorm, quant=None, modulate=False
     return _q(x, quant)
 
 
-def pc_output(r, dinv, dirichlet, y, dbar, kc, rnorm):
-    """z = D^{-1} r + (rnorm / sqrt(n_rows)) dbar_c kc_c y_c; z = r on Dirichlet rows."""
+def pc_output(r, dinv, dirichlet, y, dbar, kc, rnorm, smooth=False):
+    """z = D^{-1} r + (rnorm / sqrt(n_rows)) dbar_c kc_c y_c; z = r on Dirichlet rows.
+    smooth=True first replaces y by P R y (full weighting to the next coarser node grid
+    and Q1 interpolation back): that removes the high-frequency part of the network's
+    output, where its bfloat16 rounding noise lives and where the operator's large
+    eigenvalues would amplify it."""
     ncomp = r.shape[0]
+    if smooth:
+        coarse = tuple(k // 2 + 1 for k in y.shape[1:])
+        y = prolong(restrict(y, coarse), y.shape[1:])
     h = rnorm / np.sqrt(r.size)
     z = dinv * r + np.stack([h * dbar[c] * kc[c] * y[c] for c in range(ncomp)])
     return np.where(dirichlet, r, z)
 
 
-def pc_apply(w, r, dinv, phases, dirichlet, dbar, kc, quant=None, relu_on=True, modulate=False):
+def pc_apply(w, r, dinv, phases, dirichlet, dbar, kc, quant=None, relu_on=True, modulate=False, smooth=False):
     rnorm = float(np.linalg.norm(r))
     if rnorm == 0.0:
         return np.zeros_like(r)
     x = pc_input(r, dinv, phases, dirichlet, dbar, rnorm, quant, modulate)
     y, _ = forward(w, x, r.shape[0], quant, relu_on)
-    return pc_output(r, dinv, dirichlet, y, dbar, kc, rnorm)
+    return pc_output(r, dinv, dirichlet, y, dbar, kc, rnorm, smooth)
 
 
 def pair_target(r, e, dinv, dirichlet, dbar, rnorm):

@@ -635,12 +635,17 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& blk, const double* rhs, double* x,
       rel = bnorm > 0.0 ? std::sqrt(r2) / bnorm : 0.0;
       inf.refinements = k + 1;
       if (inf.iterations >= o.max_iter) break;
-      if (inner_pc && (inner_stalled || (rel > o.rtol && rel > 0.9 * prev))) {
-        inner_pc = nullptr;  // the network stalled: Jacobi GMRES finishes the solve
+      const bool no_gain = rel > o.rtol && rel > 0.9 * prev;
+      if (inner_pc && inner_stalled) {
+        // the network failed its job (the inner solve): Jacobi GMRES finishes the
+        // solve, retrying this refinement if it did not pay
+        inner_pc = nullptr;
         inf.fallback = 1;
-        continue;
+        if (no_gain) continue;
       }
-      if (rel > o.rtol && rel > 0.9 * prev) {
+      if (no_gain) {
+        // the inner solve reached its tolerance but the float64 residual did not
+        // follow: the attainable accuracy is reached
         inf.stalled = 1;
         break;
       }

@@ -428,6 +428,47 @@ __global__ void prolong_kernel(TView c, TView f, float s, TView add, TView mask)
   }
 }
 
+// float32 planar versions for the network output (nc channels [c][voxel]):
+// coarse = (1/8) P^T fine, fine = P coarse
+__global__ void restrict_f32_kernel(const float* __restrict__ f, Grid3 gf, float* __restrict__ c, Grid3 gc, int nc) {
+  const int64_t Vc = gc.nv(), Vf = gf.nv();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nc * Vc; i += (int64_t)gridDim.x * blockDim.x) {
+    const int ch = (int)(i / Vc);
+    const int64_t v = i - ch * Vc;
+    const int X = (int)(v % gc.nx), Y = (int)((v / gc.nx) % gc.ny), Z = (int)(v / ((int64_t)gc.nx * gc.ny));
+    float acc = 0.0f;
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int z = 2 * Z + dz;
+      if (z < 0 || z >= gf.nz) continue;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int y = 2 * Y + dy;
+        if (y < 0 || y >= gf.ny) continue;
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int x = 2 * X + dx;
+          if (x < 0 || x >= gf.nx) continue;
+          acc += f[ch * Vf + ((int64_t)z * gf.ny + y) * gf.nx + x] / (float)(1 << (abs(dx) + abs(dy) + abs(dz)));
+        }
+      }
+    }
+    c[i] = 0.125f * acc;
+  }
+}
+__global__ void prolong_f32_kernel(const float* __restrict__ c, Grid3 gc, float* __restrict__ f, Grid3 gf, int nc) {
+  const int64_t Vc = gc.nv(), Vf = gf.nv();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nc * Vf; i += (int64_t)gridDim.x * blockDim.x) {
+    const int ch = (int)(i / Vf);
+    const int64_t v = i - ch * Vf;
+    const int x = (int)(v % gf.nx), y = (int)((v / gf.nx) % gf.ny), z = (int)(v / ((int64_t)gf.nx * gf.ny));
+    const int xs[2] = {x >> 1, (x + 1) >> 1}, ys[2] = {y >> 1, (y + 1) >> 1}, zs[2] = {z >> 1, (z + 1) >> 1};
+    const int nxs = (x & 1) ? 2 : 1, nys = (y & 1) ? 2 : 1, nzs = (z & 1) ? 2 : 1;
+    float acc = 0.0f;
+    for (int a2 = 0; a2 < nzs; ++a2)
+      for (int a1 = 0; a1 < nys; ++a1)
+        for (int a0 = 0; a0 < nxs; ++a0) acc += c[ch * Vc + ((int64_t)zs[a2] * gc.ny + ys[a1]) * gc.nx + xs[a0]];
+    f[i] = acc / (float)(nxs * nys * nzs);
+  }
+}
+
 // ------------------------------------------------------------------ weight gradient
 // part[blk][co][ci][t] = sum over the CTA's voxels v of g[v][co] * x[v + t - 1][ci]
 template <int CIN>
@@ -956,6 +997,13 @@ int apply(fsi_pc* pc, const double* r, double rnorm, const double* dinv, double*
   FSI_LAUNCH(m, P_PC_AUX, (pc_pack_kernel<<<vgrid1(nn), 256, 0, m->stream>>>(
                               r, dinv, input_planes(pc), pc->modulate, pc->dmask, pc->ncomp, g, dbinv, nn, xin)));
   if ((rc = forward(pc, pc->xin))) return rc;
+  if (pc->smooth) {  // y <- P R y: keep the smooth part of the correction
+    const Grid3 g0 = pc->lv[0], g1 = pc->lv[1];
+    FSI_LAUNCH(m, P_PC_AUX, (restrict_f32_kernel<<<vgrid1(pc->cout * g1.nv()), 256, 0, m->stream>>>(
+                                pc->y32, g0, pc->ys1, g1, pc->cout)));
+    FSI_LAUNCH(m, P_PC_AUX, (prolong_f32_kernel<<<vgrid1(pc->cout * g0.nv()), 256, 0, m->stream>>>(
+                                pc->ys1, g1, pc->y32, g0, pc->cout)));
+  }
   const double h = rnorm / std::sqrt(nrows);
   const D4 dk = {{pc->dbar[0] * pc->kc[0], pc->dbar[1] * pc->kc[1], pc->dbar[2] * pc->kc[2],
                    pc->dbar[3] * pc->kc[3]}};
@@ -1076,6 +1124,7 @@ int fsi_pc_create(fsi_mesh* m, const fsi_pc_desc* d, fsi_pc** out) {
   pc->nph = m->N;
   pc->linear = d->linear != 0;
   pc->modulate = d->modulate != 0;
+  pc->smooth = d->smooth != 0;
   if (pc->modulate) {
     int ns = 0;
     for (int i = 0; i < m->N; ++i) ns += m->phases[i].is_solid ? 1 : 0;
@@ -1126,6 +1175,7 @@ int fsi_pc_create(fsi_mesh* m, const fsi_pc_desc* d, fsi_pc** out) {
   const int64_t V0 = pc->lv[0].nv();
   if ((rc = dalloc(&pc->xin, 2 * V0 * 8)) || (rc = dalloc(&pc->y32, (int64_t)pc->cout * V0)) ||
       (rc = dalloc(&pc->tmp, (int64_t)pc->ncomp * m->nn)) || (rc = dalloc(&pc->lpart, 8 * 1216)) ||
+      (rc = dalloc(&pc->ys1, (int64_t)pc->cout * pc->lv[1].nv())) ||
       (rc = dalloc(&pc->loss_dev, 1 << 16)) || (rc = dalloc(&pc->err, 1)))
     return fail(rc);
   // weight-gradient partials: room for the launch with the most CTAs over all levels
@@ -1172,7 +1222,7 @@ int fsi_pc_destroy(fsi_pc* pc) {
     cudaFree(pc->gd[l]), cudaFree(pc->ga[l]), cudaFree(pc->gb[l]), cudaFree(pc->gcat[l]), cudaFree(pc->ge[l]);
     cudaFree(pc->gx[l]);
   }
-  cudaFree(pc->xin), cudaFree(pc->y32), cudaFree(pc->tmp), cudaFree(pc->lpart), cudaFree(pc->loss_dev);
+  cudaFree(pc->xin), cudaFree(pc->y32), cudaFree(pc->ys1), cudaFree(pc->tmp), cudaFree(pc->lpart), cudaFree(pc->loss_dev);
   cudaFree(pc->err), cudaFree(pc->wpart), cudaFree(pc->ds_in), cudaFree(pc->ds_t), cudaFree(pc->ck);
   delete pc;
   return FSI_OK;

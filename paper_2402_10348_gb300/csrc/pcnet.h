@@ -13,7 +13,7 @@ constexpr int NLEVEL = 4;
 
 struct Grid3 {
   int nx, ny, nz;
-  int64_t nv() const { return (int64_t)nx * ny * nz; }
+  __host__ __device__ int64_t nv() const { return (int64_t)nx * ny * nz; }
 };
 // a channel-octet-planar bf16 tensor: voxel (x, y, z) of octet o at
 // p + (((oct0 + o) * nz + z) * ny + y) * nx + x) * 8
@@ -30,6 +30,7 @@ struct fsi_pc {
   int ncomp = 4, cout = 4, nph = 0;
   bool linear = false;    // no ReLU: the network is a linear operator
   bool modulate = false;  // input s_c (1 + phi_s) / 2 for the solids instead of phi
+  bool smooth = false;    // apply y <- P R y to the output
   fsi::pcn::Grid3 lv[fsi::pcn::NLEVEL];
   int lcin[fsi::pcn::NLAYER], lcout[fsi::pcn::NLAYER];
   int64_t woff[fsi::pcn::NLAYER];
@@ -47,6 +48,7 @@ struct fsi_pc {
            *gcat[fsi::pcn::NLEVEL] = {}, *ge[fsi::pcn::NLEVEL] = {}, *gx[fsi::pcn::NLEVEL] = {};
   uint16_t* xin = nullptr;    // packed network input of an apply
   float* y32 = nullptr;       // network output [cout][V0]
+  float* ys1 = nullptr;       // its restriction to level 1 [cout][V1] (smoothing)
   double* tmp = nullptr;      // [ncomp][nn]
   double* lpart = nullptr;    // reduction partials
   double* loss_dev = nullptr; // per-iteration training losses

@@ -309,7 +309,8 @@ def fsi_profile_read(mesh: Mesh) -> dict:
 
 # ------------------------------------------------------------------ learned preconditioner
 class fsi_pc_desc(C.Structure):
-    _fields_ = [("block", C.c_int32), ("n_pairs_cap", C.c_int32), ("linear", C.c_int32), ("modulate", C.c_int32)]
+    _fields_ = [("block", C.c_int32), ("n_pairs_cap", C.c_int32), ("linear", C.c_int32), ("modulate", C.c_int32),
+                ("smooth", C.c_int32), ("pad", C.c_int32)]
 
 
 class PC:
@@ -334,9 +335,9 @@ class PC:
 
 
 def fsi_pc_create(mesh: Mesh, block: int = 0, n_pairs_cap: int = 0, linear: bool = False,
-                  modulate: bool = False) -> PC:
+                  modulate: bool = False, smooth: bool = False) -> PC:
     h = C.c_void_p()
-    d = fsi_pc_desc(block, n_pairs_cap, 1 if linear else 0, 1 if modulate else 0)
+    d = fsi_pc_desc(block, n_pairs_cap, 1 if linear else 0, 1 if modulate else 0, 1 if smooth else 0, 0)
     _check(lib().fsi_pc_create(mesh.handle, C.byref(d), C.byref(h)))
     return PC(h, mesh)
 

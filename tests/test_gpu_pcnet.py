@@ -112,10 +112,16 @@ def test_weight_gradient_matches_oracle(n, linear):
     assert all(errs[k] <= tols[k] for k in errs), errs
 
 
-@pytest.mark.parametrize("linear,modulate", [(False, False), (True, True)])
-def test_apply_matches_oracle_and_passes_dirichlet_rows(linear, modulate):
-    d, g, pc, w, shape, (x1, xn, xdn) = _setup((10, 9, 8), seed=5, n_fluid=2, n_solid=1, linear=linear,
-                                               modulate=modulate)
+@pytest.mark.parametrize("linear,modulate,smooth", [(False, False, False), (True, True, False), (True, True, True)])
+def test_apply_matches_oracle_and_passes_dirichlet_rows(linear, modulate, smooth):
+    d = desc_small(n=(10, 9, 8), n_fluid=2, n_solid=1)
+    x1, xn, xdn = random_state(d, 5)
+    g = Gpu(d, x1, xn, xdn)
+    pc = fsi.fsi_pc_create(g.mesh, linear=linear, modulate=modulate, smooth=smooth)
+    w = he_normal_weights(pc.fan, 6, last_scale=1.0)
+    fsi.fsi_pc_set_weights(pc, w)
+    w = w.astype(np.float32).astype(np.float64)
+    shape = (d.nz + 1, d.ny + 1, d.nx + 1)
     dbar, kc = [0.7, 0.8, 0.9, 1.3], [0.6, 0.5, 0.4, 2.0]
     fsi.fsi_pc_set_norm(pc, dbar, kc)
     r = np.random.default_rng(6).normal(size=(4, d.nn))
@@ -132,7 +138,7 @@ def test_apply_matches_oracle_and_passes_dirichlet_rows(linear, modulate):
     else:
         phases = [x1[4 + i].reshape(shape) for i in range(d.n_phase)]
     ref = pn.pc_apply(w, r.reshape((4,) + shape), dinv, phases, dirichlet, np.array(dbar), np.array(kc),
-                      quant="bf16", relu_on=not linear, modulate=modulate)
+                      quant="bf16", relu_on=not linear, modulate=modulate, smooth=smooth)
     got = z.cpu().numpy().reshape(ref.shape)
     assert np.array_equal(got[dirichlet], r.reshape(ref.shape)[dirichlet])
     assert rel(got, ref) <= TOL_NET

@@ -211,3 +211,21 @@ def test_linear_network_and_modulated_input_are_linear_in_r():
     assert np.allclose(M(r1 - 2.5 * r2), M(r1) - 2.5 * M(r2), rtol=1e-10, atol=1e-12)
     x = pn.pc_input(r1, dinv, phases, dirichlet, dbar, 1.0, modulate=True)
     assert np.allclose(x[4:8], x[:4] * 0.5 * (1 + phases[0]), rtol=1e-14) and np.all(x[8:] == 0)
+
+
+def test_output_smoothing_removes_the_highest_frequency_and_keeps_linear_fields():
+    shape = (1, 9, 7, 5)
+    zz, yy, xx = np.meshgrid(*[np.arange(k, dtype=float) for k in shape[1:]], indexing="ij")
+    r = np.zeros(shape)
+    dinv = np.zeros(shape)
+    dirichlet = np.zeros(shape, dtype=bool)
+    one = np.ones(1)
+    lin = (0.3 + zz - 2 * yy + 0.5 * xx)[None]
+    # a linear field survives P R wherever the interpolation uses interior coarse
+    # nodes only (full weighting is unnormalised at the boundary); the checkerboard
+    # is removed there
+    z = pn.pc_output(r + 1.0, dinv, dirichlet, lin, one, one, np.sqrt(r.size), smooth=True)
+    assert np.allclose(z[0, 2:-2, 2:-2, 2:-2], lin[0, 2:-2, 2:-2, 2:-2], atol=1e-12)
+    checker = ((-1.0) ** (zz + yy + xx))[None]
+    z = pn.pc_output(r + 1.0, dinv, dirichlet, checker, one, one, np.sqrt(r.size), smooth=True)
+    assert np.abs(z[0, 2:-2, 2:-2, 2:-2]).max() < 1e-12
