@@ -46,9 +46,12 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner arm")
     p.add_argument("--train-steps", type=int, default=3000)
-    p.add_argument("--case", default="step", choices=["step", "solve"],
+    p.add_argument("--case", default="step", choices=["step", "solve", "pcnet", "batch"],
                    help="solve: only a fixed 40-iteration float32-IR NS GMRES solve at 64^3 (a short, "
-                        "repeatable launch sequence for ncu captures); prints no JSON")
+                        "repeatable launch sequence for ncu captures); pcnet: learned-preconditioner "
+                        "applies and training steps at 64^3 with per-kernel timing (JSON on stdout); "
+                        "batch: 64 uneven cavity instances, batched launches against per-instance "
+                        "launches (JSON on stdout)")
     return p.parse_args()
 
 
@@ -72,6 +75,176 @@ def run_solve_case():
                                         ir_inner_rtol=1e-30), allow_noconv=True)
     torch.cuda.synchronize()
     print(f"solve case: {info.iterations} iterations")
+
+
+def pc_flops_per_forward(grids, fan):
+    """Tensor-core flops of one network forward: 2 x voxels x 27 x in x out channels
+    per convolution, with the 16-wide MMA the kernels issue (the output layer's 4
+    channels are padded to 16)."""
+    lv = {"enc0": 0, "enc1": 1, "enc2": 2, "bot": 3, "dec2": 2, "dec1": 1, "dec0": 0, "out": 0}
+    names = ["enc0a", "enc0b", "enc1a", "enc1b", "enc2a", "enc2b", "bota", "botb", "dec2a", "dec2b", "dec1a",
+             "dec1b", "dec0a", "dec0b", "out"]
+    tot = 0.0
+    for name, (co, ci) in zip(names, fan):
+        key = name[:-1] if name != "out" else "out"
+        nx, ny, nz = grids[lv[key]]
+        tot += 2.0 * nx * ny * nz * 27 * ci * 16
+    return tot
+
+
+def run_pcnet_case(applies: int = 20, train_steps: int = 20):
+    """The learned preconditioner at 64^3: network applies (pack, 15 tcgen05 convolutions,
+    restrictions/prolongations, unpack) and training steps, timed by the library's
+    event profiler; the short launch sequence the convolution profile was captured on."""
+    import numpy as np
+    import torch
+    from paper_2402_10348_gb300 import fsi
+    from workloads import cavity64, he_normal_weights
+    wl = cavity64()
+    d = wl.desc
+    dev = torch.device("cuda", 0)
+    mesh = fsi.fsi_create_mesh(d)
+    stream = torch.cuda.current_stream()
+    fsi.fsi_set_stream(mesh, stream)
+    x, xn, xdn = initial_state(fsi, mesh, wl, torch, dev)
+    pc = fsi.fsi_pc_create(mesh, n_pairs_cap=2, linear=True, modulate=True)
+    fsi.fsi_pc_set_weights(pc, he_normal_weights(pc.fan, 3))
+    g = torch.Generator(device=dev).manual_seed(0)
+    r = torch.randn(4 * d.nn, dtype=torch.float64, device=dev, generator=g)
+    z = torch.zeros_like(r)
+    for _ in range(3):
+        fsi.fsi_pc_apply(pc, x, xn, xdn, r, z)
+    fsi.fsi_profile(mesh, True)
+    for _ in range(applies):
+        fsi.fsi_pc_apply(pc, x, xn, xdn, r, z)
+    prof_apply = fsi.fsi_profile_read(mesh)
+    fsi.fsi_profile(mesh, False)
+    # training steps on one stored pair (a product of the operator)
+    e = torch.randn(4 * d.nn, dtype=torch.float64, device=dev, generator=g)
+    fsi.fsi_jvp(mesh, fsi.FSI_BLOCK_NS, x, xn, xdn, e, r)
+    fsi.fsi_pc_add_pair(pc, x, xn, xdn, r, e)
+    fsi.fsi_pc_fit_norm(pc)
+    fsi.fsi_pc_train(pc, np.zeros(3, dtype=np.int32), 1e-4)
+    fsi.fsi_profile(mesh, True)
+    fsi.fsi_pc_train(pc, np.zeros(train_steps, dtype=np.int32), 1e-4)
+    prof_train = fsi.fsi_profile_read(mesh)
+    fsi.fsi_profile(mesh, False)
+    pk = peaks()
+    fl = pc_flops_per_forward(pc.grids, pc.fan)
+    conv = prof_apply["pc_conv"]
+    tflops = fl * applies / (conv[1] / 1e3) / 1e12
+    out = {"case": "pcnet", "workload": WORKLOAD, "grids": pc.grids, "applies": applies,
+           "ms_per_apply": {k: round(v[1] / applies, 4) for k, v in prof_apply.items() if v[0] > 0},
+           "conv_launches_per_apply": conv[0] / applies,
+           "conv_tflops": round(tflops, 2), "bf16_peak_tflops": pk.get("bf16_tflops"),
+           "conv_tensor_frac": round(tflops / pk["bf16_tflops"], 4) if pk.get("bf16_tflops") else None,
+           "train_steps": train_steps,
+           "ms_per_train_step": {k: round(v[1] / train_steps, 4) for k, v in prof_train.items() if v[0] > 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_batch_case(count: int = 64, reps: int = 5):
+    """64 independent cavities of uneven size (16^3 .. 48^3): the float32 NS operator
+    applied to all of them in one persistent launch against one launch per instance,
+    and the NS solve (Jacobi GMRES(64), float32 operator in float64 refinement, rel-res
+    1e-8) batched with a captured restart cycle against one fsi_gmres per instance."""
+    import torch
+    from paper_2402_10348_gb300 import fsi
+    from workloads import cavity_batch
+    dev = torch.device("cuda", 0)
+    wls = cavity_batch(count)
+    stream = torch.cuda.Stream()
+    meshes, states, rhs = [], [], []
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for wl in wls:
+            m = fsi.fsi_create_mesh(wl.desc)
+            fsi.fsi_set_stream(m, stream)
+            st = initial_state(fsi, m, wl, torch, dev)
+            r = torch.zeros(4 * wl.desc.nn, dtype=torch.float64, device=dev)
+            fsi.fsi_residual(m, fsi.FSI_BLOCK_NS, *st, r)
+            meshes.append(m)
+            states.append(st)
+            rhs.append(-r)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    b = fsi.fsi_batch_create(meshes, block=fsi.FSI_BLOCK_NS, m=64)
+    nodes = sum(wl.desc.nn for wl in wls)
+    dof = 4 * nodes
+    flags = fsi.FSI_ELASTIC_AUG | fsi.FSI_FP32
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        tm, gm, tuned_us = fsi.fsi_batch_autotune(b, states, flags)
+        torch.cuda.synchronize()
+        tune_s = time.perf_counter() - t0
+    g = torch.Generator(device=dev).manual_seed(0)
+    dx = torch.randn(dof, dtype=torch.float64, device=dev, generator=g)
+    y = torch.zeros_like(dx)
+    parts = [dx[b.offsets[i]:b.offsets[i + 1]] for i in range(count)]
+    outs = [y[b.offsets[i]:b.offsets[i + 1]] for i in range(count)]
+
+    def timed(fn, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            fn()
+            e0.record(stream)
+            for _ in range(n):
+                fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    def per_instance_jvp():
+        for i, m in enumerate(meshes):
+            fsi.fsi_jvp(m, fsi.FSI_BLOCK_NS, *states[i], parts[i], outs[i], flags)
+
+    ms_single = timed(per_instance_jvp, reps)
+    ms_batch = timed(lambda: fsi.fsi_batch_jvp(b, states, dx, y, flags), reps)
+    # the solves
+    opts = fsi.solve_opts(m=64, rtol=1e-8, max_iter=3000, precision=fsi.FSI_PREC_FP32_IR, ir_inner_rtol=1e-3,
+                          ir_max=30)
+    rhs_all = torch.cat(rhs).contiguous()
+    xb = torch.zeros_like(rhs_all)
+    sols = [torch.zeros_like(r) for r in rhs]
+
+    def per_instance_solve():
+        its = []
+        for i, m in enumerate(meshes):
+            its.append(fsi.fsi_gmres(m, fsi.FSI_BLOCK_NS, *states[i], rhs[i], sols[i], opts,
+                                     allow_noconv=True).iterations)
+        return its
+
+    def batched_solve():
+        return [i.iterations for i in fsi.fsi_batch_gmres(b, states, rhs_all, xb, opts, allow_noconv=True)]
+
+    res = {}
+    for name, fn in (("per_instance", per_instance_solve), ("batched_graph", batched_solve)):
+        with torch.cuda.stream(stream):
+            fn()  # warm-up: workspaces, graph capture
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            its = fn()
+            torch.cuda.synchronize()
+        res[name] = {"s": round(time.perf_counter() - t0, 4), "iterations_total": int(sum(its)),
+                     "iterations_max": int(max(its))}
+    fsi.fsi_batch_set_graph(b, False)
+    with torch.cuda.stream(stream):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its = batched_solve()
+        torch.cuda.synchronize()
+    res["batched_no_graph"] = {"s": round(time.perf_counter() - t0, 4), "iterations_total": int(sum(its))}
+    diff = max(float(torch.linalg.norm(xb[b.offsets[i]:b.offsets[i + 1]] - sols[i]) /
+                     max(float(torch.linalg.norm(sols[i])), 1e-300)) for i in range(count))
+    out = {"case": "batch", "instances": count, "nodes": nodes, "dof_ns": dof,
+           "sizes": sorted(int(wl.desc.nx) for wl in wls), "setup_s": round(setup_s, 2),
+           "autotune": {"target_mult": tm, "grid_mult": gm, "best_us": round(tuned_us, 1), "s": round(tune_s, 3)},
+           "ns_jvp_f32": {"per_instance_ms": round(ms_single, 4), "batched_ms": round(ms_batch, 4),
+                          "per_instance_gdofs": round(dof / ms_single / 1e6, 3),
+                          "batched_gdofs": round(dof / ms_batch / 1e6, 3), "speedup": round(ms_single / ms_batch, 3),
+                          "launches_per_instance_arm": count, "launches_batched": 2},
+           "ns_solve_fp32ir_rtol1e-8": res, "max_solution_difference": diff}
+    print(json.dumps(out), flush=True)
 
 
 def dist_env():
@@ -178,6 +351,8 @@ def peaks():
         "hbm_src": "measured" if "hbm_gbs" in pk else "fallback",
         "fp32_tflops": 152 * 128 * 2 * sm_mhz * 1e6 / 1e12,
         "fp64_tflops": 152 * 2 * 2 * sm_mhz * 1e6 / 1e12,
+        "bf16_tflops": pk.get("bf16_tflops", 1900.0),
+        "bf16_src": "measured (cuBLAS bf16 burst)" if "bf16_tflops" in pk else "fallback",
     }
 
 
@@ -515,6 +690,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.case == "pcnet":
+        run_pcnet_case()
+    elif args.case == "batch":
+        run_batch_case()
     elif args.case == "solve":
         run_solve_case()
     else:

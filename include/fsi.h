@@ -343,6 +343,44 @@ int fsi_pc_train(fsi_pc* pc, int32_t iters, float lr, const int32_t* order_host,
 /* attaches pc to its mesh for FSI_PC_LEARNED and FSI_HARVEST (NULL detaches) */
 int fsi_set_pc(fsi_mesh* mesh, fsi_pc* pc);
 
+/* --------------------------------------------------------------- batched instances
+ * (no counterpart in the paper, which treats one problem at a time.)  Many
+ * independent meshes of uneven size solved together: one persistent launch applies
+ * the block operator of every instance (its CTAs walk a list of (instance, tile)
+ * items), and GMRES runs for all instances in lock-step with per-instance Arnoldi
+ * state on the device; an instance that reaches its tolerance stops on the device
+ * without a host round trip.  One restart cycle of the inner solve is captured as a
+ * CUDA graph and replayed when the meshes' stream is not the legacy default stream.
+ * Block vectors are concatenated: instance i owns [offsets[i], offsets[i+1]).
+ * The meshes must share one device and one stream; they stay owned by the caller and
+ * must outlive the batch. */
+typedef struct fsi_batch fsi_batch;
+/* block: the same block id for every instance (FSI_BLOCK_NS, FSI_BLOCK_AC(i),
+ * FSI_BLOCK_B(s)); m: restart length (1..64) of fsi_batch_gmres.  The launch shape
+ * comes from the autotuner cache if it holds this set of instances. */
+int fsi_batch_create(fsi_mesh* const* meshes, int32_t n, int32_t block, int32_t m, fsi_batch** out);
+int fsi_batch_destroy(fsi_batch* batch);
+/* offsets: [n+1]; target_mult, grid_mult: the launch shape (tiles ~ target_mult x 152,
+ * persistent CTAs = grid_mult x 152); launches: kernels launched by the batch so far
+ * (a replayed graph counts its nodes).  Outputs are nullable. */
+int fsi_batch_layout(const fsi_batch* batch, int64_t* offsets, int32_t* target_mult, int32_t* grid_mult,
+                     int64_t* launches);
+/* y = J_i(states[i]) dx for every instance, one launch (flags as in fsi_jvp) */
+int fsi_batch_jvp(fsi_batch* batch, const fsi_state* states, const double* dx, double* y, uint32_t flags);
+/* fsi_gmres for every instance (Jacobi or no preconditioner; FSI_PREC_FP64 or
+ * FSI_PREC_FP32_IR; opts.m must be the batch's m).  infos: [n], nullable.  Returns
+ * FSI_ENOCONV if some instance misses rtol (its x holds the last iterate). */
+int fsi_batch_gmres(fsi_batch* batch, const fsi_state* states, const double* rhs, double* x,
+                    const fsi_solve_opts* opts, fsi_solve_info* infos);
+/* the project's autotuner: times the batched operator apply over candidate launch
+ * shapes (target_mult in {1,2,4,8} x grid_mult in {1,2,4}), keeps the fastest and
+ * appends it to the cache file ($FSI_AUTOTUNE_CACHE, else
+ * $HOME/.cache/fsi_gb300_autotune.txt) under a key of the instance shapes. */
+int fsi_batch_autotune(fsi_batch* batch, const fsi_state* states, uint32_t flags, int32_t* target_mult,
+                       int32_t* grid_mult, double* best_us);
+/* 0: launch the restart cycles directly instead of through the captured graph */
+int fsi_batch_set_graph(fsi_batch* batch, int32_t use_graph);
+
 /* --------------------------------------------------------------- measurement
  * (no counterpart in the paper: timing support for the benchmark)
  * fsi_profile(mesh, 1) starts recording a CUDA event pair around every kernel the

@@ -9,6 +9,8 @@
 #include "../../include/fsi.h"
 #include "ops.cuh"
 
+struct fsi_batch;
+
 namespace fsi {
 // Kernel classes of the event profiler (fsi_profile).
 enum ProfClass {
@@ -24,6 +26,18 @@ struct Profiler {
   std::vector<cudaEvent_t> ev;  // pool of event pairs
   std::vector<int> cls;         // class of each recorded pair
   int used = 0;                 // pairs recorded since the last harvest
+};
+// Records the operator structs that the launchers would launch, instead of
+// launching them (batched launches, batch.cu): one struct per instance, all of one
+// type, replayed by `launch` as a single persistent launch over every instance.
+struct BatchRec {
+  std::vector<unsigned char> bytes;  // concatenated operator structs
+  size_t op_size = 0;
+  int count = 0;
+  int cls = 0;
+  size_t smem = 0;                   // largest dynamic shared memory of the records
+  int (*launch)(fsi_batch* b, const void* ops_dev, size_t smem, int cls, int use_active) = nullptr;
+  void* (*upload)(const BatchRec& r) = nullptr;
 };
 }  // namespace fsi
 
@@ -74,6 +88,7 @@ struct fsi_mesh {
   double* Z = nullptr;       // [m][n] FGMRES preconditioned directions
   int64_t Z_n = 0;
   fsi_pc* pc = nullptr;      // attached learned preconditioner (NS block), not owned
+  fsi::BatchRec* rec = nullptr;  // non-null: operator launches are recorded, not run
   // counters (step info)
   int64_t applies = 0;
   int64_t dof_applied = 0;

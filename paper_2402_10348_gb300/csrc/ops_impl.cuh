@@ -28,13 +28,59 @@ inline void put<double>(Fields& F, int i, const double* p) { F.d[i] = p; F.f[i] 
 template <>
 inline void put<float>(Fields& F, int i, const float* p) { F.f[i] = p; F.d[i] = nullptr; }
 
+constexpr size_t SMEM_LIMIT = 232448;
+
 inline void fill_common(const fsi_mesh* m, double rh[3], double* W) {
   rh[0] = 1.0 / m->g.hx; rh[1] = 1.0 / m->g.hy; rh[2] = 1.0 / m->g.hz;
   *W = m->g.hx * m->g.hy * m->g.hz / 8.0;
 }
 
+int batch_launch_tiles_impl(fsi_batch* b, const void* ops_dev, size_t smem, int cls, int use_active,
+                            const void* kernel);
+
+template <class Op>
+int launch_batched(fsi_batch* b, const void* ops_dev, size_t smem, int cls, int use_active);
+
+template <class Op>
+void* upload_ops(const BatchRec& r) {
+  void* d = nullptr;
+  if (cudaMalloc(&d, r.bytes.size()) != cudaSuccess) return nullptr;
+  if (cudaMemcpy(d, r.bytes.data(), r.bytes.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    return nullptr;
+  }
+  return d;
+}
+
+template <class Op>
+int record_op(BatchRec* r, const Op& op, int cls) {
+  if (r->count > 0 && (r->op_size != sizeof(Op) || r->launch != &launch_batched<Op>))
+    return set_error(FSI_EINVAL, "batch: instances need the same operator type (same block and pass count)");
+  r->op_size = sizeof(Op);
+  r->launch = &launch_batched<Op>;
+  r->upload = &upload_ops<Op>;
+  r->cls = cls;
+  r->smem = std::max(r->smem, tile_smem_bytes<Op>(op.nf));
+  const unsigned char* p = reinterpret_cast<const unsigned char*>(&op);
+  r->bytes.insert(r->bytes.end(), p, p + sizeof(Op));
+  ++r->count;
+  return FSI_OK;
+}
+
+template <class Op>
+int launch_batched(fsi_batch* b, const void* ops_dev, size_t smem, int cls, int use_active) {
+  static size_t configured = 0;
+  if (configured < smem) {
+    FSI_CUDA(cudaFuncSetAttribute(tile_batch_kernel<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured = smem;
+  }
+  return batch_launch_tiles_impl(b, ops_dev, smem, cls, use_active,
+                                 reinterpret_cast<const void*>(&tile_batch_kernel<Op>));
+}
+
 template <class Op>
 int run_tile(fsi_mesh* m, const Op& op, int cls) {
+  if (m->rec) return record_op(m->rec, op, cls);
   const size_t smem = tile_smem_bytes<Op>(op.nf);
   static size_t configured = 0;
   if (smem > configured) {
@@ -58,8 +104,6 @@ constexpr int op_class(int kind) {
                    : (MODE == 0 ? (kind == 0 ? P_NS_RES : (kind == 1 ? P_AC_RES : P_B_RES))
                                 : (kind == 0 ? P_NS_DIAG : (kind == 1 ? P_AC_DIAG : P_B_DIAG)));
 }
-
-constexpr size_t SMEM_LIMIT = 232448;
 
 // The increment of a product: float64 kernels read dx itself, float32 kernels the
 // float copy the caller made (m->dx32, same layout).

@@ -145,11 +145,10 @@ struct ConvCfg {
   static constexpr int WBYTES = 27 * KC * N * 32;           // packed B operand
   static constexpr int NCOLS = 2 * N;                       // two f32 accumulators
   static constexpr int HEAD = 128;                          // barriers, TMEM address
-  static constexpr int NATURAL = HEAD + WBYTES + NSLOT * SLOT;
-  // every A address the descriptors can form stays below this bound even with the
-  // leading and stride offsets exchanged (the largest row-group offset times 15)
-  static constexpr int GUARD = HEAD + WBYTES + NSLOT * SLOT + 15 * OCT_BYTES + 1024;
-  static constexpr int SMEM = GUARD;
+  // the largest A address a descriptor forms is the last slot's last octet plane
+  // (row group 15 of tap (2, 2) ends exactly at the plane's end), so the ring and
+  // the weights are the whole footprint
+  static constexpr int SMEM = HEAD + WBYTES + NSLOT * SLOT;
 };
 
 struct ConvArgs {
@@ -778,7 +777,9 @@ int launch_conv(fsi_pc* pc, const TView& in, const TView& out, const TView& mask
   }
   const int gx = (out.nx + TILE_X - 1) / TILE_X, gy = (out.ny + TILE_Y - 1) / TILE_Y;
   const int cols = gx * gy;
-  const int zc = std::max(1, (int)((int64_t)out.nz * cols / (2 * 152)));
+  // CTAs resident per SM (shared memory bound) x 152 SMs: enough z-chunks to fill them
+  const int per_sm = std::max(1, std::min(8, (227 * 1024) / (C::SMEM + 1024)));
+  const int zc = std::max(1, (int)((int64_t)out.nz * cols / (per_sm * 152)));
   const int gz = (out.nz + zc - 1) / zc;
   ConvArgs a{in, out, mask, out32, nreal, wpk, zc, relu, pc->err};
   FSI_LAUNCH(m, P_PC_CONV, (conv_mma_kernel<CIN, N><<<dim3(gx, gy, gz), CONV_THREADS, C::SMEM, m->stream>>>(a)));

@@ -169,18 +169,20 @@ __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_
 // computed from the planes ez and ez+1, the copies of plane ez+2 are in flight.
 __host__ __device__ constexpr int plane_slot(int kz) { return ((kz % 3) + 3) % 3; }
 
+// One CTA tile (bx, by, bz) of the z-marching element loop (the body of the single
+// and the batched launches).
 template <class Op>
-__global__ void __launch_bounds__(NTHREADS, Op::MINB) tile_kernel(const __grid_constant__ Op op, const Geom g) {
+__device__ __forceinline__ void tile_body(const Op& op, const Geom& g, int bx, int by, int bz,
+                                          unsigned char* smem_raw) {
   using T = typename Op::T;
   constexpr int NC = Op::NC;
   const int NS = op.nf;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* planes = reinterpret_cast<T*>(smem_raw);       // [3][NS][PP]
   T* contrib = planes + 3 * NS * PP;                // [NC*8][NTHREADS]
 
   const int t = threadIdx.x;
   const int tx = t % TX, ty = t / TX;
-  const int i0 = blockIdx.x * OX, j0 = blockIdx.y * OY, k0 = blockIdx.z * g.zc;
+  const int i0 = bx * OX, j0 = by * OY, k0 = bz * g.zc;
   const int ex = i0 - 1 + tx, ey = j0 - 1 + ty;
   const bool exy_ok = ex >= 0 && ex < g.nx && ey >= 0 && ey < g.ny;
   // owned node of this thread (local (tx+1, ty+1))
@@ -269,6 +271,28 @@ __global__ void __launch_bounds__(NTHREADS, Op::MINB) tile_kernel(const __grid_c
     // the contributions are rewritten only after the next iteration's first barrier
   }
   op.end_cta(red);
+}
+
+template <class Op>
+__global__ void __launch_bounds__(NTHREADS, Op::MINB) tile_kernel(const __grid_constant__ Op op, const Geom g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  tile_body(op, g, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+}
+
+// Batched launch: persistent CTAs walk a list of (instance, bx, by, bz) tiles over
+// many independent meshes; ops[i] and geoms[i] describe instance i.  Instances whose
+// active flag is 0 are skipped.
+template <class Op>
+__global__ void __launch_bounds__(NTHREADS, Op::MINB)
+    tile_batch_kernel(const Op* __restrict__ ops, const Geom* __restrict__ geoms, const int4* __restrict__ work,
+                      int nwork, const int* __restrict__ active) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const int4 it = work[w];
+    if (active && !active[it.x]) continue;
+    __syncthreads();  // the previous tile's shared-memory reads are done
+    tile_body(ops[it.x], geoms[it.x], it.y, it.z, it.w, smem_raw);
+  }
 }
 
 template <class Op>

@@ -109,7 +109,8 @@ EXPORTS = ["fsi_create_mesh", "fsi_destroy_mesh", "fsi_set_stream", "fsi_mesh_in
            "fsi_profile_read", "fsi_pc_create", "fsi_pc_destroy", "fsi_pc_layout", "fsi_pc_set_weights",
            "fsi_pc_get_weights", "fsi_pc_set_norm", "fsi_pc_get_norm", "fsi_pc_forward", "fsi_pc_grad",
            "fsi_pc_apply", "fsi_pc_add_pair", "fsi_pc_pairs", "fsi_pc_fit_norm", "fsi_pc_train", "fsi_set_pc",
-           "fsi_last_error"]
+           "fsi_batch_create", "fsi_batch_destroy", "fsi_batch_layout", "fsi_batch_jvp", "fsi_batch_gmres",
+           "fsi_batch_autotune", "fsi_batch_set_graph", "fsi_last_error"]
 
 _lib = None
 
@@ -420,3 +421,66 @@ def fsi_pc_train(pc: PC, order, lr: float):
 
 def fsi_set_pc(mesh: Mesh, pc):
     _check(lib().fsi_set_pc(mesh.handle, pc.handle if pc is not None else None))
+
+
+# ------------------------------------------------------------------ batched instances
+class Batch:
+    """Owns an fsi_batch handle; keeps its meshes alive."""
+
+    def __init__(self, handle, meshes):
+        self.handle = handle
+        self.meshes = list(meshes)
+        self.n = len(self.meshes)
+        off = (C.c_int64 * (self.n + 1))()
+        _check(lib().fsi_batch_layout(handle, off, None, None, None))
+        self.offsets = [off[i] for i in range(self.n + 1)]
+
+    def layout(self):
+        tm, gm, la = C.c_int32(), C.c_int32(), C.c_int64()
+        _check(lib().fsi_batch_layout(self.handle, None, C.byref(tm), C.byref(gm), C.byref(la)))
+        return tm.value, gm.value, la.value
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.fsi_batch_destroy(h)
+            self.handle = None
+
+
+def _states(states):
+    arr = (fsi_state * len(states))()
+    for i, (x, xn, xdn) in enumerate(states):
+        arr[i] = _state(x, xn, xdn)
+    return arr
+
+
+def fsi_batch_create(meshes, block: int = 0, m: int = 64) -> Batch:
+    arr = (C.c_void_p * len(meshes))(*[mm.handle.value if hasattr(mm.handle, "value") else mm.handle
+                                       for mm in meshes])
+    h = C.c_void_p()
+    _check(lib().fsi_batch_create(arr, C.c_int32(len(meshes)), C.c_int32(block), C.c_int32(m), C.byref(h)))
+    return Batch(h, meshes)
+
+
+def fsi_batch_jvp(batch: Batch, states, dx, y, flags: int = FSI_ELASTIC_AUG):
+    st = _states(states)
+    _check(lib().fsi_batch_jvp(batch.handle, st, _dptr(dx), _dptr(y), C.c_uint32(flags)))
+
+
+def fsi_batch_gmres(batch: Batch, states, rhs, sol, opts: fsi_solve_opts, allow_noconv=False):
+    st = _states(states)
+    infos = (fsi_solve_info * batch.n)()
+    _check(lib().fsi_batch_gmres(batch.handle, st, _dptr(rhs), _dptr(sol), C.byref(opts), infos),
+           allow=(FSI_ENOCONV,) if allow_noconv else ())
+    return list(infos)
+
+
+def fsi_batch_autotune(batch: Batch, states, flags: int = FSI_ELASTIC_AUG | FSI_FP32):
+    st = _states(states)
+    tm, gm, us = C.c_int32(), C.c_int32(), C.c_double()
+    _check(lib().fsi_batch_autotune(batch.handle, st, C.c_uint32(flags), C.byref(tm), C.byref(gm), C.byref(us)))
+    return tm.value, gm.value, us.value
+
+
+def fsi_batch_set_graph(batch: Batch, use_graph: bool):
+    _check(lib().fsi_batch_set_graph(batch.handle, C.c_int32(1 if use_graph else 0)))

@@ -1,0 +1,120 @@
+"""Batched instances (csrc/batch.cu): one persistent operator launch over many uneven
+meshes, lock-step GMRES with a captured restart cycle, and the autotuner.
+
+The batched operator evaluates every element and node sum in the same order as the
+single-mesh launch (only the assignment of tiles to CTAs differs); the two kernels are
+separate instantiations of one body, so the compiler may contract a different set of
+multiply-adds: results agree to a few ulps, not bit for bit.  Batched GMRES follows
+the same algorithm per instance; its solutions are checked against the residual of
+the per-instance operator and against per-instance solves (two solutions that both
+meet rel-res 1e-10 differ by up to the condition number times 1e-10)."""
+import numpy as np
+import pytest
+
+from tests.gpu_helpers import DEV, T
+from tests.helpers import desc_small
+
+pytestmark = pytest.mark.gpu
+
+import torch  # noqa: E402
+
+from paper_2402_10348_gb300 import fsi  # noqa: E402
+from workloads import cavity, random_state  # noqa: E402
+
+
+def _instances(sizes, seed=0):
+    descs = [cavity(n).desc for n in sizes] + [desc_small(n=(7, 11, 5)), desc_small(n=(9, 4, 13))]
+    stream = torch.cuda.Stream()
+    meshes, states = [], []
+    for k, d in enumerate(descs):
+        m = fsi.fsi_create_mesh(d)
+        fsi.fsi_set_stream(m, stream)
+        meshes.append(m)
+        states.append(tuple(T(a) for a in random_state(d, seed + k, amp_v=0.3)))
+    torch.cuda.synchronize()
+    return descs, meshes, states, stream
+
+
+def _concat(parts):
+    return torch.cat([p.reshape(-1) for p in parts]).contiguous()
+
+
+@pytest.mark.parametrize("flags", [fsi.FSI_ELASTIC_AUG, fsi.FSI_ELASTIC_AUG | fsi.FSI_FP32])
+@pytest.mark.parametrize("block", [fsi.FSI_BLOCK_NS, fsi.FSI_BLOCK_AC(1), fsi.FSI_BLOCK_B(0)])
+def test_batched_jvp_matches_per_instance(flags, block):
+    descs, meshes, states, stream = _instances([8, 12, 16, 10])
+    b = fsi.fsi_batch_create(meshes, block=block, m=30)
+    rng = np.random.default_rng(5)
+    dxs = [T(rng.normal(size=b.offsets[i + 1] - b.offsets[i])) for i in range(b.n)]
+    ys = []
+    with torch.cuda.stream(stream):
+        if block == fsi.FSI_BLOCK_AC(1):
+            for m in meshes:
+                fsi.fsi_set_ac_coeffs(m, 1, 0.37, 0.11)
+        for i, m in enumerate(meshes):
+            y = torch.zeros_like(dxs[i])
+            fsi.fsi_jvp(m, block, *states[i], dxs[i], y, flags)
+            ys.append(y)
+        yb = torch.zeros(b.offsets[-1], dtype=torch.float64, device=DEV)
+        launches0 = b.layout()[2]
+        fsi.fsi_batch_jvp(b, states, _concat(dxs), yb, flags)
+        launches1 = b.layout()[2]
+    torch.cuda.synchronize()
+    ref = _concat(ys)
+    err = float((yb - ref).abs().max() / ref.abs().max())
+    print(f"block {block} flags {flags}: max relative difference {err:.2e}")
+    assert err <= (1e-6 if flags & fsi.FSI_FP32 else 1e-13)
+    assert launches1 - launches0 <= 2  # one operator launch (+ the float copy)
+
+
+@pytest.mark.parametrize("precision", [fsi.FSI_PREC_FP64, fsi.FSI_PREC_FP32_IR])
+def test_batched_gmres_matches_per_instance_solves(precision):
+    descs, meshes, states, stream = _instances([8, 12, 16], seed=3)
+    b = fsi.fsi_batch_create(meshes, block=fsi.FSI_BLOCK_NS, m=30)
+    rhs = []
+    with torch.cuda.stream(stream):
+        for i, m in enumerate(meshes):
+            r = torch.zeros(b.offsets[i + 1] - b.offsets[i], dtype=torch.float64, device=DEV)
+            fsi.fsi_residual(m, fsi.FSI_BLOCK_NS, *states[i], r)
+            rhs.append(r)
+    torch.cuda.synchronize()
+    o = fsi.solve_opts(m=30, rtol=1e-10, max_iter=4000, precision=precision, ir_inner_rtol=1e-3, ir_max=60)
+    sols = []
+    with torch.cuda.stream(stream):
+        for i, m in enumerate(meshes):
+            x = torch.zeros_like(rhs[i])
+            fsi.fsi_gmres(m, fsi.FSI_BLOCK_NS, *states[i], rhs[i], x, o)
+            sols.append(x)
+        xb = torch.zeros(b.offsets[-1], dtype=torch.float64, device=DEV)
+        infos = fsi.fsi_batch_gmres(b, states, _concat(rhs), xb, o)
+        # the same solve without the captured graph: identical kernels, identical result
+        fsi.fsi_batch_set_graph(b, False)
+        xb2 = torch.zeros_like(xb)
+        fsi.fsi_batch_gmres(b, states, _concat(rhs), xb2, o)
+    torch.cuda.synchronize()
+    assert torch.equal(xb, xb2)
+    for i, m in enumerate(meshes):
+        xi = xb[b.offsets[i]:b.offsets[i + 1]]
+        assert infos[i].rel_res <= 1e-10
+        t = torch.zeros_like(xi)
+        with torch.cuda.stream(stream):
+            fsi.fsi_jvp(m, fsi.FSI_BLOCK_NS, *states[i], xi.contiguous(), t)
+        torch.cuda.synchronize()
+        assert float(torch.linalg.norm(rhs[i] - t) / torch.linalg.norm(rhs[i])) <= 1.5e-10
+        assert float(torch.linalg.norm(xi - sols[i]) / torch.linalg.norm(sols[i])) <= 1e-5
+
+
+def test_autotuner_picks_a_shape_and_caches_it(tmp_path, monkeypatch):
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("FSI_AUTOTUNE_CACHE", str(cache))
+    descs, meshes, states, stream = _instances([8, 12, 16, 20])
+    b = fsi.fsi_batch_create(meshes, block=fsi.FSI_BLOCK_NS, m=30)
+    with torch.cuda.stream(stream):
+        tm, gm, us = fsi.fsi_batch_autotune(b, states)
+    torch.cuda.synchronize()
+    assert tm in (1, 2, 4, 8) and gm in (1, 2, 4) and us > 0.0
+    assert b.layout()[:2] == (tm, gm)
+    line = cache.read_text().strip().splitlines()[-1].split()
+    assert (int(line[1]), int(line[2])) == (tm, gm)
+    b2 = fsi.fsi_batch_create(meshes, block=fsi.FSI_BLOCK_NS, m=30)  # the cache is read at creation
+    assert b2.layout()[:2] == (tm, gm)

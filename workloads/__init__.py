@@ -207,14 +207,15 @@ class Workload:
     k_max: int
 
 
-def _cavity(n: int, name: str, steps: int, k_max: int) -> Workload:
+def _cavity(n: int, name: str, steps: int, k_max: int, center: Vec3 = (0.6, 0.5, 0.5), radius: float = 0.2,
+            mu_L: float = 0.1) -> Workload:
     h = 1.0 / n
-    phases = [Phase(rho=1.0, mu=0.01), Phase(rho=1.0, mu=0.01, mu_L=0.1, solid=True)]
+    phases = [Phase(rho=1.0, mu=0.01), Phase(rho=1.0, mu=0.01, mu_L=mu_L, solid=True)]
     faces = [FaceBC(BC_DIRICHLET, (0.0, 0.0, 0.0), 0) for _ in range(5)]
     faces.append(FaceBC(BC_DIRICHLET, (1.0, 0.0, 0.0), 1))  # lid at z=1 wins on its edges
     desc = MeshDesc(n, n, n, 1.0, 1.0, 1.0, phases, (0.0, 0.0, 0.0), eps=1.5 * h,
                     eta=0.2, dt=0.01, rho_inf=0.0, c_i=36.0, faces=faces, pin_node=0)
-    surf = icosphere((0.6, 0.5, 0.5), 0.2, h)
+    surf = icosphere(center, radius, h)
     rules = [PhaseRule(RULE_COMPLEMENT), PhaseRule(RULE_SURFACE, surface=0)]
     g = max(1, n // 4)
     return Workload(name, desc, [surf], rules, (g, g, g), steps, k_max)
@@ -230,6 +231,21 @@ def cavity64() -> Workload:
 
 def cavity(n: int) -> Workload:
     return _cavity(n, f"cavity{n}", steps=5, k_max=5)
+
+
+def cavity_batch(count: int = 64, seed: int = 0) -> List[Workload]:
+    """Uneven independent cavity instances: cube size s ~ U{16, 24, 32, 40, 48}, sphere
+    centre ~ U[0.3, 0.7]^3, radius ~ U[0.1, 0.25], shear modulus 10^U[-2, 1]; instance
+    k draws from its own stream numpy.random.default_rng([seed, k])."""
+    out = []
+    for k in range(count):
+        rng = np.random.default_rng([seed, k])
+        n = int(rng.choice([16, 24, 32, 40, 48]))
+        c = tuple(float(v) for v in rng.uniform(0.3, 0.7, size=3))
+        r = float(rng.uniform(0.1, 0.25))
+        mu_L = float(10.0 ** rng.uniform(-2.0, 1.0))
+        out.append(_cavity(n, f"batch{k}_n{n}", steps=20, k_max=5, center=c, radius=r, mu_L=mu_L))
+    return out
 
 
 def falling(scale: int = 1) -> Workload:
