@@ -12,10 +12,11 @@
 // Arnoldi step j (D = diag(dinv)):
 //   z = D V_j;  w = J z   (w: a contiguous work vector written by the operator)
 //   h = V^T w and |w|^2 in one pass over V_0..V_j      (mdot_kernel)
-//   w -= V h and |w|^2 in one pass                        (upd_kernel)
-//   if |w_new| < |w_old| / sqrt(2): once more (classical Gram-Schmidt with the DGKS
-//   re-orthogonalization test; the second pass is launched always and exits at once
-//   when the device-side flag says it is not needed)
+//   w -= V h, |w|^2 and h2 = V^T w (the second pass's projections of the updated w)
+//   in one pass                                           (upd_dot_kernel)
+//   if |w_new| < |w_old| / sqrt(2): w -= V h2 (classical Gram-Schmidt with the DGKS
+//   re-orthogonalization test; that update is launched always and exits at once when
+//   the device-side flag says it is not needed)
 //   Givens rotation of the new Hessenberg column and the residual estimate on the
 //   device; V_{j+1} = w / |w| stored into its slot.
 // The host enqueues step j and only then waits for step j-1's residual estimate
@@ -155,6 +156,87 @@ __global__ void __launch_bounds__(VB) upd_kernel(double* __restrict__ w, const d
   block_reduce_store<1>(nrm, 1, part + blockIdx.x, 1);
 }
 
+// Pass-1 update fused with the pass-2 projections: w' = w - sum_{i<k} h_i V_i, the
+// partial |w'|^2 and the partial V_i . w' (i < k) of the updated vector, from one read
+// of the basis: a thread keeps the k basis values of its element in registers, uses
+// them for the update and then for the projections, and accumulates the projections
+// in its own shared-memory column; the columns are added once at the end.
+// KMAX: k rounded up to a multiple of 8.  Rows of part: i < k the projections, row k
+// the norm; part[row * G + cta].
+constexpr int UDB = 128;  // threads per CTA (two elements of each 256-element chunk)
+template <int KMAX>
+__global__ void __launch_bounds__(UDB) upd_dot_kernel(double* __restrict__ w, const double* __restrict__ V, int M1,
+                                                      int k, const double* __restrict__ h, int64_t n, double* part) {
+  extern __shared__ double sacc[];  // [KMAX + 1][UDB]
+  __shared__ double hs[KMAX];
+  const int t = threadIdx.x;
+  for (int i = t; i < KMAX; i += UDB) hs[i] = i < k ? h[i] : 0.0;
+  for (int i = 0; i <= KMAX; ++i) sacc[i * UDB + t] = 0.0;
+  __syncthreads();
+  const int G = gridDim.x;
+  const int64_t nch = (n + CH - 1) / CH;
+  const int64_t per = (nch + G - 1) / G;
+  const int64_t c0 = blockIdx.x * per, c1 = min(nch, c0 + per);
+  double nrm = 0.0;
+  for (int64_t c = c0; c < c1; ++c) {
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+      const int64_t j = c * CH + half * UDB + t;
+      if (j >= n) continue;
+      const double* blk = V + c * (int64_t)M1 * CH + half * UDB + t;
+      double v[KMAX];
+#pragma unroll
+      for (int i = 0; i < KMAX; ++i) v[i] = i < k ? blk[i * CH] : 0.0;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll
+      for (int i = 0; i < KMAX; i += 4) {
+        s0 += hs[i] * v[i];
+        s1 += hs[i + 1] * v[i + 1];
+        s2 += hs[i + 2] * v[i + 2];
+        s3 += hs[i + 3] * v[i + 3];
+      }
+      const double ww = w[j] - ((s0 + s1) + (s2 + s3));
+      w[j] = ww;
+      nrm += ww * ww;
+#pragma unroll
+      for (int i = 0; i < KMAX; ++i) sacc[i * UDB + t] += v[i] * ww;
+    }
+  }
+  sacc[KMAX * UDB + t] = nrm;
+  __syncthreads();
+  for (int i = t; i <= k; i += UDB) {
+    const int row = i < k ? i : KMAX;
+    double s = 0.0;
+    for (int q = 0; q < UDB; ++q) s += sacc[row * UDB + q];
+    part[(int64_t)i * G + blockIdx.x] = s;
+  }
+}
+
+template <int KMAX>
+static void launch_upd_dot(fsi_mesh* m, int G, double* w, const double* V, int M1, int k, const double* h,
+                           int64_t n) {
+  const size_t smem = sizeof(double) * (size_t)(KMAX + 1) * UDB;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(upd_dot_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  upd_dot_kernel<KMAX><<<G, UDB, smem, m->stream>>>(w, V, M1, k, h, n, m->partials_dot);
+}
+
+static void upd_dot(fsi_mesh* m, int G, double* w, const double* V, int M1, int k, const double* h, int64_t n) {
+  switch ((k + 7) / 8) {
+    case 1: launch_upd_dot<8>(m, G, w, V, M1, k, h, n); break;
+    case 2: launch_upd_dot<16>(m, G, w, V, M1, k, h, n); break;
+    case 3: launch_upd_dot<24>(m, G, w, V, M1, k, h, n); break;
+    case 4: launch_upd_dot<32>(m, G, w, V, M1, k, h, n); break;
+    case 5: launch_upd_dot<40>(m, G, w, V, M1, k, h, n); break;
+    case 6: launch_upd_dot<48>(m, G, w, V, M1, k, h, n); break;
+    case 7: launch_upd_dot<56>(m, G, w, V, M1, k, h, n); break;
+    default: launch_upd_dot<64>(m, G, w, V, M1, k, h, n); break;
+  }
+}
+
 // V_slot[j] = src[j] * scale, scale = 1/sqrt(*n2) (n2 != null) or 1/K->nrm_fin
 __global__ void store_slot(double* __restrict__ V, int M1, int slot, const double* __restrict__ src, const double* n2,
                            const KryDev* K, int64_t n) {
@@ -214,6 +296,7 @@ __global__ void __launch_bounds__(VB) zcombine_kernel(double* __restrict__ x, co
 // After pass 1: the column h[0..j], |w_old|^2 = h[j+1]; |w_new|^2 in nrm_new.
 __global__ void orth_decide(KryDev* K, int j) {
   K->nrm_old = sqrt(K->h[j + 1]);
+  K->nrm_new = K->h2[j + 1];  // |w'|^2 from the fused update (h2[0..j] hold the pass-2 dots)
   const double nn = sqrt(K->nrm_new);
   K->reorth = (nn < K->nrm_old * 0.70710678118654752) ? 1 : 0;
   K->nrm_fin = nn;
@@ -480,12 +563,16 @@ static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double
       }
       // pass 1: h = V^T w and |w|^2 (slot j+1 of h)
       if ((rc = basis_dots(m, V, M1, j + 1, w, n, K->h, true))) return rc;
-      if ((rc = basis_update(m, w, V, M1, j + 1, K->h, n, &K->nrm_new))) return rc;
+      // pass-1 update fused with the pass-2 projections of the updated vector
+      {
+        const int Gc = cgrid((n + CH - 1) / CH);
+        FSI_LAUNCH(m, P_KRY_UPD, upd_dot(m, Gc, w, V, M1, j + 1, K->h, n));
+        FSI_LAUNCH(m, P_KRY_UPD, sum_partials<<<j + 2, VB, 0, m->stream>>>(m->partials_dot, Gc, K->h2, nullptr));
+      }
       prof_bytes(m, P_KRY_DOT, (j + 2) * vb);   // j+1 basis vectors and w read once
       prof_bytes(m, P_KRY_UPD, (j + 3) * vb);   // j+1 basis vectors and w read, w written
       FSI_LAUNCH(m, P_KRY_SMALL, orth_decide<<<1, 1, 0, m->stream>>>(K, j));
-      // pass 2 only when the DGKS test asks for it
-      if ((rc = basis_dots(m, V, M1, j + 1, w, n, K->h2, false, &K->reorth))) return rc;
+      // the pass-2 update only when the DGKS test asks for it
       if ((rc = basis_update(m, w, V, M1, j + 1, K->h2, n, &K->nrm_new, &K->reorth))) return rc;
       FSI_LAUNCH(m, P_KRY_SMALL, givens_kernel<<<1, 1, 0, m->stream>>>(K, j, mm));
       FSI_LAUNCH(m, P_KRYLOV, store_slot<<<G, VB, 0, m->stream>>>(V, M1, j + 1, w, nullptr, K, n));
@@ -514,10 +601,7 @@ static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double
     for (int j = 0; j < enq; ++j) {  // the second passes that ran
       int ro = 0;
       memcpy(&ro, est + 3 * j + 2, sizeof(int));
-      if (ro) {
-        prof_bytes(m, P_KRY_DOT, (j + 2) * vb);
-        prof_bytes(m, P_KRY_UPD, (j + 3) * vb);
-      }
+      if (ro) prof_bytes(m, P_KRY_UPD, (j + 3) * vb);
     }
     FSI_LAUNCH(m, P_KRY_SMALL, lsq_kernel<<<1, 1, 0, m->stream>>>(K, jend, mm));
     if (pc) {
