@@ -392,6 +392,14 @@ def roofline(name, launches, ms, nbytes, d, pk):
                    peak_src=pk["hbm_src"] + " (MEASURED_PEAKS.json copy, read+write)")
         if rec is not None:
             out["traffic_note"] = rec["note"]
+        if name.startswith("krylov_dot") or name.startswith("krylov_update"):
+            # the second roof of the projections and updates: one float64 FMA per float64
+            # the launch reads (GB300 issues ~0.63 T DFMA/s, one per 8 bytes at 5 TB/s)
+            tf = nbytes / 8.0 * 2.0 / (ms / 1e3) / 1e12
+            out["alu_fp64"] = {"achieved": round(tf, 3), "peak": round(pk["fp64_tflops"], 3), "unit": "TFLOP/s",
+                               "frac": round(tf / pk["fp64_tflops"], 4),
+                               "note": "2 flop per algorithmic float64 element; peak derived from 152 SMs x 2 "
+                                       "DFMA/clk x 2 flop x max SM clock"}
         return out
     fpe = flops_per_element(name, d.n_solid)
     if fpe > 0:
