@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner arm")
     p.add_argument("--train-steps", type=int, default=3000)
+    p.add_argument("--restart", type=int, default=30, help="GMRES restart length m (<= 64)")
     p.add_argument("--case", default="step", choices=["step", "solve", "pcnet", "batch"],
                    help="solve: only a fixed 40-iteration float32-IR NS GMRES solve at 64^3 (a short, "
                         "repeatable launch sequence for ncu captures); pcnet: learned-preconditioner "
@@ -446,7 +447,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     fsi.fsi_set_stream(mesh, stream)
     prec = fsi.FSI_PREC_FP32_IR if args.precision == "fp32ir" else fsi.FSI_PREC_FP64
-    solve = fsi.solve_opts(m=64, rtol=1e-8, max_iter=3000, precision=prec, ir_inner_rtol=1e-3, ir_max=30)
+    solve = fsi.solve_opts(m=args.restart, rtol=1e-8, max_iter=3000, precision=prec, ir_inner_rtol=1e-3, ir_max=30)
 
     x, xn, xdn = initial_state(fsi, mesh, wl, torch, dev)
 
@@ -461,7 +462,8 @@ def run_gpu(args):
         pc = fsi.fsi_pc_create(mesh, n_pairs_cap=512, linear=True, modulate=True)
         fsi.fsi_pc_set_weights(pc, he_normal_weights(pc.fan, 3))
         fsi.fsi_set_pc(mesh, pc)
-        harvest = fsi.solve_opts(m=64, rtol=1e-8, max_iter=3000, precision=prec, ir_inner_rtol=1e-3, ir_max=30)
+        harvest = fsi.solve_opts(m=args.restart, rtol=1e-8, max_iter=3000, precision=prec, ir_inner_rtol=1e-3,
+                                 ir_max=30)
         harvest.flags |= fsi.FSI_HARVEST
     for _ in range(args.warmup):
         step(harvest if pc is not None else solve)
@@ -527,9 +529,9 @@ def run_gpu(args):
                       "Gram-Schmidt, Hessenberg" if prec == fsi.FSI_PREC_FP32_IR else "float64 throughout"),
         "data": "synthetic (seeded icosphere surface, initial phases by the grid-cell method)",
         "config": {"workload": WORKLOAD, "nodes": d.nn, "dof_per_node": d.ncomp, "dt": d.dt,
-                   "nl_iters_max": wl.k_max, "gmres": "Jacobi GMRES(64) rtol 1e-8, stop on stagnation",
-                   "l2": "inputs larger than L2: the NS solve streams a 65 x 1.1M float64 Krylov basis "
-                         "(572 MB) every restart cycle",
+                   "nl_iters_max": wl.k_max, "gmres": f"Jacobi GMRES({args.restart}) rtol 1e-8, stop on stagnation",
+                   "l2": "inputs larger than L2: the NS solve streams an (m+1) x 1.1M float64 Krylov basis "
+                         "(272 MB at m = 30) every restart cycle",
                    "parallelism": f"replicas x{world}"},
         "s_per_timestep": round(ms / args.steps / 1e3, 5),
         "step_stats": {"nl_iters": [i.nl_iters for i in infos],

@@ -7,7 +7,8 @@ separate instantiations of one body, so the compiler may contract a different se
 multiply-adds: results agree to a few ulps, not bit for bit.  Batched GMRES follows
 the same algorithm per instance; its solutions are checked against the residual of
 the per-instance operator and against per-instance solves (two solutions that both
-meet rel-res 1e-10 differ by up to the condition number times 1e-10)."""
+meet rel-res 1e-10 differ by up to the condition number times 1e-10: measured up to
+2.2e-5 on these NS blocks, so the solutions are compared at 1e-4)."""
 import numpy as np
 import pytest
 
@@ -101,7 +102,7 @@ def test_batched_gmres_matches_per_instance_solves(precision):
             fsi.fsi_jvp(m, fsi.FSI_BLOCK_NS, *states[i], xi.contiguous(), t)
         torch.cuda.synchronize()
         assert float(torch.linalg.norm(rhs[i] - t) / torch.linalg.norm(rhs[i])) <= 1.5e-10
-        assert float(torch.linalg.norm(xi - sols[i]) / torch.linalg.norm(sols[i])) <= 1e-5
+        assert float(torch.linalg.norm(xi - sols[i]) / torch.linalg.norm(sols[i])) <= 1e-4
 
 
 def test_autotuner_picks_a_shape_and_caches_it(tmp_path, monkeypatch):
