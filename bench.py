@@ -47,12 +47,13 @@ def parse():
     p.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner arm")
     p.add_argument("--train-steps", type=int, default=3000)
     p.add_argument("--restart", type=int, default=30, help="GMRES restart length m (<= 64)")
-    p.add_argument("--case", default="step", choices=["step", "solve", "pcnet", "batch"],
+    p.add_argument("--case", default="step", choices=["step", "solve", "pcnet", "batch", "mixed"],
                    help="solve: only a fixed 40-iteration float32-IR NS GMRES solve at 64^3 (a short, "
                         "repeatable launch sequence for ncu captures); pcnet: learned-preconditioner "
                         "applies and training steps at 64^3 with per-kernel timing (JSON on stdout); "
                         "batch: 64 uneven cavity instances, batched launches against per-instance "
-                        "launches (JSON on stdout)")
+                        "launches (JSON on stdout); mixed: 10 steps of the 64^3 cavity in float64 and "
+                        "with float32 operators in float64 refinement, per-field drift (JSON on stdout)")
     return p.parse_args()
 
 
@@ -202,6 +203,8 @@ def run_batch_case(count: int = 64, reps: int = 5):
     ms_single = timed(per_instance_jvp, reps)
     ms_batch = timed(lambda: fsi.fsi_batch_jvp(b, states, dx, y, flags), reps)
     # the solves
+    # GMRES(64): these first solves from rest need long restarts (GMRES(30) measured 1.99 s
+    # batched and 3.70 s per instance, against 1.42 s and 2.95 s)
     opts = fsi.solve_opts(m=64, rtol=1e-8, max_iter=3000, precision=fsi.FSI_PREC_FP32_IR, ir_inner_rtol=1e-3,
                           ir_max=30)
     rhs_all = torch.cat(rhs).contiguous()
@@ -245,6 +248,44 @@ def run_batch_case(count: int = 64, reps: int = 5):
                           "batched_gdofs": round(dof / ms_batch / 1e6, 3), "speedup": round(ms_single / ms_batch, 3),
                           "launches_per_instance_arm": count, "launches_batched": 2},
            "ns_solve_fp32ir_rtol1e-8": res, "max_solution_difference": diff}
+    print(json.dumps(out), flush=True)
+
+
+def run_mixed_case(steps: int = 10):
+    """The 64^3 cavity from its initial state: `steps` time steps with float64 operators
+    and, from the same state, with float32 operators inside float64 refinement (both
+    Jacobi GMRES(30) to rel-res 1e-8); the relative L2 distance of v, p, phi and B after
+    every step, and the time per step of each."""
+    import torch
+    from paper_2402_10348_gb300 import fsi
+    from workloads import cavity64
+    wl = cavity64()
+    d = wl.desc
+    dev = torch.device("cuda", 0)
+    out = {"case": "mixed", "workload": WORKLOAD, "steps": steps}
+    states = {}
+    for name, prec in (("fp64", fsi.FSI_PREC_FP64), ("fp32ir", fsi.FSI_PREC_FP32_IR)):
+        mesh = fsi.fsi_create_mesh(d)
+        fsi.fsi_set_stream(mesh)
+        x, xn, xdn = initial_state(fsi, mesh, wl, torch, dev)
+        solve = fsi.solve_opts(m=30, rtol=1e-8, max_iter=3000, precision=prec, ir_inner_rtol=1e-3, ir_max=30)
+        hist = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            fsi.fsi_step(mesh, x, xn, xdn, k_max=wl.k_max, nl_tol=5e-4, solve=solve)
+            hist.append(xn.clone())
+        torch.cuda.synchronize()
+        out[name + "_s_per_step"] = round((time.perf_counter() - t0) / steps, 4)
+        states[name] = hist
+    nn = d.nn
+    fields = {"v": (0, 3), "p": (3, 4), "phi": (4, 4 + d.n_phase), "B": (4 + d.n_phase, d.ncomp)}
+    drift = {k: [] for k in fields}
+    for a, b in zip(states["fp64"], states["fp32ir"]):
+        for k, (c0, c1) in fields.items():
+            ref = a[c0 * nn:c1 * nn]
+            drift[k].append(float(torch.linalg.norm(b[c0 * nn:c1 * nn] - ref) / torch.linalg.norm(ref)))
+    out["relative_l2_fp32ir_vs_fp64_per_step"] = {k: [float(f"{v:.2e}") for v in vs] for k, vs in drift.items()}
     print(json.dumps(out), flush=True)
 
 
@@ -704,6 +745,8 @@ def main():
         run_pcnet_case()
     elif args.case == "batch":
         run_batch_case()
+    elif args.case == "mixed":
+        run_mixed_case()
     elif args.case == "solve":
         run_solve_case()
     else:

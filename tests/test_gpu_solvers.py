@@ -152,3 +152,36 @@ def test_init_box_surfaces_multiple_solids():
         assert np.array_equal(got_tags[s], refs[s][1])
     ref = apply_rules(d, {s: refs[s][0] for s in refs}, wl.rules, d.eps)
     assert np.abs(phi.cpu().numpy().reshape(d.n_phase, d.nn) - ref).max() <= 4e-16
+
+
+def test_time_steps_fp64_and_fp32_ir_against_oracle():
+    """Three partitioned steps of the 6^3 cavity (three fixed nonlinear iterations each):
+    the float64 GPU path and the float32-operator path inside float64 iterative
+    refinement, each against the oracle, per field and step.  Stated errors: float64
+    <= 1e-10 (relative L2), float32 refinement <= 1e-6 (the target for reduced precision
+    after refinement; measured values are printed)."""
+    wl = cavity(6)
+    d = wl.desc
+    phi, _ = signed_distance_phi(d, wl.surfaces[0], d.eps, wl.grid_cells)
+    x = np.zeros((d.ncomp, d.nn))
+    x[4:4 + d.n_phase] = apply_rules(d, {0: phi}, wl.rules, d.eps)
+    x[4 + d.n_phase: 4 + d.n_phase + 3] = 1.0
+    st = State(x.copy(), x.copy(), np.zeros_like(x))
+    g64 = Gpu(d, st.x, st.xn, st.xdn)
+    g32 = Gpu(d, st.x, st.xn, st.xdn)
+    k = 3
+    o64 = fsi.solve_opts(rtol=1e-13, max_iter=5000)
+    o32 = fsi.solve_opts(rtol=1e-12, max_iter=5000, precision=fsi.FSI_PREC_FP32_IR, ir_inner_rtol=1e-3, ir_max=80)
+    fields = {"v": slice(0, 3), "p": slice(3, 4), "phi": slice(4, 4 + d.n_phase), "B": slice(4 + d.n_phase, d.ncomp)}
+    for s in range(3):
+        step.time_step(Problem(d), st, step.StepOptions(k_max=k, fixed_nl_iters=True, rtol=1e-13, max_iter=5000))
+        fsi.fsi_step(g64.mesh, *g64.st(), k_max=k, fixed_iters=True, solve=o64)
+        fsi.fsi_step(g32.mesh, *g32.st(), k_max=k, fixed_iters=True, solve=o32)
+        a64, a32 = g64.xn.cpu().numpy(), g32.xn.cpu().numpy()
+        for name, sl in fields.items():
+            ref = np.linalg.norm(st.xn[sl])
+            e64 = np.linalg.norm(a64[sl] - st.xn[sl]) / ref
+            e32 = np.linalg.norm(a32[sl] - st.xn[sl]) / ref
+            print(f"step {s + 1} {name}: float64 {e64:.2e}, float32-IR {e32:.2e}")
+            assert e64 <= 1e-10, (s, name, e64)
+            assert e32 <= 1e-6, (s, name, e32)
