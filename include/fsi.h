@@ -155,6 +155,10 @@ int fsi_fix_gamma(fsi_mesh* mesh, int32_t phase, double gamma);
  * from Jacobi-preconditioned Arnoldi steps j = 4, 12, 20, ... (at most 8 per inner
  * solve) the pair (A z_j, z_j), z_j = D^{-1} v_j, with the operator the step used */
 #define FSI_HARVEST 0x10u
+/* solve flag with FSI_PC_LEARNED: flexible GMRES takes the network's direction at even
+ * Arnoldi steps and the Jacobi direction D^{-1} v_j at odd ones, so that its
+ * least-squares step weights the two kinds separately */
+#define FSI_PC_ALTERNATE 0x20u
 
 #define FSI_PREC_FP64 0     /* operator applies in float64                         */
 #define FSI_PREC_FP32_IR 1  /* float32 operator inside float64 iterative refinement */

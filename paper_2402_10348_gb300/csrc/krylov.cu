@@ -501,6 +501,8 @@ static int ensure_krylov(fsi_mesh* m, int64_t n, int mm) {
 static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double* x, int mm, double rtol,
                       int max_iter, unsigned flags, int* iters, int* restarts, double* rel_out, int* stalled,
                       fsi_pc* pc = nullptr, fsi_pc* harvest = nullptr) {
+  const bool alternate = (flags & FSI_PC_ALTERNATE) != 0;
+  flags &= ~FSI_PC_ALTERNATE;
   const int64_t n = blk.n;
   const int M1 = m->kry_m + 1;
   const int G = vgrid(n);
@@ -549,8 +551,14 @@ static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double
     for (int j = 0; j < jmax && !done; ++j) {
       if (pc) {  // flexible GMRES: z_j = M(v_j), |v_j| = 1
         double* zj = m->Z + (int64_t)j * n;
-        FSI_LAUNCH(m, P_KRYLOV, extract_kernel<<<G, VB, 0, m->stream>>>(V, M1, j, t, n));
-        if ((rc = pcn::apply(pc, t, 1.0, m->dinv, zj))) return rc;
+        if (alternate && (j & 1)) {
+          // every other direction is the plain Jacobi one: the least-squares step then
+          // weights network and Jacobi directions separately
+          FSI_LAUNCH(m, P_KRYLOV, precond_kernel<<<G, VB, 0, m->stream>>>(V, M1, j, m->dinv, zj, n));
+        } else {
+          FSI_LAUNCH(m, P_KRYLOV, extract_kernel<<<G, VB, 0, m->stream>>>(V, M1, j, t, n));
+          if ((rc = pcn::apply(pc, t, 1.0, m->dinv, zj))) return rc;
+        }
         if ((rc = op_jvp(m, blk, zj, w, flags))) return rc;
       } else {
         FSI_LAUNCH(m, P_KRYLOV, precond_kernel<<<G, VB, 0, m->stream>>>(V, M1, j, m->dinv, z, n));
@@ -633,7 +641,8 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& blk, const double* rhs, double* x,
   if (o.precond == FSI_PC_LEARNED && blk.kind == 0 && !pc)
     return set_error(FSI_EINVAL, "GMRES: FSI_PC_LEARNED without an attached preconditioner (fsi_set_pc)");
   fsi_pc* harvest = ((o.flags & FSI_HARVEST) && blk.kind == 0 && m->pc && m->pc->cap > 0) ? m->pc : nullptr;
-  const unsigned opflags = o.flags & ~FSI_HARVEST;
+  const unsigned opflags = o.flags & ~(FSI_HARVEST | FSI_PC_ALTERNATE);
+  const unsigned alt = o.flags & FSI_PC_ALTERNATE;  // read by the flexible solves only
   if (pc && (m->Z_n < n * mm || !m->Z)) {
     cudaFree(m->Z);
     m->Z = nullptr;
@@ -663,8 +672,16 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& blk, const double* rhs, double* x,
   };
   double* rfin = nullptr;  // final true residual (harvest)
   if (o.precision == FSI_PREC_FP64) {
-    rc = gmres_core(m, blk, rhs, x, mm, o.rtol, o.max_iter, opflags & ~FSI_FP32, &inf.iterations, &inf.restarts,
+    rc = gmres_core(m, blk, rhs, x, mm, o.rtol, o.max_iter, (opflags & ~FSI_FP32) | alt, &inf.iterations, &inf.restarts,
                     &rel, &inf.stalled, pc, pc ? nullptr : harvest);
+    if (rc == FSI_ENAN && pc) {
+      // the network produced non-finite directions (corrupted weights, overflow):
+      // Jacobi GMRES solves from scratch
+      inf.fallback = 1;
+      pc = nullptr;
+      rc = gmres_core(m, blk, rhs, x, mm, o.rtol, o.max_iter - inf.iterations, opflags & ~FSI_FP32,
+                      &inf.iterations, &inf.restarts, &rel, &inf.stalled, nullptr, harvest);
+    }
     if (rc) return rc;
     if (pc && rel > o.rtol && inf.iterations < o.max_iter) {
       // fallback: Jacobi GMRES on the remaining residual r = rhs - A x (in wk[0..n))
@@ -704,9 +721,16 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& blk, const double* rhs, double* x,
       if ((rc = checkpoint(x, r))) return rc;
       double inner_rel;
       int inner_stalled;
-      rc = gmres_core(m, blk, r, d, mm, o.ir_inner_rtol, o.max_iter - inf.iterations, (opflags | FSI_FP32),
+      rc = gmres_core(m, blk, r, d, mm, o.ir_inner_rtol, o.max_iter - inf.iterations, (opflags | FSI_FP32 | alt),
                       &inf.iterations, &inf.restarts, &inner_rel, &inner_stalled, inner_pc,
                       inner_pc ? nullptr : harvest);
+      if (rc == FSI_ENAN && inner_pc) {
+        // non-finite network directions: this refinement again, with Jacobi inner solves
+        inner_pc = nullptr;
+        inf.fallback = 1;
+        --k;
+        continue;
+      }
       if (rc) return rc;
       if ((rc = vec_axpy(m, 1.0, d, x, n))) return rc;
       if ((rc = op_jvp(m, blk, x, d, opflags & ~FSI_FP32))) return rc;

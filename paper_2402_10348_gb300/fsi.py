@@ -20,6 +20,7 @@ FSI_ELASTIC_AUG = 0x1
 FSI_FP32 = 0x2
 FSI_PC_NONE, FSI_PC_JACOBI, FSI_PC_LEARNED = 0, 1, 2
 FSI_HARVEST = 0x10
+FSI_PC_ALTERNATE = 0x20
 FSI_PREC_FP64, FSI_PREC_FP32_IR = 0, 1
 FSI_BC_NATURAL, FSI_BC_DIRICHLET = 0, 1
 FSI_RULE_SURFACE, FSI_RULE_COMPLEMENT = 0, 1

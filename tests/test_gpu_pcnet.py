@@ -193,6 +193,44 @@ def test_fgmres_with_untrained_network_reaches_the_oracle_solution():
         assert rel(x, ref) <= 1e-6
 
 
+def test_corrupted_network_falls_back_to_jacobi_and_alternate_mode_converges():
+    """Host-injected fault: NaN weights.  Both solver precisions still reach the
+    tolerance through the Jacobi fallback.  With sane weights, flexible GMRES that
+    alternates network and Jacobi directions (FSI_PC_ALTERNATE) reaches it too.  The
+    true residual is checked with the float64 operator; two solutions that both meet
+    1e-10 differ by up to the condition number times 1e-10 (about 5e-5 here)."""
+    d, g, rhs, _ = _lin_problem(seed=21)
+    b = T(rhs)
+
+    def true_rel(x):
+        t = torch.zeros_like(x)
+        fsi.fsi_jvp(g.mesh, fsi.FSI_BLOCK_NS, *g.st(), x, t)
+        torch.cuda.synchronize()
+        return float(torch.linalg.norm(b - t) / torch.linalg.norm(b))
+
+    pc = fsi.fsi_pc_create(g.mesh)
+    w = he_normal_weights(pc.fan, 22)
+    fsi.fsi_set_pc(g.mesh, pc)
+    sol = torch.zeros(4 * d.nn, dtype=torch.float64, device=DEV)
+    jac = torch.zeros_like(sol)
+    fsi.fsi_gmres(g.mesh, fsi.FSI_BLOCK_NS, *g.st(), T(rhs), jac, fsi.solve_opts(m=30, rtol=1e-10, max_iter=4000))
+    bad = w.copy()
+    bad[::97] = np.nan
+    fsi.fsi_pc_set_weights(pc, bad)
+    for prec in (fsi.FSI_PREC_FP64, fsi.FSI_PREC_FP32_IR):
+        o = fsi.solve_opts(m=30, rtol=1e-10, max_iter=4000, precond=fsi.FSI_PC_LEARNED, precision=prec,
+                           ir_inner_rtol=1e-3, ir_max=60)
+        info = fsi.fsi_gmres(g.mesh, fsi.FSI_BLOCK_NS, *g.st(), T(rhs), sol, o)
+        assert info.fallback == 1 and info.rel_res <= 1e-10 and true_rel(sol) <= 1.5e-10
+        assert float(torch.linalg.norm(sol - jac) / torch.linalg.norm(jac)) <= 1e-3
+    fsi.fsi_pc_set_weights(pc, w)
+    o = fsi.solve_opts(m=30, rtol=1e-10, max_iter=4000, precond=fsi.FSI_PC_LEARNED)
+    o.flags |= fsi.FSI_PC_ALTERNATE
+    info = fsi.fsi_gmres(g.mesh, fsi.FSI_BLOCK_NS, *g.st(), T(rhs), sol, o)
+    assert info.rel_res <= 1e-10 and true_rel(sol) <= 1.5e-10
+    assert float(torch.linalg.norm(sol - jac) / torch.linalg.norm(jac)) <= 1e-3
+
+
 def test_harvested_pairs_train_a_network_that_beats_jacobi():
     """What the trained network gains: on the 32^3 cavity's NS block, a linear U-Net
     trained on pairs harvested from Jacobi solves (refinement checkpoints and Arnoldi
