@@ -23,8 +23,8 @@
 // channels one octet plane (2880 bytes) further.  Planes stream through a 4-slot ring
 // (cp.async with zero fill at the grid boundary); the accumulator is double-buffered
 // in TMEM so that one layer's epilogue overlaps the next layer's MMAs.
-// Weight gradients are reductions over voxels done on the CUDA cores (per-CTA
-// partials, summed in a fixed order).
+// Weight gradients are implicit GEMMs over voxels on the same tensor cores (per-CTA
+// partials from TMEM, summed in a fixed order).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -43,7 +43,6 @@ constexpr int SX = TILE_X + 2, SY = TILE_Y + 2;      // staged input plane with 
 constexpr int OCT_BYTES = SX * SY * 16;      // one channel octet of one staged plane
 constexpr int NSLOT = 4;
 constexpr int CONV_THREADS = 128;
-constexpr int WG_THREADS = 256;
 // four per-component scales passed by value
 struct D4 {
   double c[4];
@@ -469,80 +468,6 @@ __global__ void prolong_f32_kernel(const float* __restrict__ c, Grid3 gc, float*
 }
 
 // ------------------------------------------------------------------ weight gradient
-// part[blk][co][ci][t] = sum over the CTA's voxels v of g[v][co] * x[v + t - 1][ci]
-template <int CIN>
-__global__ void __launch_bounds__(WG_THREADS) wgrad_kernel(TView x, TView g, int zc, float* __restrict__ part) {
-  constexpr int NO = CIN / 8;
-  constexpr int NJ = CIN / 16;
-  __shared__ __align__(16) uint16_t xs[3][NO][SY * SX][8];
-  __shared__ __align__(16) uint16_t gs[2][TILE_X * TILE_Y][8];
-  const int tid = threadIdx.x;
-  const int co = tid >> 4, cl = tid & 15;
-  const int x0 = blockIdx.x * TILE_X, y0 = blockIdx.y * TILE_Y, z0 = blockIdx.z * zc;
-  const int z1 = min(z0 + zc, g.nz);
-  float acc[NJ][27];
-#pragma unroll
-  for (int j = 0; j < NJ; ++j)
-#pragma unroll
-    for (int t = 0; t < 27; ++t) acc[j][t] = 0.0f;
-  auto load_x = [&](int slot, int z) {
-    const bool zin = z >= 0 && z < x.nz;
-    for (int i = tid; i < NO * SY * SX; i += WG_THREADS) {
-      const int o = i / (SY * SX), rem = i - o * (SY * SX), yy = rem / SX, xx = rem - yy * SX;
-      const int gx = x0 - 1 + xx, gy = y0 - 1 + yy;
-      uint4 q = make_uint4(0, 0, 0, 0);
-      if (zin && gx >= 0 && gx < x.nx && gy >= 0 && gy < x.ny)
-        q = *reinterpret_cast<const uint4*>(x.p + vox_addr(x, o, gx, gy, z));
-      *reinterpret_cast<uint4*>(&xs[slot][o][rem][0]) = q;
-    }
-  };
-  if (z0 < z1) {
-    load_x(0, z0 - 1);
-    load_x(1, z0);
-  }
-  for (int z = z0; z < z1; ++z) {
-    const int it = z - z0;
-    load_x((it + 2) % 3, z + 1);
-    for (int i = tid; i < 2 * TILE_X * TILE_Y; i += WG_THREADS) {
-      const int o = i / (TILE_X * TILE_Y), m = i - o * (TILE_X * TILE_Y);
-      const int gx = x0 + (m & 7), gy = y0 + (m >> 3);
-      uint4 q = make_uint4(0, 0, 0, 0);
-      if (gx < g.nx && gy < g.ny) q = *reinterpret_cast<const uint4*>(g.p + vox_addr(g, o, gx, gy, z));
-      *reinterpret_cast<uint4*>(&gs[o][m][0]) = q;
-    }
-    __syncthreads();
-    const int s0 = it % 3, s1 = (it + 1) % 3, s2 = (it + 2) % 3;
-#pragma unroll 1
-    for (int m = 0; m < TILE_X * TILE_Y; ++m) {
-      const float gv = bf2f(gs[co >> 3][m][co & 7]);
-      const int mx = m & 7, my = m >> 3;
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        const int ci = cl + 16 * j;
-        const int o = ci >> 3, k = ci & 7;
-#pragma unroll
-        for (int dz = 0; dz < 3; ++dz) {
-          const int sl = dz == 0 ? s0 : (dz == 1 ? s1 : s2);
-#pragma unroll
-          for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 3; ++dx)
-              acc[j][dz * 9 + dy * 3 + dx] += gv * bf2f(xs[sl][o][(my + dy) * SX + mx + dx][k]);
-        }
-      }
-    }
-    __syncthreads();
-  }
-  const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  float* dst = part + blk * (16 * CIN * 27);
-#pragma unroll
-  for (int j = 0; j < NJ; ++j) {
-    const int ci = cl + 16 * j;
-#pragma unroll
-    for (int t = 0; t < 27; ++t) dst[((int64_t)co * CIN + ci) * 27 + t] = acc[j][t];
-  }
-}
-
 // g[(co cin + ci) 27 + t] = sum_b part[b][co][ci][t] for co < cout, in block order
 __global__ void wgrad_reduce_kernel(const float* __restrict__ part, int nblk, int cin, int cout,
                                     float* __restrict__ g) {
@@ -553,6 +478,149 @@ __global__ void wgrad_reduce_kernel(const float* __restrict__ part, int nblk, in
     for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * stride + e];
     g[e] = s;
   }
+}
+
+// ------------------------------------------------------------------ weight gradient on tensor cores
+// dW[co][ci][t] = sum_v dY[v][co] X[v + delta_t][ci] as implicit GEMMs, one per group of
+// MT = 128 / CIN taps: D[(t_local, ci)][co] (M = 128, N = 16) accumulates over K = voxels,
+// 16 voxels per tcgen05.mma.  Both operands are staged K-major without swizzle (core
+// matrix = 8 rows x 8 voxels, the layout the convolution's B operand uses):
+// A[m][k] = X[v_k + delta_t(m)][ci(m)], B[co][k] = dY[v_k][co].  Each CTA walks a
+// contiguous range of voxels with double-buffered staging; its TMEM accumulators (16
+// columns per tap group) become per-CTA partials in the [co][ci][27] layout that
+// wgrad_reduce_kernel sums in a fixed order.
+constexpr int WGM_THREADS = 128;
+constexpr int WGM_KS = 16;  // voxels per stage: one MMA K-step
+
+template <int CIN>
+struct WgmCfg {
+  static constexpr int MT = 128 / CIN;             // taps per group
+  static constexpr int NG = (27 + MT - 1) / MT;    // tap groups
+  static constexpr int ABYTES = 128 * WGM_KS * 2;  // one group's A tile
+  static constexpr int BBYTES = 16 * WGM_KS * 2;
+  static constexpr int STAGE = NG * ABYTES + BBYTES;
+  static constexpr int HEAD = 128;
+  static constexpr int SMEM = HEAD + 2 * STAGE;
+  static constexpr int NCOLS = NG * 16 <= 32 ? 32 : (NG * 16 <= 64 ? 64 : 128);
+};
+
+template <int CIN>
+__global__ void __launch_bounds__(WGM_THREADS) wgrad_mma_kernel(TView x, TView g, int spc, int64_t nstages,
+                                                              float* __restrict__ part, int* err) {
+  using C = WgmCfg<CIN>;
+  extern __shared__ __align__(1024) uint8_t sm[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm);
+  uint32_t* holder = reinterpret_cast<uint32_t*>(sm + 16);
+  uint8_t* stage_base = sm + C::HEAD;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t V = (int64_t)g.nx * g.ny * g.nz;
+  const int64_t s0 = (int64_t)blockIdx.x * spc, s1 = min(nstages, s0 + spc);
+  if (tid == 0) {
+    mbar_init(smem_u32(&bars[0]), 1);
+    mbar_init(smem_u32(&bars[1]), 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(smem_u32(holder), C::NCOLS);
+  // both buffers start at zero: the rows of the taps past 26 stay zero
+  for (int i = tid; i < 2 * C::STAGE / 16; i += WGM_THREADS)
+    reinterpret_cast<uint4*>(stage_base)[i] = make_uint4(0, 0, 0, 0);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *holder;
+  constexpr uint32_t IDESC = idesc_bf16(16, 128);
+  bool bad = false;
+  for (int64_t st = s0; st < s1; ++st) {
+    const int it = (int)(st - s0), b = it & 1;
+    if (it >= 2) {  // the MMAs that read this buffer two stages ago are done
+      const bool ok = mbar_wait(smem_u32(&bars[b]), (uint32_t)(((it - 2) >> 1) & 1));
+      if (__syncthreads_or(!ok)) {
+        bad = true;
+        break;
+      }
+    }
+    uint16_t* A = reinterpret_cast<uint16_t*>(stage_base + b * C::STAGE);
+    uint16_t* B = reinterpret_cast<uint16_t*>(stage_base + b * C::STAGE + C::NG * C::ABYTES);
+    const int64_t vbase = st * WGM_KS;
+    // A: items (voxel k, tap t, input octet o)
+    for (int i = tid; i < WGM_KS * 27 * (CIN / 8); i += WGM_THREADS) {
+      const int k = i % WGM_KS, rest = i / WGM_KS, t = rest % 27, o = rest / 27;
+      const int64_t v = vbase + k;
+      uint4 q = make_uint4(0, 0, 0, 0);
+      if (v < V) {
+        const int vx = (int)(v % g.nx), vy = (int)((v / g.nx) % g.ny), vz = (int)(v / ((int64_t)g.nx * g.ny));
+        const int xx = vx + t % 3 - 1, yy = vy + (t / 3) % 3 - 1, zz = vz + t / 9 - 1;
+        if (xx >= 0 && xx < x.nx && yy >= 0 && yy < x.ny && zz >= 0 && zz < x.nz)
+          q = *reinterpret_cast<const uint4*>(x.p + vox_addr(x, o, xx, yy, zz));
+      }
+      const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+      uint16_t* At = A + (t / C::MT) * (C::ABYTES / 2);
+      const int m0 = (t % C::MT) * CIN + o * 8;  // rows m0 .. m0+7 (one core-matrix row group)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int m = m0 + e;
+        At[((k >> 3) * 16 + (m >> 3)) * 64 + (m & 7) * 8 + (k & 7)] = (uint16_t)(u[e >> 1] >> (16 * (e & 1)));
+      }
+    }
+    // B: items (voxel k, gradient octet q)
+    for (int i = tid; i < WGM_KS * 2; i += WGM_THREADS) {
+      const int k = i % WGM_KS, qo = i / WGM_KS;
+      const int64_t v = vbase + k;
+      uint4 q = make_uint4(0, 0, 0, 0);
+      if (v < V) {
+        const int vx = (int)(v % g.nx), vy = (int)((v / g.nx) % g.ny), vz = (int)(v / ((int64_t)g.nx * g.ny));
+        q = *reinterpret_cast<const uint4*>(g.p + vox_addr(g, qo, vx, vy, vz));
+      }
+      const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int co = qo * 8 + e;
+        B[((k >> 3) * 2 + (co >> 3)) * 64 + (co & 7) * 8 + (k & 7)] = (uint16_t)(u[e >> 1] >> (16 * (e & 1)));
+      }
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t abase = smem_u32(A), bbase = smem_u32(B);
+#pragma unroll 1
+      for (int gi = 0; gi < C::NG; ++gi)
+        mma_bf16(tmem + (uint32_t)(gi * 16), sdesc(abase + gi * C::ABYTES, 16 * 128, 128), sdesc(bbase, 2 * 128, 128),
+                 IDESC, it > 0 ? 1u : 0u);
+      mma_commit(smem_u32(&bars[b]));
+    }
+    __syncwarp();
+  }
+  const int nst = (int)(s1 - s0);
+  if (!bad && nst > 0) {
+    const int last = nst - 1;
+    const bool ok = mbar_wait(smem_u32(&bars[last & 1]), (uint32_t)((last >> 1) & 1));
+    if (__syncthreads_or(!ok)) bad = true;
+  }
+  if (!bad) {
+    tc_fence_after();
+    const int m = warp * 32 + lane;
+    const int t_local = m / CIN, ci = m % CIN;
+    float* dst = part + (int64_t)blockIdx.x * (16 * CIN * 27);
+#pragma unroll 1
+    for (int gi = 0; gi < C::NG; ++gi) {
+      uint32_t r[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(gi * 16), r);
+      const int t = gi * C::MT + t_local;
+      if (t < 27) {
+#pragma unroll
+        for (int co = 0; co < 16; ++co)
+          dst[((int64_t)co * CIN + ci) * 27 + t] = nst > 0 ? __uint_as_float(r[co]) : 0.0f;
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, C::NCOLS);
 }
 
 // ------------------------------------------------------------------ loss
@@ -798,20 +866,35 @@ int conv(fsi_pc* pc, int cin, int n, const TView& in, const TView& out, const TV
   return set_error(FSI_EINVAL, "pc: unsupported convolution shape");
 }
 
+template <int CIN>
+int launch_wgrad_mma(fsi_pc* pc, const TView& x, const TView& g, int* nblk_out) {
+  using C = WgmCfg<CIN>;
+  fsi_mesh* m = pc->m;
+  static bool attr = false;
+  if (!attr) {
+    FSI_CUDA(cudaFuncSetAttribute(wgrad_mma_kernel<CIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    attr = true;
+  }
+  const int64_t V = (int64_t)g.nx * g.ny * g.nz;
+  const int64_t nst = (V + WGM_KS - 1) / WGM_KS;
+  const int per_sm = std::max(1, std::min(std::min(8, 512 / C::NCOLS), (227 * 1024) / (C::SMEM + 1024)));
+  const int64_t target = (int64_t)per_sm * 152;
+  const int spc = (int)std::max<int64_t>(1, (nst + target - 1) / target);
+  const int nblk = (int)((nst + spc - 1) / spc);
+  if ((int64_t)nblk * 16 * CIN * 27 > pc->wpart_n) return set_error(FSI_EINVAL, "pc: weight-gradient scratch too small");
+  FSI_LAUNCH(m, P_PC_WGRAD, (wgrad_mma_kernel<CIN><<<nblk, WGM_THREADS, C::SMEM, m->stream>>>(x, g, spc, nst,
+                                                                                              pc->wpart, pc->err)));
+  *nblk_out = nblk;
+  return FSI_OK;
+}
+
 int wgrad(fsi_pc* pc, int layer, const TView& x, const TView& g) {
   fsi_mesh* m = pc->m;
   const int cin = pc->lcin[layer], cout = pc->lcout[layer];
-  const int gx = (g.nx + TILE_X - 1) / TILE_X, gy = (g.ny + TILE_Y - 1) / TILE_Y;
-  const int cols = gx * gy;
-  const int zc = std::max(1, (int)((int64_t)g.nz * cols / (2 * 152)));
-  const int gz = (g.nz + zc - 1) / zc;
-  const int nblk = gx * gy * gz;
-  if ((int64_t)nblk * 16 * cin * 27 > pc->wpart_n) return set_error(FSI_EINVAL, "pc: weight-gradient scratch too small");
-  if (cin == 16) {
-    FSI_LAUNCH(m, P_PC_WGRAD, (wgrad_kernel<16><<<dim3(gx, gy, gz), WG_THREADS, 0, m->stream>>>(x, g, zc, pc->wpart)));
-  } else {
-    FSI_LAUNCH(m, P_PC_WGRAD, (wgrad_kernel<32><<<dim3(gx, gy, gz), WG_THREADS, 0, m->stream>>>(x, g, zc, pc->wpart)));
-  }
+  int nblk = 0, rc;
+  if (cin == 16) rc = launch_wgrad_mma<16>(pc, x, g, &nblk);
+  else rc = launch_wgrad_mma<32>(pc, x, g, &nblk);
+  if (rc) return rc;
   const int n = cout * cin * 27;
   FSI_LAUNCH(m, P_PC_WGRAD, (wgrad_reduce_kernel<<<(n + 255) / 256, 256, 0, m->stream>>>(pc->wpart, nblk, cin, cout,
                                                                                           pc->grad + pc->woff[layer])));
@@ -1188,7 +1271,7 @@ int fsi_pc_create(fsi_mesh* m, const fsi_pc_desc* d, fsi_pc** out) {
       const int zc = std::max(1, (int)((int64_t)g.nz * gx * gy / (2 * 152)));
       nblk = std::max(nblk, (int64_t)gx * gy * ((g.nz + zc - 1) / zc));
     }
-    pc->wpart_n = nblk * 16 * 32 * 27;
+    pc->wpart_n = std::max<int64_t>(nblk, 8 * 152) * 16 * 32 * 27;
     if ((rc = dalloc(&pc->wpart, pc->wpart_n))) return fail(rc);
   }
   pc->dmask = m->mask;
