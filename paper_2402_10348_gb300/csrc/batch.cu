@@ -910,12 +910,12 @@ int fsi_batch_gmres(fsi_batch* b, const fsi_state* states, const double* rhs, do
   cudaStream_t s = b->stream;
   int rc;
   if ((rc = stage_all(b, states, f32))) return rc;
-  // Jacobi diagonal of the float64 operator, one launch per instance (once per solve)
+  // Jacobi diagonal of the inner operator, one launch per instance (once per solve)
   for (int i = 0; i < nb; ++i) {
     BlockInfo bi;
     if ((rc = block_info(b->meshes[i], b->block, &bi))) return rc;
     if (o->precond == FSI_PC_JACOBI) {
-      if ((rc = op_diag(b->meshes[i], bi, b->dinv + b->off[i], base))) return rc;
+      if ((rc = op_diag(b->meshes[i], bi, b->dinv + b->off[i], f32 ? (base | FSI_FP32) : base))) return rc;
     } else {
       std::vector<double> ones(bi.n, 1.0);
       FSI_CUDA(cudaMemcpy(b->dinv + b->off[i], ones.data(), sizeof(double) * bi.n, cudaMemcpyHostToDevice));

@@ -56,8 +56,9 @@ struct KryDev {
   double nrm_old, nrm_new, nrm_fin;
   double bnorm;
   double est;              // |g_{j+1}| / |b|
-  int reorth;
+  int reorth;              // est, reorth, breakdown: one 16-byte copy to the host per step
   int breakdown;
+  unsigned counter;        // CTAs done in sum_partials_decide (back to 0 after each use)
 };
 
 template <int K>
@@ -293,17 +294,20 @@ __global__ void __launch_bounds__(VB) zcombine_kernel(double* __restrict__ x, co
 }
 
 // --------------------------------------------------------- small device kernels
-// After pass 1: the column h[0..j], |w_old|^2 = h[j+1]; |w_new|^2 in nrm_new.
-__global__ void orth_decide(KryDev* K, int j) {
+// After pass 1: the column h[0..j], |w_old|^2 = h[j+1]; |w_new|^2 in h2[j+1] (the fused
+// update's row of norms; h2[0..j] hold the pass-2 projections).  Read through a volatile
+// pointer: other CTAs wrote h2 just before.
+__device__ void orth_decide_body(KryDev* K, int j) {
+  volatile double* h2 = K->h2;
   K->nrm_old = sqrt(K->h[j + 1]);
-  K->nrm_new = K->h2[j + 1];  // |w'|^2 from the fused update (h2[0..j] hold the pass-2 dots)
+  K->nrm_new = h2[j + 1];
   const double nn = sqrt(K->nrm_new);
   K->reorth = (nn < K->nrm_old * 0.70710678118654752) ? 1 : 0;
   K->nrm_fin = nn;
 }
 
 // After the (possible) second pass: fold h2 into h, rotate, update the estimate.
-__global__ void givens_kernel(KryDev* K, int j, int mm) {
+__device__ void givens_body(KryDev* K, int j, int mm) {
   if (K->reorth) {
     for (int i = 0; i <= j; ++i) K->h[i] += K->h2[i];
     K->nrm_fin = sqrt(K->nrm_new);
@@ -326,6 +330,44 @@ __global__ void givens_kernel(KryDev* K, int j, int mm) {
   K->g[j] = K->cs[j] * K->g[j];
   K->est = fabs(K->g[j + 1]) / K->bnorm;
   K->breakdown = (hn == 0.0 || den == 0.0 || !isfinite(hn)) ? 1 : 0;
+}
+
+// Rows of the fused update's partials into K->h2 (one CTA per row, fixed order); the last
+// CTA to finish takes the DGKS decision, so no single-thread launch follows.
+__global__ void sum_partials_decide(const double* __restrict__ part, int G, KryDev* K, int j) {
+  const int i = blockIdx.x;
+  double s = 0.0;
+  for (int c = threadIdx.x; c < G; c += VB) s += part[(int64_t)i * G + c];
+  double acc[1] = {s};
+  __shared__ double res;
+  __shared__ bool last;
+  block_reduce_store<1>(acc, 1, &res, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    K->h2[i] = res;
+    __threadfence();
+    last = atomicAdd(&K->counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    K->counter = 0;
+    orth_decide_body(K, j);
+  }
+}
+
+// The second pass's |w|^2 (only when it ran) and the Givens step, in one CTA.
+__global__ void sum_partials_givens(const double* __restrict__ part, int G, KryDev* K, int j, int mm) {
+  if (K->reorth) {
+    double s = 0.0;
+    for (int c = threadIdx.x; c < G; c += VB) s += part[c];
+    double acc[1] = {s};
+    __shared__ double res;
+    block_reduce_store<1>(acc, 1, &res, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) K->nrm_new = res;
+  }
+  if (threadIdx.x == 0) givens_body(K, j, mm);
 }
 
 // y = R^{-1} g for the first jend columns (back substitution).
@@ -487,6 +529,7 @@ static int ensure_krylov(fsi_mesh* m, int64_t n, int mm) {
   if (int rc = ensure_partials(m)) return rc;
   if (!m->kry_dev) {
     FSI_CUDA(cudaMalloc(&m->kry_dev, sizeof(KryDev)));
+    FSI_CUDA(cudaMemset(m->kry_dev, 0, sizeof(KryDev)));
     FSI_CUDA(cudaMallocHost(&m->kry_est, sizeof(double) * 3 * (MMAX + 1)));
     m->kry_ev.resize(MMAX + 1);
     for (auto& e : m->kry_ev) FSI_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -512,7 +555,7 @@ static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double
   double* t = m->wk + 2 * n;
   double* w = m->wk + 6 * n;
   KryDev* K = static_cast<KryDev*>(m->kry_dev);
-  double* est = m->kry_est;  // pinned: [3j] estimate, [3j+1] breakdown flag, [3j+2] second pass ran
+  double* est = m->kry_est;  // pinned, 3 slots per step: the estimate, then the reorth and breakdown ints
   FSI_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, m->stream));
   double bnorm2;
   int rc = vec_dot(m, b, b, n, &bnorm2);
@@ -575,18 +618,19 @@ static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double
       {
         const int Gc = cgrid((n + CH - 1) / CH);
         FSI_LAUNCH(m, P_KRY_UPD, upd_dot(m, Gc, w, V, M1, j + 1, K->h, n));
-        FSI_LAUNCH(m, P_KRY_UPD, sum_partials<<<j + 2, VB, 0, m->stream>>>(m->partials_dot, Gc, K->h2, nullptr));
+        FSI_LAUNCH(m, P_KRY_UPD, sum_partials_decide<<<j + 2, VB, 0, m->stream>>>(m->partials_dot, Gc, K, j));
+        prof_bytes(m, P_KRY_DOT, (j + 2) * vb);  // j+1 basis vectors and w read once
+        prof_bytes(m, P_KRY_UPD, (j + 3) * vb);  // j+1 basis vectors and w read, w written
+        // the pass-2 update only when the DGKS test asked for it (exits at once otherwise),
+        // then its norm and the Givens step
+        FSI_LAUNCH(m, P_KRY_UPD, upd_kernel<<<Gc, VB, 0, m->stream>>>(w, V, M1, j + 1, K->h2, n, m->partials_dot,
+                                                                       &K->reorth));
+        FSI_LAUNCH(m, P_KRY_SMALL, sum_partials_givens<<<1, VB, 0, m->stream>>>(m->partials_dot, Gc, K, j, mm));
       }
-      prof_bytes(m, P_KRY_DOT, (j + 2) * vb);   // j+1 basis vectors and w read once
-      prof_bytes(m, P_KRY_UPD, (j + 3) * vb);   // j+1 basis vectors and w read, w written
-      FSI_LAUNCH(m, P_KRY_SMALL, orth_decide<<<1, 1, 0, m->stream>>>(K, j));
-      // the pass-2 update only when the DGKS test asks for it
-      if ((rc = basis_update(m, w, V, M1, j + 1, K->h2, n, &K->nrm_new, &K->reorth))) return rc;
-      FSI_LAUNCH(m, P_KRY_SMALL, givens_kernel<<<1, 1, 0, m->stream>>>(K, j, mm));
       FSI_LAUNCH(m, P_KRYLOV, store_slot<<<G, VB, 0, m->stream>>>(V, M1, j + 1, w, nullptr, K, n));
-      FSI_CUDA(cudaMemcpyAsync(est + 3 * j, &K->est, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
-      FSI_CUDA(cudaMemcpyAsync(est + 3 * j + 1, &K->breakdown, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
-      FSI_CUDA(cudaMemcpyAsync(est + 3 * j + 2, &K->reorth, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+      // estimate, reorth and breakdown flags: one copy (the fields are adjacent)
+      FSI_CUDA(cudaMemcpyAsync(est + 3 * j, &K->est, sizeof(double) + 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                               m->stream));
       FSI_CUDA(cudaEventRecord(m->kry_ev[j], m->stream));
       ++*iters;
       jend = j + 1;
@@ -595,7 +639,7 @@ static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double
       if (j >= 1) {
         FSI_CUDA(cudaEventSynchronize(m->kry_ev[j - 1]));
         int bd = 0;
-        memcpy(&bd, est + 3 * (j - 1) + 1, sizeof(int));
+        memcpy(&bd, reinterpret_cast<const char*>(est + 3 * (j - 1)) + sizeof(double) + sizeof(int), sizeof(int));
         const double e = est[3 * (j - 1)];
         if (!std::isfinite(e)) return set_error(FSI_ENAN, "GMRES: Arnoldi vector is not finite");
         if (e <= rtol || bd) {
@@ -608,7 +652,7 @@ static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double
     if (!done && !std::isfinite(est[3 * (jend - 1)])) return set_error(FSI_ENAN, "GMRES: Arnoldi vector is not finite");
     for (int j = 0; j < enq; ++j) {  // the second passes that ran
       int ro = 0;
-      memcpy(&ro, est + 3 * j + 2, sizeof(int));
+      memcpy(&ro, reinterpret_cast<const char*>(est + 3 * j) + sizeof(double), sizeof(int));
       if (ro) prof_bytes(m, P_KRY_UPD, (j + 3) * vb);
     }
     FSI_LAUNCH(m, P_KRY_SMALL, lsq_kernel<<<1, 1, 0, m->stream>>>(K, jend, mm));
@@ -650,9 +694,12 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& blk, const double* rhs, double* x,
     m->Z_n = n * mm;
   }
   if (harvest && (rc = pcn::ensure_checkpoints(harvest))) return rc;
-  // Jacobi diagonal of the float64 operator (also the learned preconditioner's scale)
+  // Jacobi diagonal (also the learned preconditioner's scale), from the operator the
+  // inner solves apply: a preconditioner's rounding does not reach the refined solution,
+  // and the float64 diagonal costs as much as 20 float32 ones on this GPU
   if (o.precond == FSI_PC_JACOBI || o.precond == FSI_PC_LEARNED || harvest) {
-    if ((rc = op_diag(m, blk, m->wk + 3 * n, opflags & ~FSI_FP32))) return rc;
+    const unsigned dflags = o.precision == FSI_PREC_FP32_IR ? (opflags | FSI_FP32) : (opflags & ~FSI_FP32);
+    if ((rc = op_diag(m, blk, m->wk + 3 * n, dflags))) return rc;
     if ((rc = vec_recip(m, m->wk + 3 * n, m->dinv, n))) return rc;
   }
   if (o.precond == FSI_PC_NONE) {
