@@ -162,14 +162,21 @@ __global__ void to_float_kernel(const double* __restrict__ a, float* __restrict_
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) b[i] = (float)a[i];
 }
 
+int ensure_dx32(fsi_mesh* m) {
+  if (!m->dx32) FSI_CUDA(cudaMalloc(&m->dx32, sizeof(float) * 6 * (size_t)m->nn));
+  return FSI_OK;
+}
+
 int op_jvp(fsi_mesh* m, const BlockInfo& b, const double* dx, double* y, unsigned flags) {
   m->applies++;
   m->dof_applied += b.n;
   const bool f32 = flags & FSI_FP32;
-  if (f32) {  // float copy of the increment for the float32 kernels
-    if (!m->dx32) FSI_CUDA(cudaMalloc(&m->dx32, sizeof(float) * 6 * (size_t)m->nn));
-    FSI_LAUNCH(m, P_KRY_CONV, to_float_kernel<<<vec_grid(b.n), 256, 0, m->stream>>>(dx, m->dx32, b.n));
+  if (f32) {  // float copy of the increment for the float32 kernels (unless the caller wrote it)
+    if (int rc = ensure_dx32(m)) return rc;
+    if (!(flags & OP_DX32_READY))
+      FSI_LAUNCH(m, P_KRY_CONV, to_float_kernel<<<vec_grid(b.n), 256, 0, m->stream>>>(dx, m->dx32, b.n));
   }
+  flags &= ~OP_DX32_READY;
   if (b.kind == 0)
     return f32 ? launch_ns<float>(m, 1, dx, y, flags) : launch_ns<double>(m, 1, dx, y, flags);
   if (b.kind == 1)
@@ -411,7 +418,7 @@ int fsi_jvp(fsi_mesh* m, int32_t block, const fsi_state* st, const double* dx, d
   int rc = block_info(m, block, &b);
   if (rc) return rc;
   if ((rc = stage(m, st, flags & FSI_FP32))) return rc;
-  return op_jvp(m, b, dx, y, flags);
+  return op_jvp(m, b, dx, y, flags & ~OP_DX32_READY);
 }
 
 int fsi_diag(fsi_mesh* m, int32_t block, const fsi_state* st, double* d, uint32_t flags) {

@@ -121,6 +121,10 @@ int block_info(const fsi_mesh* m, int32_t block, BlockInfo* bi);
 // operator launches on staged state (ops_f64.cu / ops_f32.cu)
 int op_residual(fsi_mesh* m, const BlockInfo& b, double* r);
 int op_jvp(fsi_mesh* m, const BlockInfo& b, const double* dx, double* y, unsigned flags);
+// op_jvp flag, internal only: with FSI_FP32, the float32 increment is already in m->dx32
+// (the Krylov solver's preconditioner kernel wrote it) and dx is not read
+constexpr unsigned OP_DX32_READY = 0x80000000u;
+int ensure_dx32(fsi_mesh* m);  // allocates m->dx32 (6 x nn floats) on first use
 int op_diag(fsi_mesh* m, const BlockInfo& b, double* d, unsigned flags);
 int op_coeffs(fsi_mesh* m, int phase, double* gamma_beta);  // synchronises
 

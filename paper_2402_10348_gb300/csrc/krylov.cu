@@ -1,6 +1,7 @@
 // Krylov solver of libfsi: restarted right-preconditioned GMRES(m) (the paper's
 // linear solver, Section 2.5) on float64 vectors, optionally with a float32 operator
-// inside float64 iterative refinement.
+// inside float64 iterative refinement; the inner solves of the refinement keep their
+// Arnoldi basis in float32 (Hessenberg, Givens and every residual stay float64).
 //
 // Basis layout: the vectors V_0..V_m are stored chunk-interleaved, CH = 256
 // elements per chunk, all m+1 vectors of a chunk contiguous:
@@ -81,32 +82,43 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[K], int kc, dou
 }
 
 // --------------------------------------------------------- basis (chunked) kernels
+// The basis type VT is double for float64 solves and float for the inner solves of
+// iterative refinement (a float32 operator inside float64 refinement: the inner solve
+// only has to reduce its residual by ir_inner_rtol, far above float32 rounding, and the
+// refinement's float64 residual removes what the inner solve leaves).  Products and
+// per-thread sums are taken in VT, the sums across threads and CTAs in float64.  The work
+// vector w, the preconditioner diagonal and every vector outside the basis stay float64.
+
 // part[(ib + i) * G + cta] = sum over the CTA's chunks of V_{ib+i} . w, i < KC,
 // ib = i0 + KC * blockIdx.y; with SELF the KC+1-th row is w . w (row i0 + KC).
-template <int KC, bool SELF>
-__global__ void __launch_bounds__(VB) mdot_kernel(const double* __restrict__ V, int M1, int i0,
+template <int KC, bool SELF, typename VT>
+__global__ void __launch_bounds__(VB) mdot_kernel(const VT* __restrict__ V, int M1, int i0,
                                                   const double* __restrict__ w, int64_t n, double* part,
                                                   const int* skip) {
   if (skip && !*skip) return;
   constexpr int NA = KC + (SELF ? 1 : 0);
+  constexpr int NR = NA > 0 ? NA : 1;
   const int G = gridDim.x;
   const int ib = i0 + blockIdx.y * KC;
   const int64_t nch = (n + CH - 1) / CH;
   const int64_t per = (nch + G - 1) / G;
   const int64_t c0 = blockIdx.x * per, c1 = min(nch, c0 + per);
-  double acc[NA > 0 ? NA : 1];
+  VT acc[NR];
 #pragma unroll
-  for (int i = 0; i < NA; ++i) acc[i] = 0.0;
+  for (int i = 0; i < NR; ++i) acc[i] = VT(0);
   for (int64_t c = c0; c < c1; ++c) {
     const int64_t j = c * CH + threadIdx.x;
     if (j >= n) break;
-    const double wj = w[j];
-    const double* blk = V + c * (int64_t)M1 * CH + (int64_t)ib * CH + threadIdx.x;
+    const VT wj = (VT)w[j];
+    const VT* blk = V + c * (int64_t)M1 * CH + (int64_t)ib * CH + threadIdx.x;
 #pragma unroll
     for (int i = 0; i < KC; ++i) acc[i] += blk[i * CH] * wj;
     if (SELF) acc[NA - 1] += wj * wj;
   }
-  block_reduce_store<(NA > 0 ? NA : 1)>(acc, NA, part + (int64_t)ib * G + blockIdx.x, G);
+  double accd[NR];
+#pragma unroll
+  for (int i = 0; i < NR; ++i) accd[i] = (double)acc[i];
+  block_reduce_store<NR>(accd, NA, part + (int64_t)ib * G + blockIdx.x, G);
 }
 
 // out[i] = sum_c part[i*G + c] (fixed order), i = blockIdx.x
@@ -123,8 +135,9 @@ __global__ void sum_partials(const double* __restrict__ part, int G, double* out
 }
 
 // sum_{i<k} hs_i V_i[j] for the element of this thread in chunk blk (8 loads in flight)
-__device__ __forceinline__ double lin_comb_chunk(const double* __restrict__ hs, const double* __restrict__ blk, int k) {
-  double p[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+template <typename VT>
+__device__ __forceinline__ VT lin_comb_chunk(const VT* __restrict__ hs, const VT* __restrict__ blk, int k) {
+  VT p[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int i = 0;
   for (; i + 8 <= k; i += 8) {
 #pragma unroll
@@ -135,60 +148,63 @@ __device__ __forceinline__ double lin_comb_chunk(const double* __restrict__ hs, 
 }
 
 // w -= sum_{i<k} h_i V_i ; part[cta] = partial of |w|^2   (w contiguous)
-__global__ void __launch_bounds__(VB) upd_kernel(double* __restrict__ w, const double* __restrict__ V, int M1, int k,
+template <typename VT>
+__global__ void __launch_bounds__(VB) upd_kernel(double* __restrict__ w, const VT* __restrict__ V, int M1, int k,
                                                  const double* __restrict__ h, int64_t n, double* part,
                                                  const int* skip) {
   if (skip && !*skip) return;
-  __shared__ double hs[MMAX + 2];
-  for (int i = threadIdx.x; i < k; i += VB) hs[i] = h[i];
+  __shared__ VT hs[MMAX + 2];
+  for (int i = threadIdx.x; i < k; i += VB) hs[i] = (VT)h[i];
   __syncthreads();
   const int G = gridDim.x;
   const int64_t nch = (n + CH - 1) / CH;
   const int64_t per = (nch + G - 1) / G;
   const int64_t c0 = blockIdx.x * per, c1 = min(nch, c0 + per);
-  double nrm[1] = {0.0};
+  VT nrm = VT(0);
   for (int64_t c = c0; c < c1; ++c) {
     const int64_t j = c * CH + threadIdx.x;
     if (j >= n) break;
-    const double s = w[j] - lin_comb_chunk(hs, V + c * (int64_t)M1 * CH + threadIdx.x, k);
-    w[j] = s;
-    nrm[0] += s * s;
+    const VT s = (VT)w[j] - lin_comb_chunk<VT>(hs, V + c * (int64_t)M1 * CH + threadIdx.x, k);
+    w[j] = (double)s;
+    nrm += s * s;
   }
-  block_reduce_store<1>(nrm, 1, part + blockIdx.x, 1);
+  double nd[1] = {(double)nrm};
+  block_reduce_store<1>(nd, 1, part + blockIdx.x, 1);
 }
 
 // Pass-1 update fused with the pass-2 projections: w' = w - sum_{i<k} h_i V_i, the
 // partial |w'|^2 and the partial V_i . w' (i < k) of the updated vector, from one read
 // of the basis: a thread keeps the k basis values of its element in registers, uses
 // them for the update and then for the projections, and accumulates the projections
-// in its own shared-memory column; the columns are added once at the end.
+// in its own shared-memory column; the columns are added once at the end (float64).
 // KMAX: k rounded up to a multiple of 8.  Rows of part: i < k the projections, row k
 // the norm; part[row * G + cta].
 constexpr int UDB = 128;  // threads per CTA (two elements of each 256-element chunk)
-template <int KMAX>
-__global__ void __launch_bounds__(UDB) upd_dot_kernel(double* __restrict__ w, const double* __restrict__ V, int M1,
+template <int KMAX, typename VT>
+__global__ void __launch_bounds__(UDB) upd_dot_kernel(double* __restrict__ w, const VT* __restrict__ V, int M1,
                                                       int k, const double* __restrict__ h, int64_t n, double* part) {
-  extern __shared__ double sacc[];  // [KMAX + 1][UDB]
-  __shared__ double hs[KMAX];
+  extern __shared__ __align__(16) unsigned char upd_smem[];
+  VT* sacc = reinterpret_cast<VT*>(upd_smem);  // [KMAX + 1][UDB]
+  __shared__ VT hs[KMAX];
   const int t = threadIdx.x;
-  for (int i = t; i < KMAX; i += UDB) hs[i] = i < k ? h[i] : 0.0;
-  for (int i = 0; i <= KMAX; ++i) sacc[i * UDB + t] = 0.0;
+  for (int i = t; i < KMAX; i += UDB) hs[i] = i < k ? (VT)h[i] : VT(0);
+  for (int i = 0; i <= KMAX; ++i) sacc[i * UDB + t] = VT(0);
   __syncthreads();
   const int G = gridDim.x;
   const int64_t nch = (n + CH - 1) / CH;
   const int64_t per = (nch + G - 1) / G;
   const int64_t c0 = blockIdx.x * per, c1 = min(nch, c0 + per);
-  double nrm = 0.0;
+  VT nrm = VT(0);
   for (int64_t c = c0; c < c1; ++c) {
 #pragma unroll 1
     for (int half = 0; half < 2; ++half) {
       const int64_t j = c * CH + half * UDB + t;
       if (j >= n) continue;
-      const double* blk = V + c * (int64_t)M1 * CH + half * UDB + t;
-      double v[KMAX];
+      const VT* blk = V + c * (int64_t)M1 * CH + half * UDB + t;
+      VT v[KMAX];
 #pragma unroll
-      for (int i = 0; i < KMAX; ++i) v[i] = i < k ? blk[i * CH] : 0.0;
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      for (int i = 0; i < KMAX; ++i) v[i] = i < k ? blk[i * CH] : VT(0);
+      VT s0 = 0, s1 = 0, s2 = 0, s3 = 0;
 #pragma unroll
       for (int i = 0; i < KMAX; i += 4) {
         s0 += hs[i] * v[i];
@@ -196,8 +212,8 @@ __global__ void __launch_bounds__(UDB) upd_dot_kernel(double* __restrict__ w, co
         s2 += hs[i + 2] * v[i + 2];
         s3 += hs[i + 3] * v[i + 3];
       }
-      const double ww = w[j] - ((s0 + s1) + (s2 + s3));
-      w[j] = ww;
+      const VT ww = (VT)w[j] - ((s0 + s1) + (s2 + s3));
+      w[j] = (double)ww;
       nrm += ww * ww;
 #pragma unroll
       for (int i = 0; i < KMAX; ++i) sacc[i * UDB + t] += v[i] * ww;
@@ -208,24 +224,24 @@ __global__ void __launch_bounds__(UDB) upd_dot_kernel(double* __restrict__ w, co
   for (int i = t; i <= k; i += UDB) {
     const int row = i < k ? i : KMAX;
     double s = 0.0;
-    for (int q = 0; q < UDB; ++q) s += sacc[row * UDB + q];
+    for (int q = 0; q < UDB; ++q) s += (double)sacc[row * UDB + q];
     part[(int64_t)i * G + blockIdx.x] = s;
   }
 }
 
-template <int KMAX>
-static void launch_upd_dot(fsi_mesh* m, int G, double* w, const double* V, int M1, int k, const double* h,
-                           int64_t n) {
-  const size_t smem = sizeof(double) * (size_t)(KMAX + 1) * UDB;
+template <int KMAX, typename VT>
+static void launch_upd_dot(fsi_mesh* m, int G, double* w, const VT* V, int M1, int k, const double* h, int64_t n) {
+  const size_t smem = sizeof(VT) * (size_t)(KMAX + 1) * UDB;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(upd_dot_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(upd_dot_kernel<KMAX, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  upd_dot_kernel<KMAX><<<G, UDB, smem, m->stream>>>(w, V, M1, k, h, n, m->partials_dot);
+  upd_dot_kernel<KMAX, VT><<<G, UDB, smem, m->stream>>>(w, V, M1, k, h, n, m->partials_dot);
 }
 
-static void upd_dot(fsi_mesh* m, int G, double* w, const double* V, int M1, int k, const double* h, int64_t n) {
+template <typename VT>
+static void upd_dot(fsi_mesh* m, int G, double* w, const VT* V, int M1, int k, const double* h, int64_t n) {
   switch ((k + 7) / 8) {
     case 1: launch_upd_dot<8>(m, G, w, V, M1, k, h, n); break;
     case 2: launch_upd_dot<16>(m, G, w, V, M1, k, h, n); break;
@@ -239,7 +255,8 @@ static void upd_dot(fsi_mesh* m, int G, double* w, const double* V, int M1, int 
 }
 
 // V_slot[j] = src[j] * scale, scale = 1/sqrt(*n2) (n2 != null) or 1/K->nrm_fin
-__global__ void store_slot(double* __restrict__ V, int M1, int slot, const double* __restrict__ src, const double* n2,
+template <typename VT>
+__global__ void store_slot(VT* __restrict__ V, int M1, int slot, const double* __restrict__ src, const double* n2,
                            const KryDev* K, int64_t n) {
   double s;
   if (n2) {
@@ -249,35 +266,38 @@ __global__ void store_slot(double* __restrict__ V, int M1, int slot, const doubl
     s = nf > 0.0 ? 1.0 / nf : 0.0;
   }
   for (int64_t j = blockIdx.x * (int64_t)VB + threadIdx.x; j < n; j += (int64_t)gridDim.x * VB)
-    V[(j / CH) * (int64_t)M1 * CH + (int64_t)slot * CH + (j % CH)] = src[j] * s;
+    V[(j / CH) * (int64_t)M1 * CH + (int64_t)slot * CH + (j % CH)] = (VT)(src[j] * s);
 }
 
-// z = dinv * V_slot
-__global__ void precond_kernel(const double* __restrict__ V, int M1, int slot, const double* __restrict__ dinv,
-                               double* __restrict__ z, int64_t n) {
+// z = dinv * V_slot (ZT float: the float32 operator's increment, written directly)
+template <typename VT, typename ZT>
+__global__ void precond_kernel(const VT* __restrict__ V, int M1, int slot, const double* __restrict__ dinv,
+                               ZT* __restrict__ z, int64_t n) {
   for (int64_t j = blockIdx.x * (int64_t)VB + threadIdx.x; j < n; j += (int64_t)gridDim.x * VB)
-    z[j] = dinv[j] * V[(j / CH) * (int64_t)M1 * CH + (int64_t)slot * CH + (j % CH)];
+    z[j] = (ZT)(dinv[j] * (double)V[(j / CH) * (int64_t)M1 * CH + (int64_t)slot * CH + (j % CH)]);
 }
 
 // x += dinv * sum_i y_i V_i
+template <typename VT>
 __global__ void __launch_bounds__(VB) combine_kernel(double* __restrict__ x, const double* __restrict__ dinv,
-                                                     const double* __restrict__ V, int M1, int k, const KryDev* K,
+                                                     const VT* __restrict__ V, int M1, int k, const KryDev* K,
                                                      int64_t n) {
-  __shared__ double ys[MMAX];
-  for (int i = threadIdx.x; i < k; i += VB) ys[i] = K->y[i];
+  __shared__ VT ys[MMAX];
+  for (int i = threadIdx.x; i < k; i += VB) ys[i] = (VT)K->y[i];
   __syncthreads();
   const int64_t nch = (n + CH - 1) / CH;
   for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
     const int64_t j = c * CH + threadIdx.x;
     if (j >= n) continue;
-    x[j] += dinv[j] * lin_comb_chunk(ys, V + c * (int64_t)M1 * CH + threadIdx.x, k);
+    x[j] += dinv[j] * (double)lin_comb_chunk<VT>(ys, V + c * (int64_t)M1 * CH + threadIdx.x, k);
   }
 }
 
-// z = V_slot (contiguous copy of one basis vector)
-__global__ void extract_kernel(const double* __restrict__ V, int M1, int slot, double* __restrict__ z, int64_t n) {
+// z = V_slot (contiguous float64 copy of one basis vector)
+template <typename VT>
+__global__ void extract_kernel(const VT* __restrict__ V, int M1, int slot, double* __restrict__ z, int64_t n) {
   for (int64_t j = blockIdx.x * (int64_t)VB + threadIdx.x; j < n; j += (int64_t)gridDim.x * VB)
-    z[j] = V[(j / CH) * (int64_t)M1 * CH + (int64_t)slot * CH + (j % CH)];
+    z[j] = (double)V[(j / CH) * (int64_t)M1 * CH + (int64_t)slot * CH + (j % CH)];
 }
 
 // x += sum_i y_i Z_i (flexible GMRES: the stored preconditioned directions)
@@ -416,14 +436,14 @@ __global__ void fill_kernel(double* y, double v, int64_t n) {
 }
 
 // ---------------------------------------------------------------- host helpers
-template <int R, bool SELF>
-static void launch_mdot(fsi_mesh* m, dim3 grid, const double* V, int M1, int i0, const double* w, int64_t n,
+template <int R, bool SELF, typename VT>
+static void launch_mdot(fsi_mesh* m, dim3 grid, const VT* V, int M1, int i0, const double* w, int64_t n,
                         const int* skip) {
-  mdot_kernel<R, SELF><<<grid, VB, 0, m->stream>>>(V, M1, i0, w, n, m->partials_dot, skip);
+  mdot_kernel<R, SELF, VT><<<grid, VB, 0, m->stream>>>(V, M1, i0, w, n, m->partials_dot, skip);
 }
 
-template <bool SELF>
-static void launch_mdot_rem(fsi_mesh* m, int rem, dim3 g1, const double* V, int M1, int i0, const double* w,
+template <bool SELF, typename VT>
+static void launch_mdot_rem(fsi_mesh* m, int rem, dim3 g1, const VT* V, int M1, int i0, const double* w,
                             int64_t n, const int* skip) {
   switch (rem) {
     case 0: launch_mdot<0, SELF>(m, g1, V, M1, i0, w, n, skip); break;
@@ -446,7 +466,8 @@ static void launch_mdot_rem(fsi_mesh* m, int rem, dim3 g1, const double* V, int 
 }
 
 // out[0..k) = V_i . w for the basis slots i < k; with self, out[k] = w . w.
-static int basis_dots(fsi_mesh* m, const double* V, int M1, int k, const double* w, int64_t n, double* out, bool self,
+template <typename VT>
+static int basis_dots(fsi_mesh* m, const VT* V, int M1, int k, const double* w, int64_t n, double* out, bool self,
                       const int* skip = nullptr) {
   const int G = cgrid((n + CH - 1) / CH);
   const int nfull = k / DCH, rem = k % DCH;
@@ -460,14 +481,6 @@ static int basis_dots(fsi_mesh* m, const double* V, int M1, int k, const double*
   }
   const int rows = k + (self ? 1 : 0);
   FSI_LAUNCH(m, P_KRY_DOT, sum_partials<<<rows, VB, 0, m->stream>>>(m->partials_dot, G, out, skip));
-  return FSI_OK;
-}
-
-static int basis_update(fsi_mesh* m, double* w, const double* V, int M1, int k, const double* h, int64_t n,
-                        double* nrm_out, const int* skip = nullptr) {
-  const int G = cgrid((n + CH - 1) / CH);
-  FSI_LAUNCH(m, P_KRY_UPD, upd_kernel<<<G, VB, 0, m->stream>>>(w, V, M1, k, h, n, m->partials_dot, skip));
-  FSI_LAUNCH(m, P_KRY_UPD, sum_partials<<<1, VB, 0, m->stream>>>(m->partials_dot, G, nrm_out, skip));
   return FSI_OK;
 }
 
@@ -540,16 +553,19 @@ static int ensure_krylov(fsi_mesh* m, int64_t n, int mm) {
 }
 
 // One GMRES(m) solve A x = b from x = 0 with A = the block operator (flags) and the
-// right preconditioner diag(dinv).
-static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double* x, int mm, double rtol,
-                      int max_iter, unsigned flags, int* iters, int* restarts, double* rel_out, int* stalled,
-                      fsi_pc* pc = nullptr, fsi_pc* harvest = nullptr) {
+// right preconditioner diag(dinv).  VT: the basis type (float exactly when the operator
+// is the float32 one, i.e. the inner solves of iterative refinement).
+template <typename VT>
+static int gmres_core_t(fsi_mesh* m, const BlockInfo& blk, const double* b, double* x, int mm, double rtol,
+                        int max_iter, unsigned flags, int* iters, int* restarts, double* rel_out, int* stalled,
+                        fsi_pc* pc, fsi_pc* harvest) {
+  constexpr bool F32 = sizeof(VT) == 4;
   const bool alternate = (flags & FSI_PC_ALTERNATE) != 0;
   flags &= ~FSI_PC_ALTERNATE;
   const int64_t n = blk.n;
   const int M1 = m->kry_m + 1;
   const int G = vgrid(n);
-  double* V = m->V;
+  VT* V = reinterpret_cast<VT*>(m->V);  // the float basis reuses the float64 allocation
   double* r = m->wk;
   double* z = m->wk + n;
   double* t = m->wk + 2 * n;
@@ -586,28 +602,36 @@ static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double
     first_cycle = false;
     cycle_rel = rel;
     FSI_LAUNCH(m, P_KRY_SMALL, cycle_start<<<1, 1, 0, m->stream>>>(K, m->red, mm));
-    FSI_LAUNCH(m, P_KRYLOV, store_slot<<<G, VB, 0, m->stream>>>(V, M1, 0, r, m->red, K, n));
+    FSI_LAUNCH(m, P_KRYLOV, store_slot<VT><<<G, VB, 0, m->stream>>>(V, M1, 0, r, m->red, K, n));
     int jend = 0, enq = 0;
     bool done = false;
     const int jmax = std::min(mm, max_iter - *iters);
-    const double vb = 8.0 * (double)n;  // bytes of one vector
+    const double vb = (double)sizeof(VT) * (double)n;  // bytes of one basis vector
+    const double wb = 8.0 * (double)n;                 // bytes of the float64 work vector
     for (int j = 0; j < jmax && !done; ++j) {
       if (pc) {  // flexible GMRES: z_j = M(v_j), |v_j| = 1
         double* zj = m->Z + (int64_t)j * n;
         if (alternate && (j & 1)) {
           // every other direction is the plain Jacobi one: the least-squares step then
           // weights network and Jacobi directions separately
-          FSI_LAUNCH(m, P_KRYLOV, precond_kernel<<<G, VB, 0, m->stream>>>(V, M1, j, m->dinv, zj, n));
+          FSI_LAUNCH(m, P_KRYLOV, (precond_kernel<VT, double><<<G, VB, 0, m->stream>>>(V, M1, j, m->dinv, zj, n)));
         } else {
-          FSI_LAUNCH(m, P_KRYLOV, extract_kernel<<<G, VB, 0, m->stream>>>(V, M1, j, t, n));
+          FSI_LAUNCH(m, P_KRYLOV, extract_kernel<VT><<<G, VB, 0, m->stream>>>(V, M1, j, t, n));
           if ((rc = pcn::apply(pc, t, 1.0, m->dinv, zj))) return rc;
         }
         if ((rc = op_jvp(m, blk, zj, w, flags))) return rc;
       } else {
-        FSI_LAUNCH(m, P_KRYLOV, precond_kernel<<<G, VB, 0, m->stream>>>(V, M1, j, m->dinv, z, n));
-        if ((rc = op_jvp(m, blk, z, w, flags))) return rc;
+        if (F32) {
+          // the float32 increment goes straight to the operator's input buffer
+          FSI_LAUNCH(m, P_KRYLOV, (precond_kernel<VT, float><<<G, VB, 0, m->stream>>>(V, M1, j, m->dinv, m->dx32, n)));
+          if ((rc = op_jvp(m, blk, nullptr, w, flags | OP_DX32_READY))) return rc;
+        } else {
+          FSI_LAUNCH(m, P_KRYLOV, (precond_kernel<VT, double><<<G, VB, 0, m->stream>>>(V, M1, j, m->dinv, z, n)));
+          if ((rc = op_jvp(m, blk, z, w, flags))) return rc;
+        }
         // broadband training pairs: A z_j = w exactly for the operator just applied
-        if (harvest && j % 8 == 4 && n_arnoldi_pairs < 8) {
+        // (harvesting solves run with the float64 basis)
+        if (!F32 && harvest && j % 8 == 4 && n_arnoldi_pairs < 8) {
           if ((rc = pcn::add_pair(harvest, w, nullptr, z, nullptr, m->dinv))) return rc;
           ++n_arnoldi_pairs;
         }
@@ -617,17 +641,17 @@ static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double
       // pass-1 update fused with the pass-2 projections of the updated vector
       {
         const int Gc = cgrid((n + CH - 1) / CH);
-        FSI_LAUNCH(m, P_KRY_UPD, upd_dot(m, Gc, w, V, M1, j + 1, K->h, n));
+        FSI_LAUNCH(m, P_KRY_UPD, upd_dot<VT>(m, Gc, w, V, M1, j + 1, K->h, n));
         FSI_LAUNCH(m, P_KRY_UPD, sum_partials_decide<<<j + 2, VB, 0, m->stream>>>(m->partials_dot, Gc, K, j));
-        prof_bytes(m, P_KRY_DOT, (j + 2) * vb);  // j+1 basis vectors and w read once
-        prof_bytes(m, P_KRY_UPD, (j + 3) * vb);  // j+1 basis vectors and w read, w written
+        prof_bytes(m, P_KRY_DOT, (j + 1) * vb + wb);      // j+1 basis vectors and w read once
+        prof_bytes(m, P_KRY_UPD, (j + 1) * vb + 2 * wb);  // j+1 basis vectors and w read, w written
         // the pass-2 update only when the DGKS test asked for it (exits at once otherwise),
         // then its norm and the Givens step
-        FSI_LAUNCH(m, P_KRY_UPD, upd_kernel<<<Gc, VB, 0, m->stream>>>(w, V, M1, j + 1, K->h2, n, m->partials_dot,
-                                                                       &K->reorth));
+        FSI_LAUNCH(m, P_KRY_UPD, upd_kernel<VT><<<Gc, VB, 0, m->stream>>>(w, V, M1, j + 1, K->h2, n, m->partials_dot,
+                                                                           &K->reorth));
         FSI_LAUNCH(m, P_KRY_SMALL, sum_partials_givens<<<1, VB, 0, m->stream>>>(m->partials_dot, Gc, K, j, mm));
       }
-      FSI_LAUNCH(m, P_KRYLOV, store_slot<<<G, VB, 0, m->stream>>>(V, M1, j + 1, w, nullptr, K, n));
+      FSI_LAUNCH(m, P_KRYLOV, store_slot<VT><<<G, VB, 0, m->stream>>>(V, M1, j + 1, w, nullptr, K, n));
       // estimate, reorth and breakdown flags: one copy (the fields are adjacent)
       FSI_CUDA(cudaMemcpyAsync(est + 3 * j, &K->est, sizeof(double) + 2 * sizeof(int), cudaMemcpyDeviceToHost,
                                m->stream));
@@ -653,14 +677,14 @@ static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double
     for (int j = 0; j < enq; ++j) {  // the second passes that ran
       int ro = 0;
       memcpy(&ro, reinterpret_cast<const char*>(est + 3 * j) + sizeof(double), sizeof(int));
-      if (ro) prof_bytes(m, P_KRY_UPD, (j + 3) * vb);
+      if (ro) prof_bytes(m, P_KRY_UPD, (j + 1) * vb + 2 * wb);
     }
     FSI_LAUNCH(m, P_KRY_SMALL, lsq_kernel<<<1, 1, 0, m->stream>>>(K, jend, mm));
     if (pc) {
       FSI_LAUNCH(m, P_KRYLOV, zcombine_kernel<<<G, VB, 0, m->stream>>>(x, m->Z, jend, K, n));
     } else {
-      FSI_LAUNCH(m, P_KRYLOV, combine_kernel<<<cgrid((n + CH - 1) / CH), VB, 0, m->stream>>>(x, m->dinv, V, M1, jend,
-                                                                                            K, n));
+      FSI_LAUNCH(m, P_KRYLOV, combine_kernel<VT><<<cgrid((n + CH - 1) / CH), VB, 0, m->stream>>>(x, m->dinv, V, M1,
+                                                                                                jend, K, n));
     }
     // true residual r = b - A x
     if ((rc = op_jvp(m, blk, x, t, flags))) return rc;
@@ -670,6 +694,19 @@ static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double
   }
   *rel_out = rel;
   return FSI_OK;
+}
+
+static int gmres_core(fsi_mesh* m, const BlockInfo& blk, const double* b, double* x, int mm, double rtol,
+                      int max_iter, unsigned flags, int* iters, int* restarts, double* rel_out, int* stalled,
+                      fsi_pc* pc = nullptr, fsi_pc* harvest = nullptr) {
+  // harvesting solves keep the float64 basis: their Arnoldi pairs and refinement
+  // checkpoints are the training data of the learned preconditioner
+  if ((flags & FSI_FP32) && !harvest) {
+    if (int rc = ensure_dx32(m)) return rc;
+    return gmres_core_t<float>(m, blk, b, x, mm, rtol, max_iter, flags, iters, restarts, rel_out, stalled, pc,
+                               harvest);
+  }
+  return gmres_core_t<double>(m, blk, b, x, mm, rtol, max_iter, flags, iters, restarts, rel_out, stalled, pc, harvest);
 }
 
 int gmres_solve(fsi_mesh* m, const BlockInfo& blk, const double* rhs, double* x, const fsi_solve_opts& o,
@@ -685,7 +722,7 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& blk, const double* rhs, double* x,
   if (o.precond == FSI_PC_LEARNED && blk.kind == 0 && !pc)
     return set_error(FSI_EINVAL, "GMRES: FSI_PC_LEARNED without an attached preconditioner (fsi_set_pc)");
   fsi_pc* harvest = ((o.flags & FSI_HARVEST) && blk.kind == 0 && m->pc && m->pc->cap > 0) ? m->pc : nullptr;
-  const unsigned opflags = o.flags & ~(FSI_HARVEST | FSI_PC_ALTERNATE);
+  const unsigned opflags = o.flags & ~(FSI_HARVEST | FSI_PC_ALTERNATE | OP_DX32_READY);
   const unsigned alt = o.flags & FSI_PC_ALTERNATE;  // read by the flexible solves only
   if (pc && (m->Z_n < n * mm || !m->Z)) {
     cudaFree(m->Z);

@@ -72,6 +72,7 @@ __host__ __device__ constexpr int sym_idx(int k, int l) {
 struct OutDesc {
   double* y;            // output block [NC][nn]
   const double* dx;     // JVP input block (Dirichlet rows copy it), or null
+  const float* dx32;    // its float copy: the rows copy this one when dx is null
   const double* x;      // state x^{n+1} (residual Dirichlet rows), or null
   const uint8_t* mask;  // Dirichlet mask (NS only): bits 0-2 velocity, bit 3 pressure
   const double* vD;     // Dirichlet velocity values [3][nn]
@@ -317,7 +318,7 @@ struct NSOp {
         if (MODE == 0) {
           *y = out.x[(int64_t)k * nn + nc.n] - (k < 3 ? out.vD[(int64_t)k * nn + nc.n] : 0.0);
         } else if (MODE == 1) {
-          *y = out.dx[(int64_t)k * nn + nc.n];
+          *y = out.dx ? out.dx[(int64_t)k * nn + nc.n] : (double)out.dx32[(int64_t)k * nn + nc.n];
         } else {
           *y = 1.0;
         }

@@ -154,6 +154,7 @@ int ns_pass(fsi_mesh* m, const double* dx, double* y, unsigned flags, int s0, in
   fill_common(m, op.rh, &op.W);
   op.out.y = y;
   op.out.dx = dx;
+  op.out.dx32 = sizeof(T) == 4 ? m->dx32 : nullptr;
   op.out.x = m->staged_x;
   op.out.mask = m->mask;
   op.out.vD = m->vD;
