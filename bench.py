@@ -417,7 +417,7 @@ def traffic_record(kernel: str):
     return rec if h.hexdigest() == rec["sha256"] else None
 
 
-def roofline(name, launches, ms, nbytes, d, pk):
+def roofline(name, launches, ms, nbytes, d, pk, basis_f64=True):
     """Roofline of one kernel class over the timed region: HBM-bound classes from the
     algorithmic bytes their launch sites declare, ALU-bound element operators from
     the flop count of one element evaluation times the elements of a launch."""
@@ -434,9 +434,10 @@ def roofline(name, launches, ms, nbytes, d, pk):
                    peak_src=pk["hbm_src"] + " (MEASURED_PEAKS.json copy, read+write)")
         if rec is not None:
             out["traffic_note"] = rec["note"]
-        if name.startswith("krylov_dot") or name.startswith("krylov_update"):
-            # the second roof of the projections and updates: one float64 FMA per float64
-            # the launch reads (GB300 issues ~0.63 T DFMA/s, one per 8 bytes at 5 TB/s)
+        if basis_f64 and (name.startswith("krylov_dot") or name.startswith("krylov_update")):
+            # the second roof of the float64 projections and updates: one float64 FMA per
+            # float64 the launch reads (GB300 issues ~0.63 T DFMA/s, one per 8 bytes at
+            # 5 TB/s); a float32 basis has no such roof
             tf = nbytes / 8.0 * 2.0 / (ms / 1e3) / 1e12
             out["alu_fp64"] = {"achieved": round(tf, 3), "peak": round(pk["fp64_tflops"], 3), "unit": "TFLOP/s",
                                "frac": round(tf / pk["fp64_tflops"], 4),
@@ -515,7 +516,6 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    fsi.fsi_profile(mesh, True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     dof, infos = 0, []
@@ -528,9 +528,28 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.barrier()
     ms_local = e0.elapsed_time(e1)
+    final = (x.clone(), xn.clone(), xdn.clone())
+    # the same steps again from the same state with every launch bracketed by CUDA
+    # events (the library's profiler): per-class launch counts and device times.  The
+    # solver is deterministic, so the replay runs the timed region's launches; the
+    # events cost host time per launch and are kept out of the timed region itself.
+    for a, b in zip((x, xn, xdn), snapshot):
+        a.copy_(b)
+    torch.cuda.synchronize()
+    fsi.fsi_profile(mesh, True)
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    replay = [step() for _ in range(args.steps)]
+    r1.record(stream)
+    torch.cuda.synchronize()
     prof = fsi.fsi_profile_read(mesh)
     fsi.fsi_profile(mesh, False)
     clk = clocks.stop()
+    replay_same = all(a.gmres_iters_ns == b.gmres_iters_ns and a.gmres_iters_ac == b.gmres_iters_ac
+                      and a.gmres_iters_b == b.gmres_iters_b and a.nl_iters == b.nl_iters
+                      for a, b in zip(infos, replay))
+    replay_same = replay_same and all(bool(torch.equal(a, b)) for a, b in zip((x, xn, xdn), final))
+    profiled = {"ms_per_step": round(r0.elapsed_time(r1) / args.steps, 3), "identical_to_timed": replay_same}
     ms = reduce_max(ms_local, world, dev)
     dof_all = reduce_sum(float(dof), world, dev)
     seconds = ms / 1e3
@@ -541,12 +560,12 @@ def run_gpu(args):
     # dominant operator kernel is reported beside it
     pk = peaks()
     dom = max(prof.items(), key=lambda kv: kv[1][1])
-    roof = roofline(dom[0], *dom[1], d, pk)
+    roof = roofline(dom[0], *dom[1], d, pk, basis_f64=prec == fsi.FSI_PREC_FP64)
     ops = {k: v for k, v in prof.items() if flops_per_element(k, d.n_solid) > 0 and v[0] > 0}
     roof_op = None
     if ops:
         oname, ov = max(ops.items(), key=lambda kv: kv[1][1])
-        roof_op = roofline(oname, *ov, d, pk)
+        roof_op = roofline(oname, *ov, d, pk, basis_f64=prec == fsi.FSI_PREC_FP64)
 
     learned = None
     if pc is not None:
@@ -566,13 +585,16 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == fsi.FSI_PREC_FP32_IR else "f64",
-        "precision": ("float32 operator applies inside float64 iterative refinement; float64 residuals, "
-                      "Gram-Schmidt, Hessenberg" if prec == fsi.FSI_PREC_FP32_IR else "float64 throughout"),
+        "precision": ("float32 operator applies and float32 Arnoldi basis inside float64 iterative "
+                      "refinement; float64 residuals, reductions, Hessenberg and Givens"
+                      if prec == fsi.FSI_PREC_FP32_IR else "float64 throughout"),
         "data": "synthetic (seeded icosphere surface, initial phases by the grid-cell method)",
         "config": {"workload": WORKLOAD, "nodes": d.nn, "dof_per_node": d.ncomp, "dt": d.dt,
                    "nl_iters_max": wl.k_max, "gmres": f"Jacobi GMRES({args.restart}) rtol 1e-8, stop on stagnation",
-                   "l2": "inputs larger than L2: the NS solve streams an (m+1) x 1.1M float64 Krylov basis "
-                         "(272 MB at m = 30) every restart cycle",
+                   "l2": ("inputs larger than L2: a time step streams the 64^3 state, the float64 "
+                          "refinement vectors and the (m+1) x 1.1M Krylov basis of the NS block "
+                          f"({(args.restart + 1) * 4 * d.nn * (4 if prec == fsi.FSI_PREC_FP32_IR else 8) / 1e6:.0f}"
+                          " MB) every restart cycle, against a 129 MB L2"),
                    "parallelism": f"replicas x{world}"},
         "s_per_timestep": round(ms / args.steps / 1e3, 5),
         "step_stats": {"nl_iters": [i.nl_iters for i in infos],
@@ -582,6 +604,7 @@ def run_gpu(args):
                        "worst_rel_res": max(i.worst_rel_res for i in infos),
                        "stalled_solves": [i.stalled_solves for i in infos]},
         "gpu_launches": launches,
+        "profiled_replay": profiled,
         "kernel_ms": {k: [v[0], round(v[1], 3)] for k, v in prof.items() if v[0] > 0},
         "roofline": roof,
         "roofline_operator": roof_op,

@@ -11,7 +11,8 @@
 // 3.9 vs 2.7 TB/s read on GB300 for 33 vectors of the 64^3 NS block).
 //
 // Arnoldi step j (D = diag(dinv)):
-//   z = D V_j;  w = J z   (w: a contiguous work vector written by the operator)
+//   w = J z, z = D V_j    (z written together with V_j; w: a contiguous work vector
+//                          written by the operator)
 //   h = V^T w and |w|^2 in one pass over V_0..V_j      (mdot_kernel)
 //   w -= V h, |w|^2 and h2 = V^T w (the second pass's projections of the updated w)
 //   in one pass                                           (upd_dot_kernel)
@@ -19,7 +20,7 @@
 //   re-orthogonalization test; that update is launched always and exits at once when
 //   the device-side flag says it is not needed)
 //   Givens rotation of the new Hessenberg column and the residual estimate on the
-//   device; V_{j+1} = w / |w| stored into its slot.
+//   device; V_{j+1} = w / |w| stored into its slot, and z = D V_{j+1} beside it.
 // The host enqueues step j and only then waits for step j-1's residual estimate
 // (copied to pinned memory), so it never stalls the GPU between steps; at most one
 // step beyond convergence is computed and ignored.  The least-squares solution and
@@ -254,10 +255,12 @@ static void upd_dot(fsi_mesh* m, int G, double* w, const VT* V, int M1, int k, c
   }
 }
 
-// V_slot[j] = src[j] * scale, scale = 1/sqrt(*n2) (n2 != null) or 1/K->nrm_fin
+// V_slot[j] = src[j] * scale, scale = 1/sqrt(*n2) (n2 != null) or 1/K->nrm_fin; with z,
+// also the next operator input z[j] = dinv[j] * V_slot[j] from the stored value (the
+// float32 operator's increment when VT is float)
 template <typename VT>
 __global__ void store_slot(VT* __restrict__ V, int M1, int slot, const double* __restrict__ src, const double* n2,
-                           const KryDev* K, int64_t n) {
+                           const KryDev* K, int64_t n, const double* __restrict__ dinv, VT* __restrict__ z) {
   double s;
   if (n2) {
     s = 1.0 / sqrt(*n2);
@@ -265,8 +268,11 @@ __global__ void store_slot(VT* __restrict__ V, int M1, int slot, const double* _
     const double nf = K->nrm_fin;
     s = nf > 0.0 ? 1.0 / nf : 0.0;
   }
-  for (int64_t j = blockIdx.x * (int64_t)VB + threadIdx.x; j < n; j += (int64_t)gridDim.x * VB)
-    V[(j / CH) * (int64_t)M1 * CH + (int64_t)slot * CH + (j % CH)] = (VT)(src[j] * s);
+  for (int64_t j = blockIdx.x * (int64_t)VB + threadIdx.x; j < n; j += (int64_t)gridDim.x * VB) {
+    const VT v = (VT)(src[j] * s);
+    V[(j / CH) * (int64_t)M1 * CH + (int64_t)slot * CH + (j % CH)] = v;
+    if (z) z[j] = (VT)(dinv[j] * (double)v);
+  }
 }
 
 // z = dinv * V_slot (ZT float: the float32 operator's increment, written directly)
@@ -602,7 +608,9 @@ static int gmres_core_t(fsi_mesh* m, const BlockInfo& blk, const double* b, doub
     first_cycle = false;
     cycle_rel = rel;
     FSI_LAUNCH(m, P_KRY_SMALL, cycle_start<<<1, 1, 0, m->stream>>>(K, m->red, mm));
-    FSI_LAUNCH(m, P_KRYLOV, store_slot<VT><<<G, VB, 0, m->stream>>>(V, M1, 0, r, m->red, K, n));
+    // the operator input of the plain (Jacobi) steps: z = dinv V_j, written with V_j
+    VT* zn = pc ? nullptr : (F32 ? reinterpret_cast<VT*>(m->dx32) : reinterpret_cast<VT*>(z));
+    FSI_LAUNCH(m, P_KRYLOV, store_slot<VT><<<G, VB, 0, m->stream>>>(V, M1, 0, r, m->red, K, n, m->dinv, zn));
     int jend = 0, enq = 0;
     bool done = false;
     const int jmax = std::min(mm, max_iter - *iters);
@@ -621,12 +629,11 @@ static int gmres_core_t(fsi_mesh* m, const BlockInfo& blk, const double* b, doub
         }
         if ((rc = op_jvp(m, blk, zj, w, flags))) return rc;
       } else {
+        // z = dinv V_j was written with V_j (the float32 increment straight into the
+        // operator's input buffer)
         if (F32) {
-          // the float32 increment goes straight to the operator's input buffer
-          FSI_LAUNCH(m, P_KRYLOV, (precond_kernel<VT, float><<<G, VB, 0, m->stream>>>(V, M1, j, m->dinv, m->dx32, n)));
           if ((rc = op_jvp(m, blk, nullptr, w, flags | OP_DX32_READY))) return rc;
         } else {
-          FSI_LAUNCH(m, P_KRYLOV, (precond_kernel<VT, double><<<G, VB, 0, m->stream>>>(V, M1, j, m->dinv, z, n)));
           if ((rc = op_jvp(m, blk, z, w, flags))) return rc;
         }
         // broadband training pairs: A z_j = w exactly for the operator just applied
@@ -651,7 +658,7 @@ static int gmres_core_t(fsi_mesh* m, const BlockInfo& blk, const double* b, doub
                                                                            &K->reorth));
         FSI_LAUNCH(m, P_KRY_SMALL, sum_partials_givens<<<1, VB, 0, m->stream>>>(m->partials_dot, Gc, K, j, mm));
       }
-      FSI_LAUNCH(m, P_KRYLOV, store_slot<VT><<<G, VB, 0, m->stream>>>(V, M1, j + 1, w, nullptr, K, n));
+      FSI_LAUNCH(m, P_KRYLOV, store_slot<VT><<<G, VB, 0, m->stream>>>(V, M1, j + 1, w, nullptr, K, n, m->dinv, zn));
       // estimate, reorth and breakdown flags: one copy (the fields are adjacent)
       FSI_CUDA(cudaMemcpyAsync(est + 3 * j, &K->est, sizeof(double) + 2 * sizeof(int), cudaMemcpyDeviceToHost,
                                m->stream));

@@ -26,6 +26,8 @@ def test_roofline_hbm_and_alu():
     assert r["frac"] == pytest.approx(1.0, rel=1e-3)
     # the projections' second roof: one float64 FMA per float64 read
     assert r["alu_fp64"]["achieved"] == pytest.approx(13.55e9 / 8 * 2 / 2e-3 / 1e12, rel=1e-3)
+    # a float32 basis (the inner solves of refinement) has no float64 roof
+    assert "alu_fp64" not in bench.roofline("krylov_dot", 10, 2.0, 13.55e9, d, pk, basis_f64=False)
     r = bench.roofline("ns_jvp_f32", 4, 1.0, 0.0, d, pk)
     flops = 8 * (858 + 407 * d.n_solid) * d.ne
     assert r["bound"] == "alu"
