@@ -122,6 +122,64 @@ __global__ void __launch_bounds__(VB) mdot_kernel(const VT* __restrict__ V, int 
   block_reduce_store<NR>(accd, NA, part + (int64_t)ib * G + blockIdx.x, G);
 }
 
+// The float32 basis: the same projections with 16-byte loads.  A CTA works on four
+// chunks at a time, a thread on four adjacent elements of one chunk (one float4 per
+// basis vector), so a warp moves as many bytes per load as with a float64 basis and
+// keeps as many in flight.  Elements at or past n (the ragged end of the last chunk,
+// whose basis slots hold stale bytes) are never read.
+template <int KC, bool SELF>
+__global__ void __launch_bounds__(VB) mdot4_kernel(const float* __restrict__ V, int M1, int i0,
+                                                   const double* __restrict__ w, int64_t n, double* part,
+                                                   const int* skip) {
+  if (skip && !*skip) return;
+  constexpr int NA = KC + (SELF ? 1 : 0);
+  constexpr int NR = NA > 0 ? NA : 1;
+  const int G = gridDim.x;
+  const int ib = i0 + blockIdx.y * KC;
+  const int64_t nch = (n + CH - 1) / CH;
+  const int64_t per = (nch + G - 1) / G;
+  const int64_t c0 = blockIdx.x * per, c1 = min(nch, c0 + per);
+  const int sub = threadIdx.x >> 6;       // which of the CTA's four chunks
+  const int e0 = (threadIdx.x & 63) * 4;  // first of the thread's four elements
+  float acc[NR];
+#pragma unroll
+  for (int i = 0; i < NR; ++i) acc[i] = 0.f;
+  for (int64_t c = c0 + sub; c < c1; c += 4) {
+    const int64_t j = c * CH + e0;
+    if (j >= n) break;
+    const float* blk = V + c * (int64_t)M1 * CH + (int64_t)ib * CH + e0;
+    float w0, w1, w2, w3;
+    if (j + 4 <= n) {
+      const double2 a = *reinterpret_cast<const double2*>(w + j);
+      const double2 b = *reinterpret_cast<const double2*>(w + j + 2);
+      w0 = (float)a.x, w1 = (float)a.y, w2 = (float)b.x, w3 = (float)b.y;
+#pragma unroll
+      for (int i = 0; i < KC; ++i) {
+        const float4 v = *reinterpret_cast<const float4*>(blk + i * CH);
+        acc[i] += (v.x * w0 + v.y * w1) + (v.z * w2 + v.w * w3);
+      }
+    } else {
+      w0 = (float)w[j];
+      w1 = j + 1 < n ? (float)w[j + 1] : 0.f;
+      w2 = j + 2 < n ? (float)w[j + 2] : 0.f;
+      w3 = 0.f;
+#pragma unroll
+      for (int i = 0; i < KC; ++i) {
+        const float* p = blk + i * CH;
+        float t = p[0] * w0;
+        if (j + 1 < n) t += p[1] * w1;
+        if (j + 2 < n) t += p[2] * w2;
+        acc[i] += t;
+      }
+    }
+    if (SELF) acc[NA - 1] += (w0 * w0 + w1 * w1) + (w2 * w2 + w3 * w3);
+  }
+  double accd[NR];
+#pragma unroll
+  for (int i = 0; i < NR; ++i) accd[i] = (double)acc[i];
+  block_reduce_store<NR>(accd, NA, part + (int64_t)ib * G + blockIdx.x, G);
+}
+
 // out[i] = sum_c part[i*G + c] (fixed order), i = blockIdx.x
 __global__ void sum_partials(const double* __restrict__ part, int G, double* out, const int* skip) {
   if (skip && !*skip) return;
@@ -230,15 +288,88 @@ __global__ void __launch_bounds__(UDB) upd_dot_kernel(double* __restrict__ w, co
   }
 }
 
+// The fused update for the float32 basis: a thread takes two adjacent elements of each
+// chunk (one float2 per basis vector, one double2 of w), so a warp moves as many bytes
+// per load as with a float64 basis.  Elements at or past n are never read.
+template <int KMAX>
+__global__ void __launch_bounds__(UDB) upd_dot2_kernel(double* __restrict__ w, const float* __restrict__ V, int M1,
+                                                       int k, const double* __restrict__ h, int64_t n, double* part) {
+  extern __shared__ __align__(16) unsigned char upd_smem[];
+  float* sacc = reinterpret_cast<float*>(upd_smem);  // [KMAX + 1][UDB]
+  __shared__ float hs[KMAX];
+  const int t = threadIdx.x;
+  for (int i = t; i < KMAX; i += UDB) hs[i] = i < k ? (float)h[i] : 0.f;
+  for (int i = 0; i <= KMAX; ++i) sacc[i * UDB + t] = 0.f;
+  __syncthreads();
+  const int G = gridDim.x;
+  const int64_t nch = (n + CH - 1) / CH;
+  const int64_t per = (nch + G - 1) / G;
+  const int64_t c0 = blockIdx.x * per, c1 = min(nch, c0 + per);
+  const int e0 = 2 * t;
+  float nrm = 0.f;
+  for (int64_t c = c0; c < c1; ++c) {
+    const int64_t j = c * CH + e0;
+    if (j >= n) break;
+    const bool pair = j + 2 <= n;
+    const float* blk = V + c * (int64_t)M1 * CH + e0;
+    float2 v[KMAX];
+    if (pair) {
+#pragma unroll
+      for (int i = 0; i < KMAX; ++i) v[i] = i < k ? *reinterpret_cast<const float2*>(blk + i * CH) : make_float2(0.f, 0.f);
+    } else {
+#pragma unroll
+      for (int i = 0; i < KMAX; ++i) v[i] = make_float2(i < k ? blk[i * CH] : 0.f, 0.f);
+    }
+    float sx0 = 0.f, sx1 = 0.f, sy0 = 0.f, sy1 = 0.f;
+#pragma unroll
+    for (int i = 0; i < KMAX; i += 2) {
+      sx0 += hs[i] * v[i].x;
+      sx1 += hs[i + 1] * v[i + 1].x;
+      sy0 += hs[i] * v[i].y;
+      sy1 += hs[i + 1] * v[i + 1].y;
+    }
+    float wx, wy;
+    if (pair) {
+      const double2 wd = *reinterpret_cast<const double2*>(w + j);
+      wx = (float)wd.x - (sx0 + sx1);
+      wy = (float)wd.y - (sy0 + sy1);
+      *reinterpret_cast<double2*>(w + j) = make_double2((double)wx, (double)wy);
+    } else {
+      wx = (float)w[j] - (sx0 + sx1);
+      wy = 0.f;
+      w[j] = (double)wx;
+    }
+    nrm += wx * wx + wy * wy;
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) sacc[i * UDB + t] += v[i].x * wx + v[i].y * wy;
+  }
+  sacc[KMAX * UDB + t] = nrm;
+  __syncthreads();
+  for (int i = t; i <= k; i += UDB) {
+    const int row = i < k ? i : KMAX;
+    double s = 0.0;
+    for (int q = 0; q < UDB; ++q) s += (double)sacc[row * UDB + q];
+    part[(int64_t)i * G + blockIdx.x] = s;
+  }
+}
+
 template <int KMAX, typename VT>
 static void launch_upd_dot(fsi_mesh* m, int G, double* w, const VT* V, int M1, int k, const double* h, int64_t n) {
   const size_t smem = sizeof(VT) * (size_t)(KMAX + 1) * UDB;
   static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(upd_dot_kernel<KMAX, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
+  if constexpr (sizeof(VT) == 4) {
+    if (!attr) {
+      cudaFuncSetAttribute(upd_dot2_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = true;
+    }
+    upd_dot2_kernel<KMAX><<<G, UDB, smem, m->stream>>>(w, V, M1, k, h, n, m->partials_dot);
+  } else {
+    if (!attr) {
+      cudaFuncSetAttribute(upd_dot_kernel<KMAX, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = true;
+    }
+    upd_dot_kernel<KMAX, VT><<<G, UDB, smem, m->stream>>>(w, V, M1, k, h, n, m->partials_dot);
   }
-  upd_dot_kernel<KMAX, VT><<<G, UDB, smem, m->stream>>>(w, V, M1, k, h, n, m->partials_dot);
 }
 
 template <typename VT>
@@ -445,7 +576,10 @@ __global__ void fill_kernel(double* y, double v, int64_t n) {
 template <int R, bool SELF, typename VT>
 static void launch_mdot(fsi_mesh* m, dim3 grid, const VT* V, int M1, int i0, const double* w, int64_t n,
                         const int* skip) {
-  mdot_kernel<R, SELF, VT><<<grid, VB, 0, m->stream>>>(V, M1, i0, w, n, m->partials_dot, skip);
+  if constexpr (sizeof(VT) == 4)
+    mdot4_kernel<R, SELF><<<grid, VB, 0, m->stream>>>(V, M1, i0, w, n, m->partials_dot, skip);
+  else
+    mdot_kernel<R, SELF, VT><<<grid, VB, 0, m->stream>>>(V, M1, i0, w, n, m->partials_dot, skip);
 }
 
 template <bool SELF, typename VT>
