@@ -82,6 +82,28 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[K], int kc, dou
   }
 }
 
+// The same in float32 up to the CTA's sums, which are stored as float64: this GPU
+// issues float64 adds at 1/64 of the float32 rate, so a float64 tree over every
+// thread's sums costs more than the float32 basis kernel's streaming.
+template <int K>
+__device__ __forceinline__ void block_reduce_store_f(float (&acc)[K], int kc, double* out, int stride) {
+  __shared__ float smf[K][VB / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    float v = acc[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) smf[i][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kc) {
+    float s = 0.f;
+    for (int wi = 0; wi < VB / 32; ++wi) s += smf[threadIdx.x][wi];
+    out[threadIdx.x * stride] = (double)s;
+  }
+}
+
 // --------------------------------------------------------- basis (chunked) kernels
 // The basis type VT is double for float64 solves and float for the inner solves of
 // iterative refinement (a float32 operator inside float64 refinement: the inner solve
@@ -174,10 +196,7 @@ __global__ void __launch_bounds__(VB) mdot4_kernel(const float* __restrict__ V, 
     }
     if (SELF) acc[NA - 1] += (w0 * w0 + w1 * w1) + (w2 * w2 + w3 * w3);
   }
-  double accd[NR];
-#pragma unroll
-  for (int i = 0; i < NR; ++i) accd[i] = (double)acc[i];
-  block_reduce_store<NR>(accd, NA, part + (int64_t)ib * G + blockIdx.x, G);
+  block_reduce_store_f<NR>(acc, NA, part + (int64_t)ib * G + blockIdx.x, G);
 }
 
 // out[i] = sum_c part[i*G + c] (fixed order), i = blockIdx.x
@@ -239,6 +258,7 @@ __global__ void __launch_bounds__(VB) upd_kernel(double* __restrict__ w, const V
 // KMAX: k rounded up to a multiple of 8.  Rows of part: i < k the projections, row k
 // the norm; part[row * G + cta].
 constexpr int UDB = 128;  // threads per CTA (two elements of each 256-element chunk)
+static_assert(UDB == 128, "the row sums take four columns per lane");
 template <int KMAX, typename VT>
 __global__ void __launch_bounds__(UDB) upd_dot_kernel(double* __restrict__ w, const VT* __restrict__ V, int M1,
                                                       int k, const double* __restrict__ h, int64_t n, double* part) {
@@ -345,11 +365,14 @@ __global__ void __launch_bounds__(UDB) upd_dot2_kernel(double* __restrict__ w, c
   }
   sacc[KMAX * UDB + t] = nrm;
   __syncthreads();
-  for (int i = t; i <= k; i += UDB) {
-    const int row = i < k ? i : KMAX;
-    double s = 0.0;
-    for (int q = 0; q < UDB; ++q) s += (double)sacc[row * UDB + q];
-    part[(int64_t)i * G + blockIdx.x] = s;
+  // one warp per row, lanes on consecutive columns (no bank conflicts), float32 sums
+  const int lane = t & 31;
+  for (int i = t >> 5; i <= k; i += UDB / 32) {
+    const float* rp = sacc + (i < k ? i : KMAX) * UDB;
+    float s = (rp[lane] + rp[lane + 32]) + (rp[lane + 64] + rp[lane + 96]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) part[(int64_t)i * G + blockIdx.x] = (double)s;
   }
 }
 
