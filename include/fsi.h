@@ -161,7 +161,10 @@ int fsi_fix_gamma(fsi_mesh* mesh, int32_t phase, double gamma);
 #define FSI_PC_ALTERNATE 0x20u
 
 #define FSI_PREC_FP64 0     /* operator applies in float64                         */
-#define FSI_PREC_FP32_IR 1  /* float32 operator inside float64 iterative refinement */
+#define FSI_PREC_FP32_IR 1  /* float32 operator inside float64 iterative refinement: the
+                               inner solves keep their Arnoldi basis in float32 (float64
+                               Hessenberg, Givens and residuals); FSI_HARVEST solves keep
+                               the float64 basis */
 
 typedef struct {
   int32_t m;          /* restart length (GMRES(m)), <= 64                         */
