@@ -380,6 +380,22 @@ def flops_per_element(kernel: str, n_solid: int) -> float:
     return 0.0
 
 
+def operator_rates(prof: dict, nn: int) -> dict:
+    """GDoF/s of each element-operator class over the profiled steps: block DoF per
+    launch (NS 4 nn, one AC phase nn, one solid's B 6 nn) x launches / summed event
+    time.  One launch is one apply on a mesh whose solids fit one operator pass (the
+    cavity's one solid does)."""
+    dof = {"ns": 4 * nn, "ac": nn, "b": 6 * nn}
+    out = {}
+    for k, (launches, ms) in prof.items():
+        kind = k.split("_")[0]
+        if kind not in dof or not ("_jvp_" in k or k.endswith("_residual")) or launches <= 0 or ms <= 0:
+            continue
+        out[k] = {"gdofs": round(dof[kind] * launches / (ms / 1e3) / 1e9, 3),
+                  "us_per_launch": round(ms / launches * 1e3, 2)}
+    return out
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     pk = {}
@@ -606,6 +622,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "profiled_replay": profiled,
         "kernel_ms": {k: [v[0], round(v[1], 3)] for k, v in prof.items() if v[0] > 0},
+        "operator_gdofs": operator_rates({k: (v[0], v[1]) for k, v in prof.items()}, d.nn),
         "roofline": roof,
         "roofline_operator": roof_op,
         "clocks": clk,

@@ -72,3 +72,15 @@ def test_rank_reductions_gloo_world_size_2():
     for p in ps:
         p.join(timeout=60)
     assert all(r[1] == 2.0 and r[2] == 30.0 for r in res)
+
+
+def test_operator_rates():
+    prof = {"ns_jvp_f32": (10, 2.0), "ns_jvp_f64": (2, 12.0), "ac_residual": (4, 0.4), "b_jvp_f32": (3, 0.6),
+            "krylov_dot": (100, 5.0), "ns_diag": (1, 0.1), "stage": (0, 0.0)}
+    r = bench.operator_rates(prof, 1000)
+    assert set(r) == {"ns_jvp_f32", "ns_jvp_f64", "ac_residual", "b_jvp_f32"}
+    assert r["ns_jvp_f32"]["gdofs"] == pytest.approx(4000 * 10 / 2e-3 / 1e9, rel=1e-3)
+    assert r["ac_residual"]["gdofs"] == pytest.approx(1000 * 4 / 0.4e-3 / 1e9, rel=1e-3)
+    assert r["b_jvp_f32"]["gdofs"] == pytest.approx(6000 * 3 / 0.6e-3 / 1e9, rel=1e-3)
+    assert r["ns_jvp_f64"]["us_per_launch"] == pytest.approx(6000.0)
+
