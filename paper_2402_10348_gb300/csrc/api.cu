@@ -3,6 +3,9 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "internal.h"
 
@@ -18,6 +21,19 @@ int set_error(int code, const std::string& msg) {
 int cuda_check(cudaError_t e, const char* what) {
   g_err = std::string(what) + ": " + cudaGetErrorString(e);
   return e == cudaErrorMemoryAllocation ? FSI_ENOMEM : FSI_ECUDA;
+}
+
+int ensure_smem_attr(const void* func, size_t bytes) {
+  int dev = 0;
+  FSI_CUDA(cudaGetDevice(&dev));
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> done;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& have = done[std::make_pair(func, dev)];
+  if (have >= bytes) return FSI_OK;
+  FSI_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  have = bytes;
+  return FSI_OK;
 }
 
 static const char* kProfNames[P_NCLS] = {

@@ -147,6 +147,10 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& b, const double* rhs, double* x, c
 // tile launch geometry
 void tile_grid(const fsi_mesh* m, dim3* grid);
 
+// Raises a kernel's cudaFuncAttributeMaxDynamicSharedMemorySize to at least `bytes` on
+// the current device, once per (kernel, device, size); safe from several host threads.
+int ensure_smem_attr(const void* func, size_t bytes);
+
 // profiler: bracket every launch with prof_begin / prof_end (api.cu)
 int prof_begin(fsi_mesh* m, int cls);
 int prof_end(fsi_mesh* m, int cls);

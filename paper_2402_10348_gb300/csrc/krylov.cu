@@ -377,35 +377,29 @@ __global__ void __launch_bounds__(UDB) upd_dot2_kernel(double* __restrict__ w, c
 }
 
 template <int KMAX, typename VT>
-static void launch_upd_dot(fsi_mesh* m, int G, double* w, const VT* V, int M1, int k, const double* h, int64_t n) {
+static int launch_upd_dot(fsi_mesh* m, int G, double* w, const VT* V, int M1, int k, const double* h, int64_t n) {
   const size_t smem = sizeof(VT) * (size_t)(KMAX + 1) * UDB;
-  static bool attr = false;
   if constexpr (sizeof(VT) == 4) {
-    if (!attr) {
-      cudaFuncSetAttribute(upd_dot2_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr = true;
-    }
+    if (int rc = ensure_smem_attr(reinterpret_cast<const void*>(&upd_dot2_kernel<KMAX>), smem)) return rc;
     upd_dot2_kernel<KMAX><<<G, UDB, smem, m->stream>>>(w, V, M1, k, h, n, m->partials_dot);
   } else {
-    if (!attr) {
-      cudaFuncSetAttribute(upd_dot_kernel<KMAX, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr = true;
-    }
+    if (int rc = ensure_smem_attr(reinterpret_cast<const void*>(&upd_dot_kernel<KMAX, VT>), smem)) return rc;
     upd_dot_kernel<KMAX, VT><<<G, UDB, smem, m->stream>>>(w, V, M1, k, h, n, m->partials_dot);
   }
+  return FSI_OK;
 }
 
 template <typename VT>
-static void upd_dot(fsi_mesh* m, int G, double* w, const VT* V, int M1, int k, const double* h, int64_t n) {
+static int upd_dot(fsi_mesh* m, int G, double* w, const VT* V, int M1, int k, const double* h, int64_t n) {
   switch ((k + 7) / 8) {
-    case 1: launch_upd_dot<8>(m, G, w, V, M1, k, h, n); break;
-    case 2: launch_upd_dot<16>(m, G, w, V, M1, k, h, n); break;
-    case 3: launch_upd_dot<24>(m, G, w, V, M1, k, h, n); break;
-    case 4: launch_upd_dot<32>(m, G, w, V, M1, k, h, n); break;
-    case 5: launch_upd_dot<40>(m, G, w, V, M1, k, h, n); break;
-    case 6: launch_upd_dot<48>(m, G, w, V, M1, k, h, n); break;
-    case 7: launch_upd_dot<56>(m, G, w, V, M1, k, h, n); break;
-    default: launch_upd_dot<64>(m, G, w, V, M1, k, h, n); break;
+    case 1: return launch_upd_dot<8>(m, G, w, V, M1, k, h, n);
+    case 2: return launch_upd_dot<16>(m, G, w, V, M1, k, h, n);
+    case 3: return launch_upd_dot<24>(m, G, w, V, M1, k, h, n);
+    case 4: return launch_upd_dot<32>(m, G, w, V, M1, k, h, n);
+    case 5: return launch_upd_dot<40>(m, G, w, V, M1, k, h, n);
+    case 6: return launch_upd_dot<48>(m, G, w, V, M1, k, h, n);
+    case 7: return launch_upd_dot<56>(m, G, w, V, M1, k, h, n);
+    default: return launch_upd_dot<64>(m, G, w, V, M1, k, h, n);
   }
 }
 
@@ -805,7 +799,8 @@ static int gmres_core_t(fsi_mesh* m, const BlockInfo& blk, const double* b, doub
       // pass-1 update fused with the pass-2 projections of the updated vector
       {
         const int Gc = cgrid((n + CH - 1) / CH);
-        FSI_LAUNCH(m, P_KRY_UPD, upd_dot<VT>(m, Gc, w, V, M1, j + 1, K->h, n));
+        FSI_LAUNCH(m, P_KRY_UPD, rc = upd_dot<VT>(m, Gc, w, V, M1, j + 1, K->h, n));
+        if (rc) return rc;
         FSI_LAUNCH(m, P_KRY_UPD, sum_partials_decide<<<j + 2, VB, 0, m->stream>>>(m->partials_dot, Gc, K, j));
         prof_bytes(m, P_KRY_DOT, (j + 1) * vb + wb);      // j+1 basis vectors and w read once
         prof_bytes(m, P_KRY_UPD, (j + 1) * vb + 2 * wb);  // j+1 basis vectors and w read, w written

@@ -69,11 +69,7 @@ int record_op(BatchRec* r, const Op& op, int cls) {
 
 template <class Op>
 int launch_batched(fsi_batch* b, const void* ops_dev, size_t smem, int cls, int use_active) {
-  static size_t configured = 0;
-  if (configured < smem) {
-    FSI_CUDA(cudaFuncSetAttribute(tile_batch_kernel<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured = smem;
-  }
+  if (int rc = ensure_smem_attr(reinterpret_cast<const void*>(&tile_batch_kernel<Op>), smem)) return rc;
   return batch_launch_tiles_impl(b, ops_dev, smem, cls, use_active,
                                  reinterpret_cast<const void*>(&tile_batch_kernel<Op>));
 }
@@ -82,11 +78,7 @@ template <class Op>
 int run_tile(fsi_mesh* m, const Op& op, int cls) {
   if (m->rec) return record_op(m->rec, op, cls);
   const size_t smem = tile_smem_bytes<Op>(op.nf);
-  static size_t configured = 0;
-  if (smem > configured) {
-    FSI_CUDA(cudaFuncSetAttribute(tile_kernel<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured = smem;
-  }
+  if (int rc = ensure_smem_attr(reinterpret_cast<const void*>(&tile_kernel<Op>), smem)) return rc;
   dim3 grid;
   tile_grid(m, &grid);
   FSI_LAUNCH(m, cls, tile_kernel<Op><<<grid, NTHREADS, smem, m->stream>>>(op, m->g));

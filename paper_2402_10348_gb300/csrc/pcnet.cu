@@ -838,11 +838,7 @@ int launch_conv(fsi_pc* pc, const TView& in, const TView& out, const TView& mask
                 const uint16_t* wpk, int relu) {
   using C = ConvCfg<CIN, N>;
   fsi_mesh* m = pc->m;
-  static bool attr = false;
-  if (!attr) {
-    FSI_CUDA(cudaFuncSetAttribute(conv_mma_kernel<CIN, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    attr = true;
-  }
+  if (int rc = ensure_smem_attr(reinterpret_cast<const void*>(&conv_mma_kernel<CIN, N>), C::SMEM)) return rc;
   const int gx = (out.nx + TILE_X - 1) / TILE_X, gy = (out.ny + TILE_Y - 1) / TILE_Y;
   const int cols = gx * gy;
   // CTAs resident per SM (shared memory bound) x 152 SMs: enough z-chunks to fill them
@@ -870,11 +866,7 @@ template <int CIN>
 int launch_wgrad_mma(fsi_pc* pc, const TView& x, const TView& g, int* nblk_out) {
   using C = WgmCfg<CIN>;
   fsi_mesh* m = pc->m;
-  static bool attr = false;
-  if (!attr) {
-    FSI_CUDA(cudaFuncSetAttribute(wgrad_mma_kernel<CIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    attr = true;
-  }
+  if (int rc = ensure_smem_attr(reinterpret_cast<const void*>(&wgrad_mma_kernel<CIN>), C::SMEM)) return rc;
   const int64_t V = (int64_t)g.nx * g.ny * g.nz;
   const int64_t nst = (V + WGM_KS - 1) / WGM_KS;
   const int per_sm = std::max(1, std::min(std::min(8, 512 / C::NCOLS), (227 * 1024) / (C::SMEM + 1024)));
