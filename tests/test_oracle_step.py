@@ -59,3 +59,63 @@ def test_cavity_step_converges():
     assert np.allclose(st.xdn, (st.xn - xprev) / d.dt, rtol=1e-12, atol=1e-12)
     i, j, k = pb.mesh.ijk()
     assert np.all(st.xn[0, k == d.nz] == 1.0)
+
+
+def _mirror_x(pb, x):
+    """The state seen in the mirror x -> Lx - x: nodal fields re-indexed, v_x and the
+    B components with one x index (B12, B13) change sign."""
+    d = pb.desc
+    y = x.reshape(x.shape[0], d.nz + 1, d.ny + 1, d.nx + 1)[:, :, :, ::-1].reshape(x.shape).copy()
+    y[0] *= -1.0
+    for s in range(pb.ns):
+        y[pb.b_comp(s, 3)] *= -1.0  # B12
+        y[pb.b_comp(s, 5)] *= -1.0  # B13
+    return y
+
+
+def _swap_xy(pb, x):
+    """The state with the x and y axes exchanged: nodal fields transposed, v_x <-> v_y,
+    B11 <-> B22 and B23 <-> B13 (order [11, 22, 33, 12, 23, 13])."""
+    d = pb.desc
+    y = x.reshape(x.shape[0], d.nz + 1, d.ny + 1, d.nx + 1).transpose(0, 1, 3, 2).reshape(x.shape).copy()
+    y[[0, 1]] = y[[1, 0]]
+    for s in range(pb.ns):
+        a, b = pb.b_comp(s, 0), pb.b_comp(s, 1)
+        y[[a, b]] = y[[b, a]]
+        a, b = pb.b_comp(s, 4), pb.b_comp(s, 5)
+        y[[a, b]] = y[[b, a]]
+    return y
+
+
+def test_falling_sphere_steps_keep_the_box_symmetries():
+    """A heavier elastic sphere on the vertical axis of a closed no-slip box under
+    gravity: the problem is unchanged by the mirrors x -> 1 - x, y -> 1 - y and by the
+    exchange of x and y, so two time steps (Section 2.5) must return states with the
+    same symmetries (up to the linear tolerance).  A dropped or mis-indexed term in one
+    direction, a wrong sign of an off-diagonal B component or B components stored in
+    the wrong order breaks one of them; the at-rest start makes every term of the
+    momentum, Allen-Cahn and B equations take part by the second step."""
+    from workloads import BC_DIRICHLET, FaceBC, MeshDesc, Phase
+    phases = [Phase(rho=1.0, mu=0.02), Phase(rho=2.0, mu=0.02, mu_L=0.5, solid=True)]
+    faces = [FaceBC(BC_DIRICHLET, (0.0, 0.0, 0.0), 0) for _ in range(6)]
+    d = MeshDesc(4, 4, 4, 1.0, 1.0, 1.0, phases, (0.0, 0.0, -9.81), eps=0.375, eta=0.2, dt=0.02,
+                 rho_inf=0.0, c_i=36.0, faces=faces, pin_node=0)
+    pb = Problem(d)
+    X = node_coords(d)
+    x = np.zeros((d.ncomp, d.nn))
+    r = np.sqrt((X[0] - 0.5) ** 2 + (X[1] - 0.5) ** 2 + (X[2] - 0.55) ** 2)
+    x[5] = np.tanh((0.3 - r) / (np.sqrt(2) * d.eps))
+    x[4] = -x[5]
+    x[pb.b_comp(0, 0): pb.b_comp(0, 3)] = 1.0
+    st = State(x.copy(), x.copy(), np.zeros_like(x))
+    opt = step.StepOptions(k_max=3, fixed_nl_iters=True, rtol=1e-12, max_iter=4000)
+    for _ in range(2):
+        step.time_step(pb, st, opt)
+    xs = st.xn
+    assert np.abs(xs[2]).max() > 1e-4                         # the sphere moves
+    assert np.abs(xs[pb.b_comp(0, 4)]).max() > 1e-8          # B23 is no longer zero
+    scale = np.abs(xs).max(axis=1, keepdims=True) + 1e-300
+    mirror_y = _swap_xy(pb, _mirror_x(pb, _swap_xy(pb, xs)))
+    for name, img in (("mirror x", _mirror_x(pb, xs)), ("mirror y", mirror_y), ("swap x y", _swap_xy(pb, xs))):
+        err = (np.abs(img - xs) / scale).max()
+        assert err < 1e-8, (name, err)
