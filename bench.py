@@ -47,13 +47,15 @@ def parse():
     p.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner arm")
     p.add_argument("--train-steps", type=int, default=3000)
     p.add_argument("--restart", type=int, default=30, help="GMRES restart length m (<= 64)")
-    p.add_argument("--case", default="step", choices=["step", "solve", "pcnet", "batch", "mixed"],
+    p.add_argument("--case", default="step", choices=["step", "solve", "pcnet", "batch", "mixed", "operators"],
                    help="solve: only a fixed 40-iteration float32-IR NS GMRES solve at 64^3 (a short, "
                         "repeatable launch sequence for ncu captures); pcnet: learned-preconditioner "
                         "applies and training steps at 64^3 with per-kernel timing (JSON on stdout); "
                         "batch: 64 uneven cavity instances, batched launches against per-instance "
                         "launches (JSON on stdout); mixed: 10 steps of the 64^3 cavity in float64 and "
-                        "with float32 operators in float64 refinement, per-field drift (JSON on stdout)")
+                        "with float32 operators in float64 refinement, per-field drift (JSON on stdout); "
+                        "operators: per-apply GDoF/s of every residual and JVP (float64 and float32) "
+                        "on the 64^3 cavity, the falling sphere and ship/ice meshes (JSON on stdout)")
     return p.parse_args()
 
 
@@ -249,6 +251,76 @@ def run_batch_case(count: int = 64, reps: int = 5):
                           "launches_per_instance_arm": count, "launches_batched": 2},
            "ns_solve_fp32ir_rtol1e-8": res, "max_solution_difference": diff}
     print(json.dumps(out), flush=True)
+
+
+def run_operators_case(reps: int = 3):
+    """Per-apply GDoF/s of every element operator (residual, float64 JVP, float32 JVP of
+    each block) at the three single-mesh sizes: the 64^3 cavity, the falling sphere
+    (96x96x192, 3 phases, 2 solids) and ship/ice (256x128x64, 11 phases, 9 solids).  The
+    states are drawn on the device (phase fractions a partition of unity, B near I);
+    per-apply times come from the library's CUDA-event profiler (staging excluded)."""
+    import collections
+    import torch
+    from paper_2402_10348_gb300 import fsi
+    from workloads import cavity64, falling, shipice
+    dev = torch.device("cuda", 0)
+    out = {}
+    for wl in (cavity64(), falling(), shipice()):
+        d = wl.desc
+        nn, N, ns = d.nn, d.n_phase, d.n_solid
+        g = torch.Generator(device=dev).manual_seed(0)
+
+        def rnd(*shape):
+            return torch.rand(*shape, dtype=torch.float64, device=dev, generator=g)
+
+        x = torch.empty(d.ncomp, nn, dtype=torch.float64, device=dev)
+        x[0:3] = 0.2 * (rnd(3, nn) - 0.5)
+        x[3] = rnd(nn)
+        a = rnd(N, nn) + 0.05
+        x[4:4 + N] = 2.0 * a / a.sum(0) - 1.0
+        for s in range(ns):
+            b0 = 4 + N + 6 * s
+            x[b0:b0 + 3] = 1.0 + 0.05 * (rnd(3, nn) - 0.5)
+            x[b0 + 3:b0 + 6] = 0.05 * (rnd(3, nn) - 0.5)
+        x = x.reshape(-1).contiguous()
+        xn = (x + 0.01 * (rnd(x.numel()) - 0.5)).contiguous()
+        xdn = (0.1 * (rnd(x.numel()) - 0.5)).contiguous()
+        del a
+        mesh = fsi.fsi_create_mesh(d)
+        fsi.fsi_set_stream(mesh)
+        for i in range(N):
+            fsi.fsi_set_ac_coeffs(mesh, i, 0.5, 0.1)
+        blocks = [("ns", fsi.FSI_BLOCK_NS, 4 * nn)] + [("ac", fsi.FSI_BLOCK_AC(i), nn) for i in range(N)] + \
+                 [("b", fsi.FSI_BLOCK_B(s), 6 * nn) for s in range(ns)]
+        applies, dofs = collections.Counter(), {}
+        for profiled in (False, True):  # one untimed pass, then the profiled ones
+            if profiled:
+                fsi.fsi_profile(mesh, True)
+            for kind, blk, n in blocks:
+                r = torch.empty(n, dtype=torch.float64, device=dev)
+                y = torch.empty(n, dtype=torch.float64, device=dev)
+                dx = (rnd(n) - 0.5).contiguous()
+                for _ in range(reps if profiled else 1):
+                    fsi.fsi_residual(mesh, blk, x, xn, xdn, r)
+                    fsi.fsi_jvp(mesh, blk, x, xn, xdn, dx, y)
+                    fsi.fsi_jvp(mesh, blk, x, xn, xdn, dx, y, fsi.FSI_ELASTIC_AUG | fsi.FSI_FP32)
+                if profiled:
+                    for cls in (f"{kind}_residual", f"{kind}_jvp_f64", f"{kind}_jvp_f32"):
+                        applies[cls] += reps
+                        dofs[cls] = n
+        prof = fsi.fsi_profile_read(mesh)
+        fsi.fsi_profile(mesh, False)
+        torch.cuda.synchronize()
+        ops = {}
+        for cls, k in applies.items():
+            launches, ms = prof[cls][0], prof[cls][1]
+            if ms > 0:
+                ops[cls] = {"gdofs": round(dofs[cls] * k / (ms / 1e3) / 1e9, 3),
+                            "us_per_apply": round(ms / k * 1e3, 2), "launches_per_apply": launches / k}
+        out[wl.name] = {"nodes": nn, "phases": N, "solids": ns, "dof_per_node": d.ncomp, "ops": ops}
+        del mesh, x, xn, xdn
+        torch.cuda.empty_cache()
+    print(json.dumps({"case": "operators", "reps": reps, "unit": "GDoF/s per apply", "configs": out}), flush=True)
 
 
 def run_mixed_case(steps: int = 10):
@@ -787,6 +859,8 @@ def main():
         run_batch_case()
     elif args.case == "mixed":
         run_mixed_case()
+    elif args.case == "operators":
+        run_operators_case()
     elif args.case == "solve":
         run_solve_case()
     else:
