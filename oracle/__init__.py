@@ -26,6 +26,7 @@ the steps in the order the paper states them:
   step.py      partitioned block Newton time step (Section 2.5).
   gridcell.py  grid-cell distance and ray-casting sign with non-duplicated plane
                partitioning (Section 3, Algorithms 1 and 2).
+  diagnostics.py  solid centre of mass (Section 5.2) and point tracking (Appendix C).
 
 Parity pins for every function live in tests/test_oracle_*.py.  Where a function is
 not pinned to something outside itself, its docstring says "parity unpinned".
