@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner arm")
     p.add_argument("--train-steps", type=int, default=3000)
     p.add_argument("--restart", type=int, default=30, help="GMRES restart length m (<= 64)")
+    p.add_argument("--ir-inner-rtol", type=float, default=1e-3,
+                   help="relative tolerance of each inner float32 solve of the refinement")
     p.add_argument("--case", default="step", choices=["step", "solve", "pcnet", "batch", "mixed", "operators"],
                    help="solve: only a fixed 40-iteration float32-IR NS GMRES solve at 64^3 (a short, "
                         "repeatable launch sequence for ncu captures); pcnet: learned-preconditioner "
@@ -577,7 +579,8 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     fsi.fsi_set_stream(mesh, stream)
     prec = fsi.FSI_PREC_FP32_IR if args.precision == "fp32ir" else fsi.FSI_PREC_FP64
-    solve = fsi.solve_opts(m=args.restart, rtol=1e-8, max_iter=3000, precision=prec, ir_inner_rtol=1e-3, ir_max=30)
+    solve = fsi.solve_opts(m=args.restart, rtol=1e-8, max_iter=3000, precision=prec, ir_inner_rtol=args.ir_inner_rtol,
+                           ir_max=30)
 
     x, xn, xdn = initial_state(fsi, mesh, wl, torch, dev)
 
@@ -592,7 +595,8 @@ def run_gpu(args):
         pc = fsi.fsi_pc_create(mesh, n_pairs_cap=512, linear=True, modulate=True)
         fsi.fsi_pc_set_weights(pc, he_normal_weights(pc.fan, 3))
         fsi.fsi_set_pc(mesh, pc)
-        harvest = fsi.solve_opts(m=args.restart, rtol=1e-8, max_iter=3000, precision=prec, ir_inner_rtol=1e-3,
+        harvest = fsi.solve_opts(m=args.restart, rtol=1e-8, max_iter=3000, precision=prec,
+                                 ir_inner_rtol=args.ir_inner_rtol,
                                  ir_max=30)
         harvest.flags |= fsi.FSI_HARVEST
     for _ in range(args.warmup):
@@ -678,7 +682,8 @@ def run_gpu(args):
                       if prec == fsi.FSI_PREC_FP32_IR else "float64 throughout"),
         "data": "synthetic (seeded icosphere surface, initial phases by the grid-cell method)",
         "config": {"workload": WORKLOAD, "nodes": d.nn, "dof_per_node": d.ncomp, "dt": d.dt,
-                   "nl_iters_max": wl.k_max, "gmres": f"Jacobi GMRES({args.restart}) rtol 1e-8, stop on stagnation",
+                   "nl_iters_max": wl.k_max, "gmres": f"Jacobi GMRES({args.restart}) rtol 1e-8, stop on stagnation"
+                   + (f"; inner solves to {args.ir_inner_rtol:g}" if prec == fsi.FSI_PREC_FP32_IR else ""),
                    "l2": ("inputs larger than L2: a time step streams the 64^3 state, the float64 "
                           "refinement vectors and the (m+1) x 1.1M Krylov basis of the NS block "
                           f"({(args.restart + 1) * 4 * d.nn * (4 if prec == fsi.FSI_PREC_FP32_IR else 8) / 1e6:.0f}"
