@@ -260,6 +260,22 @@ int fsi_init_phases(fsi_mesh* mesh, const fsi_surface* surfaces, int32_t n_surf,
                     const fsi_phase_rule* rules, int32_t gx, int32_t gy, int32_t gz,
                     double* phi_out, int32_t* tags_out);
 
+/* --------------------------------------------------------------- diagnostics
+ * Centre of mass of solid `solid` (Section 5.2): x_c = int x alpha^s / int alpha^s,
+ * alpha^s = (1 + phi^s)/2, integrated exactly element by element (the operators'
+ * 2x2x2 Gauss rule is exact for these integrands).  x: device state [ncomp][nn] (only
+ * the solid's phase plane is read).  out: host double[3].  Deterministic (fixed-order
+ * sums).  Synchronises the stream.  FSI_EINVAL for a bad solid index or an indicator
+ * with no positive mass. */
+int fsi_center_of_mass(fsi_mesh* mesh, const double* x, int32_t solid, double* out);
+
+/* Point tracking (Appendix C): moves n points, device double [n][3] (x, y, z per point)
+ * in place, by one forward-Euler step p <- p + dt v(p), v the trilinear interpolant of
+ * the velocity planes of the device state x (pass x^{n+1}) in the element that holds
+ * the point; a point outside the box is located at its position clamped onto the box.
+ * n = 0 is a no-op; n < 0 is FSI_EINVAL.  Asynchronous. */
+int fsi_track_points(fsi_mesh* mesh, const double* x, int64_t n, double* points);
+
 /* --------------------------------------------------------------- allocation-free variant
  * (no counterpart in the paper.)  gamma and beta of one phase, as fsi_update_ac_coeffs
  * computes them, for callers that cannot call cudaMalloc: code that must not

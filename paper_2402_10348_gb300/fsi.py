@@ -111,7 +111,8 @@ EXPORTS = ["fsi_create_mesh", "fsi_destroy_mesh", "fsi_set_stream", "fsi_mesh_in
            "fsi_pc_get_weights", "fsi_pc_set_norm", "fsi_pc_get_norm", "fsi_pc_forward", "fsi_pc_grad",
            "fsi_pc_apply", "fsi_pc_add_pair", "fsi_pc_pairs", "fsi_pc_fit_norm", "fsi_pc_train", "fsi_set_pc",
            "fsi_batch_create", "fsi_batch_destroy", "fsi_batch_layout", "fsi_batch_jvp", "fsi_batch_gmres",
-           "fsi_batch_autotune", "fsi_batch_set_graph", "fsi_last_error"]
+           "fsi_batch_autotune", "fsi_batch_set_graph", "fsi_center_of_mass", "fsi_track_points",
+           "fsi_last_error"]
 
 _lib = None
 
@@ -286,6 +287,21 @@ def fsi_init_phases(mesh: Mesh, surfaces, rules, grid, phi_out, tags_out=None):
         tp = _ptr(tags_out)
     _check(lib().fsi_init_phases(mesh.handle, S, C.c_int32(len(surfaces)), R, C.c_int32(grid[0]),
                                  C.c_int32(grid[1]), C.c_int32(grid[2]), _dptr(phi_out), tp))
+
+
+def fsi_center_of_mass(mesh: Mesh, x, solid: int):
+    """(x, y, z) centre of mass of solid `solid` from the device state x; synchronises."""
+    out = (C.c_double * 3)()
+    _check(lib().fsi_center_of_mass(mesh.handle, _dptr(x), C.c_int32(solid), out))
+    return out[0], out[1], out[2]
+
+
+def fsi_track_points(mesh: Mesh, x, points):
+    """Moves the device float64 points [n, 3] in place by one step with the velocity of x."""
+    if points.dim() != 2 or points.shape[1] != 3:
+        raise ValueError("points: a [n, 3] tensor")
+    n = points.shape[0]
+    _check(lib().fsi_track_points(mesh.handle, _dptr(x), C.c_int64(n), _dptr(points) if n else None))
 
 
 def fsi_gamma_beta_noalloc(nx, ny, nz, lx, ly, lz, eta, v, phi, gamma_beta, stream=None):

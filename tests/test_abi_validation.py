@@ -55,6 +55,9 @@ def test_null_handles_and_pointers_are_rejected():
     assert L.fsi_jvp(None, C.c_int32(0), C.byref(st), None, None, C.c_uint32(0)) == fsi.FSI_EINVAL
     assert L.fsi_residual(None, C.c_int32(0), C.byref(st), None) == fsi.FSI_EINVAL
     assert L.fsi_diag(None, C.c_int32(0), C.byref(st), None, C.c_uint32(0)) == fsi.FSI_EINVAL
+    out = (C.c_double * 3)()
+    assert L.fsi_center_of_mass(None, None, C.c_int32(0), out) == fsi.FSI_EINVAL
+    assert L.fsi_track_points(None, None, C.c_int64(-1), None) == fsi.FSI_EINVAL
 
 
 def test_last_error_is_per_thread():
