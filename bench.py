@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--restart", type=int, default=30, help="GMRES restart length m (<= 64)")
     p.add_argument("--ir-inner-rtol", type=float, default=1e-3,
                    help="relative tolerance of each inner float32 solve of the refinement")
-    p.add_argument("--case", default="step", choices=["step", "solve", "pcnet", "batch", "mixed", "operators"],
+    p.add_argument("--case", default="step", choices=["step", "solve", "pcnet", "batch", "mixed", "operators", "diagnostics"],
                    help="solve: only a fixed 40-iteration float32-IR NS GMRES solve at 64^3 (a short, "
                         "repeatable launch sequence for ncu captures); pcnet: learned-preconditioner "
                         "applies and training steps at 64^3 with per-kernel timing (JSON on stdout); "
@@ -57,7 +57,8 @@ def parse():
                         "launches (JSON on stdout); mixed: 10 steps of the 64^3 cavity in float64 and "
                         "with float32 operators in float64 refinement, per-field drift (JSON on stdout); "
                         "operators: per-apply GDoF/s of every residual and JVP (float64 and float32) "
-                        "on the 64^3 cavity, the falling sphere and ship/ice meshes (JSON on stdout)")
+                        "on the 64^3 cavity, the falling sphere and ship/ice meshes (JSON on stdout); "
+                        "diagnostics: centre of mass and tracking of 10^6 points at 64^3 (JSON on stdout)")
     return p.parse_args()
 
 
@@ -323,6 +324,50 @@ def run_operators_case(reps: int = 3):
         del mesh, x, xn, xdn
         torch.cuda.empty_cache()
     print(json.dumps({"case": "operators", "reps": reps, "unit": "GDoF/s per apply", "configs": out}), flush=True)
+
+
+def run_diagnostics_case(reps: int = 20):
+    """Centre of mass of the solid (Section 5.2) and tracking of 10^6 points (Appendix C)
+    on the 64^3 cavity's initial state, CUDA-event times averaged over `reps` calls.
+    Algorithmic bytes: the indicator plane (8 B per node) for the centre of mass; per
+    point 48 B (read and write of its coordinates) for the tracking, whose gathers of
+    8 corners x 3 velocity values hit the L2-resident velocity planes (6.6 MB)."""
+    import torch
+    from paper_2402_10348_gb300 import fsi
+    from workloads import cavity64
+    wl = cavity64()
+    d = wl.desc
+    dev = torch.device("cuda", 0)
+    mesh = fsi.fsi_create_mesh(d)
+    stream = torch.cuda.current_stream()
+    fsi.fsi_set_stream(mesh, stream)
+    x, _, _ = initial_state(fsi, mesh, wl, torch, dev)
+    x[0:3 * d.nn] = 0.1 * torch.rand(3 * d.nn, dtype=torch.float64, device=dev)
+    npts = 1_000_000
+    g = torch.Generator(device=dev).manual_seed(0)
+    pts = torch.rand(npts, 3, dtype=torch.float64, device=dev, generator=g)
+    com = fsi.fsi_center_of_mass(mesh, x, 0)
+    fsi.fsi_track_points(mesh, x, pts)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fsi.fsi_center_of_mass(mesh, x, 0)  # synchronises (host reads the result)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    com_us = e0.elapsed_time(e1) / reps * 1e3
+    e0.record(stream)
+    for _ in range(reps):
+        fsi.fsi_track_points(mesh, x, pts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    trk_us = e0.elapsed_time(e1) / reps * 1e3
+    trk_bytes = npts * 48
+    print(json.dumps({"case": "diagnostics", "workload": WORKLOAD, "center_of_mass": [round(c, 6) for c in com],
+                      "center_of_mass_us": round(com_us, 2), "center_of_mass_bytes": 8 * d.nn,
+                      "points": npts, "track_us": round(trk_us, 2),
+                      "track_gbs": round(trk_bytes / (trk_us * 1e-6) / 1e9, 1),
+                      "note": "center_of_mass includes its device-to-host copy and synchronisation"}), flush=True)
 
 
 def run_mixed_case(steps: int = 10):
@@ -866,6 +911,8 @@ def main():
         run_mixed_case()
     elif args.case == "operators":
         run_operators_case()
+    elif args.case == "diagnostics":
+        run_diagnostics_case()
     elif args.case == "solve":
         run_solve_case()
     else:
