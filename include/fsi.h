@@ -191,7 +191,7 @@ typedef struct {
 } fsi_solve_info;
 
 /* Solves J(st) x = rhs for one block by right-preconditioned restarted GMRES from
- * x = 0 (Arnoldi with classical Gram-Schmidt applied twice, Givens rotations; the
+ * x = 0 (Arnoldi with classical Gram-Schmidt and the DGKS second pass, Givens rotations; the
  * paper solves every block with GMRES, Section 2.5).  rhs and x are device block
  * vectors.  Returns FSI_ENOCONV (x holds the last iterate) if rtol is not met within
  * max_iter.  Synchronises the stream. */
