@@ -127,6 +127,10 @@ constexpr unsigned OP_DX32_READY = 0x80000000u;
 int ensure_dx32(fsi_mesh* m);  // allocates m->dx32 (6 x nn floats) on first use
 int op_diag(fsi_mesh* m, const BlockInfo& b, double* d, unsigned flags);
 int op_coeffs(fsi_mesh* m, int phase, double* gamma_beta);  // synchronises
+// Final fixed-order sum of the gamma/beta per-CTA partials {sum val^2, n_band, int F',
+// int sqrt F} into out[0] = gamma, out[1] = beta (ops_f64.cu; one CTA of NTHREADS).
+// Shared by fsi_update_ac_coeffs and fsi_gamma_beta_noalloc.
+__global__ void coef_finalize(const double* partials, int64_t n, double eta, double* out);
 
 template <typename T>
 int launch_ns(fsi_mesh* m, int mode, const double* dx, double* y, unsigned flags);

@@ -306,7 +306,24 @@ def fsi_track_points(mesh: Mesh, x, points):
 
 def fsi_gamma_beta_noalloc(nx, ny, nz, lx, ly, lz, eta, v, phi, gamma_beta, stream=None):
     """gamma, beta of one phase written to the device tensor gamma_beta[2]; no allocation.
-    v: device float64 [3*nn] (v^{n+alpha}), phi: device float64 [nn] (phi^{n+alpha})."""
+    v: device float64 [3*nn] (v^{n+alpha}), phi: device float64 [nn] (phi^{n+alpha}),
+    nn = (nx+1)(ny+1)(nz+1).  The C call takes no mesh handle, so the sizes and the
+    device are checked here: undersized tensors or tensors on a GPU other than the
+    current one raise ValueError before anything is launched."""
+    for name, t in (("v", v), ("phi", phi), ("gamma_beta", gamma_beta)):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name}: expected a torch tensor")
+    if min(nx, ny, nz) >= 1:
+        nn = (nx + 1) * (ny + 1) * (nz + 1)
+        for name, t, need in (("v", v, 3 * nn), ("phi", phi, nn), ("gamma_beta", gamma_beta, 2)):
+            if t.numel() < need:
+                raise ValueError(f"fsi_gamma_beta_noalloc: {name} has {t.numel()} elements, needs {need}")
+    for name, t in (("v", v), ("phi", phi), ("gamma_beta", gamma_beta)):
+        if not t.is_cuda:
+            raise ValueError(f"fsi_gamma_beta_noalloc: {name} is not a CUDA tensor")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"fsi_gamma_beta_noalloc: {name} is on cuda:{t.device.index}, "
+                             f"the current device is cuda:{torch.cuda.current_device()}")
     st = torch.cuda.current_stream() if stream is None else stream
     _check(lib().fsi_gamma_beta_noalloc(C.c_int32(nx), C.c_int32(ny), C.c_int32(nz), C.c_double(lx),
                                         C.c_double(ly), C.c_double(lz), C.c_double(eta), _dptr(v), _dptr(phi),

@@ -87,3 +87,23 @@ def test_binding_refuses_host_and_mistyped_tensors():
         fsi._dptr(torch.zeros(4, dtype=torch.float32))
     with pytest.raises(TypeError):
         fsi._ptr([0.0, 1.0])
+
+
+@pytest.mark.parametrize("which, sizes", [
+    ("v", (3 * 5 * 5 * 5 - 1, 5 * 5 * 5, 2)),
+    ("phi", (3 * 5 * 5 * 5, 5 * 5 * 5 - 1, 2)),
+    ("gamma_beta", (3 * 5 * 5 * 5, 5 * 5 * 5, 1)),
+])
+def test_noalloc_binding_rejects_undersized_tensors(which, sizes):
+    """fsi_gamma_beta_noalloc takes no mesh handle, so the binding checks the tensor
+    sizes against the mesh sizes before anything reaches the library."""
+    v, phi, gb = (torch.zeros(n, dtype=torch.float64) for n in sizes)
+    with pytest.raises(ValueError, match=f"{which} has"):
+        fsi.fsi_gamma_beta_noalloc(4, 4, 4, 1.0, 1.0, 1.0, 0.2, v, phi, gb)
+
+
+def test_noalloc_binding_rejects_host_tensors():
+    nn = 5 * 5 * 5
+    v, phi, gb = (torch.zeros(n, dtype=torch.float64) for n in (3 * nn, nn, 2))
+    with pytest.raises(ValueError, match="not a CUDA tensor"):
+        fsi.fsi_gamma_beta_noalloc(4, 4, 4, 1.0, 1.0, 1.0, 0.2, v, phi, gb)

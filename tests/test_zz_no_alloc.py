@@ -53,11 +53,31 @@ def test_noalloc_matches_update_ac_coeffs_twice(n):
             out.fill_(float("nan"))
 
 
+def _raw_call(nx, ny, nz, v, phi, out):
+    return fsi.lib().fsi_gamma_beta_noalloc(
+        ctypes.c_int32(nx), ctypes.c_int32(ny), ctypes.c_int32(nz), ctypes.c_double(1.0), ctypes.c_double(1.0),
+        ctypes.c_double(1.0), ctypes.c_double(0.2), ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(phi.data_ptr()),
+        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
 def test_noalloc_rejects_meshes_beyond_the_scratch():
     buf = torch.zeros(8, dtype=torch.float64, device=DEV)
-    with pytest.raises(fsi.FsiError) as e:
-        # 4096 x 4096 x 4096 would need far more than 16384 partial sums; rejected
-        # from the sizes alone, before any kernel runs
-        fsi.fsi_gamma_beta_noalloc(4096, 4096, 4096, 1.0, 1.0, 1.0, 0.2, buf, buf, buf)
-    assert e.value.code == fsi.FSI_EINVAL
-    assert "static scratch" in str(e.value)
+    # 4096^3 and the int32 extreme would need far more than 16384 partial sums: the
+    # library rejects them from the sizes alone, before any kernel runs (the binding
+    # would already refuse the undersized tensors, so the C call is made directly)
+    for n in (4096, 2 ** 31 - 1):
+        rc = _raw_call(n, n, n, buf, buf, buf)
+        assert rc == fsi.FSI_EINVAL
+        assert "static scratch" in fsi.lib().fsi_last_error().decode()
+
+
+def test_noalloc_binding_rejects_tensors_on_another_device(monkeypatch):
+    """The kernel runs on the current device with that device's scratch, so tensors on
+    any other GPU are refused by the binding (simulated: the current device is
+    reported as another ordinal)."""
+    d = desc_small(n=(4, 4, 4))
+    x, _, _ = _state(d, 1)
+    out = torch.zeros(2, dtype=torch.float64, device=DEV)
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 1)
+    with pytest.raises(ValueError, match="current device is cuda:1"):
+        fsi.fsi_gamma_beta_noalloc(d.nx, d.ny, d.nz, d.lx, d.ly, d.lz, d.eta, x[:3 * d.nn], x[4 * d.nn:5 * d.nn], out)
