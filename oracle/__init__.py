@@ -23,6 +23,8 @@ the steps in the order the paper states them:
                Lagrange multiplier beta (Section 2.2.1).
   diag.py      Jacobi diagonal by probing (definition e_i^T J e_i).
   gmres.py     restarted right-preconditioned GMRES with modified Gram-Schmidt.
+  assemble.py  sparse block Jacobians by 27-colour probing and the exact (sparse LU)
+               linear solve.
   step.py      partitioned block Newton time step (Section 2.5).
   gridcell.py  grid-cell distance and ray-casting sign with non-duplicated plane
                partitioning (Section 3, Algorithms 1 and 2).
