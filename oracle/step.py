@@ -13,10 +13,16 @@ Section 2.1.2 (predictor-multicorrector) and Section 2.5:
      stop when ||d_blk|| / ||x_blk|| < nl_tol for every block;
   corrector:  xdot^{n+1} from the generalized-alpha relation, then
               x^n <- x^{n+1}, xdot^n <- xdot^{n+1}.
-Every block's linear system is solved by Jacobi-preconditioned GMRES(m) from 0.
+Every block's linear system is solved by Jacobi-preconditioned GMRES(m) from 0, or
+(option `direct`) exactly, by a sparse LU solve of the probed block Jacobian: the
+Newton step that every convergent linear solver approaches.  Option `pin_shift`: on an
+enclosed domain the NS step is computed from the system in which the pin node keeps
+its continuity equation (singular, consistent) followed by the shift p -= p[pin]; in
+exact arithmetic this is the pinned step.
 """
 from __future__ import annotations
 
+import copy
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -25,7 +31,9 @@ from . import blocks, mobility
 from .bc import dirichlet
 from .diag import block_diagonal
 from .fields import Problem, State
+from .assemble import assemble, direct_solve
 from .gmres import gmres
+from workloads import BC_DIRICHLET
 
 
 @dataclass
@@ -38,6 +46,9 @@ class StepOptions:
     fixed_nl_iters: bool = False       # run exactly k_max iterations (parity mode)
     fixed_gamma: list | None = None    # per-phase gamma instead of the mobility model
     elastic_aug: bool = True
+    direct: bool = False               # exact linear solves (sparse LU of the probed Jacobian)
+    pin_shift: bool = False            # enclosed domain: NS solve keeps the pin node's continuity
+                                       # equation, then p -= p[pin] (same Newton step)
 
 
 @dataclass
@@ -63,13 +74,48 @@ def corrector(pb: Problem, st: State) -> None:
     st.xdn[:] = xd1
 
 
+def enclosed(desc) -> bool:
+    """Every face has a Dirichlet velocity: constant pressure is a null mode of the NS
+    Jacobian (the pressure appears only through its gradient and through boundary
+    rows that are all velocity Dirichlet rows)."""
+    return all(f.kind == BC_DIRICHLET for f in desc.faces)
+
+
+def _unpinned(pb: Problem) -> Problem:
+    d = copy.copy(pb.desc)
+    d.pin_node = -1
+    return Problem(d)
+
+
 def solve_block(pb: Problem, st: State, block, opt: StepOptions, coeffs=None):
+    if block == "ns" and opt.pin_shift and pb.desc.pin_node >= 0 and enclosed(pb.desc):
+        if opt.direct:
+            raise ValueError("pin_shift solves a singular system: it needs the iterative solver")
+        # the pinned Newton step, reached through the singular but consistent system in
+        # which the pin node keeps its continuity equation (x_p + dx_p is then fixed
+        # only up to a constant, removed by the shift to p = 0 at the pin node)
+        x_before = st.x[0:4].copy()
+        _, it, rel = _solve(_unpinned(pb), st, block, opt, coeffs)
+        st.x[3] -= st.x[3, pb.desc.pin_node]
+        dx = float(np.linalg.norm(st.x[0:4] - x_before))
+        xnorm = float(np.linalg.norm(st.x[0:4]))
+        return dx / xnorm if xnorm > 0.0 else dx, it, rel
+    return _solve(pb, st, block, opt, coeffs)
+
+
+def _solve(pb: Problem, st: State, block, opt: StepOptions, coeffs=None):
     comps = blocks.components(pb, block)
     r = blocks.residual(pb, st, block, coeffs)
-    d = block_diagonal(pb, st, block, coeffs, opt.elastic_aug)
-    minv = 1.0 / d
-    dx, it, rel = gmres(lambda u: blocks.jvp(pb, st, block, u, coeffs, opt.elastic_aug),
-                        -r, minv, opt.m, opt.rtol, opt.max_iter)
+    if opt.direct:
+        A = assemble(pb, st, block, coeffs, opt.elastic_aug)
+        dx = direct_solve(A, -r)
+        it = 0
+        rel = float(np.linalg.norm(A @ dx + r)) / max(float(np.linalg.norm(r)), 1e-300)
+    else:
+        d = block_diagonal(pb, st, block, coeffs, opt.elastic_aug)
+        minv = 1.0 / d
+        dx, it, rel = gmres(lambda u: blocks.jvp(pb, st, block, u, coeffs, opt.elastic_aug),
+                            -r, minv, opt.m, opt.rtol, opt.max_iter)
     nn = pb.mesh.nn
     dx = dx.reshape(len(comps), nn)
     st.x[comps] += dx
