@@ -141,6 +141,18 @@ int fsi_update_ac_coeffs(fsi_mesh* mesh, int32_t phase, const fsi_state* st, dou
 int fsi_set_ac_coeffs(fsi_mesh* mesh, int32_t phase, double gamma, double beta);
 /* Fixes gamma^i for the time step (gamma >= 0), or restores the mobility model (< 0). */
 int fsi_fix_gamma(fsi_mesh* mesh, int32_t phase, double gamma);
+/* Pressure level of an enclosed domain (every face with a Dirichlet velocity; the
+ * pressure is then determined up to a constant, Section 2.1.2's momentum/continuity
+ * system has constant pressure in its null space).  active = 1 (default): the NS
+ * residual, product and diagonal replace the continuity row of pin_node by the row
+ * p = 0.  active = 0: that node keeps its continuity equation, and the system is
+ * singular but consistent for residuals of states that meet the velocity conditions;
+ * a solve of it plus the shift p -= p[pin_node] gives the pinned solution.  fsi_step
+ * solves the NS block this way on enclosed domains (far better conditioned: the pin
+ * row makes the near-constant pressure mode converge about 30x slower under Jacobi
+ * GMRES on the 16^3 cavity and stall it above 1e-8 from 24^3 up) unless the solve
+ * flag FSI_PINNED_SOLVE is given. */
+int fsi_set_pressure_pin(fsi_mesh* mesh, int32_t active);
 
 /* --------------------------------------------------------------- solvers */
 
@@ -159,6 +171,14 @@ int fsi_fix_gamma(fsi_mesh* mesh, int32_t phase, double gamma);
  * Arnoldi steps and the Jacobi direction D^{-1} v_j at odd ones, so that its
  * least-squares step weights the two kinds separately */
 #define FSI_PC_ALTERNATE 0x20u
+/* solve flag: never stop on stagnation.  Without it a solve stops ("stalled") when a
+ * whole restart cycle reduces the true residual by less than 1 % (FP32_IR: when a
+ * refinement reduces it by less than 10 %); with it the solve runs until rtol or
+ * max_iter (and, for FP32_IR, ir_max refinements) */
+#define FSI_NO_STALL_STOP 0x40u
+/* step flag (solve options of fsi_step): solve the NS block of an enclosed domain with
+ * the pressure pin row instead of the continuity equation plus the pressure shift */
+#define FSI_PINNED_SOLVE 0x80u
 
 #define FSI_PREC_FP64 0     /* operator applies in float64                         */
 #define FSI_PREC_FP32_IR 1  /* float32 operator inside float64 iterative refinement: the
@@ -410,7 +430,13 @@ int fsi_batch_set_graph(fsi_batch* batch, int32_t use_graph);
  * mesh launches (counters reset); fsi_profile(mesh, 0) stops.  Launch counts are
  * kept whether or not events are recorded.  fsi_profile_read synchronises the
  * stream and returns, per kernel class, the launches and the summed event time. */
-#define FSI_PROF_CLASSES 23
+/* Measured ceilings of the current GPU, for rooflines: float32 and float64 FMA rates
+ * (TFLOP/s, 8 independent FMA chains per thread on 8 x 256 threads per SM), read-only
+ * and copy (read + write) bandwidth over 2 GiB buffers (GB/s), each the best of five
+ * launches.  Allocates and frees 4 GiB of device memory; synchronises the device. */
+int fsi_probe_peaks(double* fp32_tflops, double* fp64_tflops, double* read_gbs, double* copy_gbs);
+
+#define FSI_PROF_CLASSES 24
 typedef struct {
   char name[24];
   int64_t launches;

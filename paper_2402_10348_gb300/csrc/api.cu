@@ -39,7 +39,7 @@ int ensure_smem_attr(const void* func, size_t bytes) {
 static const char* kProfNames[P_NCLS] = {
     "stage", "ns_residual", "ns_jvp_f64", "ns_jvp_f32", "ns_diag", "ac_residual", "ac_jvp_f64", "ac_jvp_f32",
     "ac_diag", "b_residual", "b_jvp_f64", "b_jvp_f32", "b_diag", "gamma_beta", "krylov_vector", "init",
-    "krylov_dot", "krylov_update", "krylov_scalar", "to_float", "pc_conv", "pc_wgrad", "pc_aux"};
+    "krylov_dot", "krylov_update", "krylov_scalar", "to_float", "pc_conv", "pc_wgrad", "pc_aux", "ns_coeffs"};
 constexpr int PROF_PAIRS = 4096;
 
 int prof_harvest(fsi_mesh* m) {
@@ -145,6 +145,7 @@ int stage(fsi_mesh* m, const fsi_state* st, bool fp32) {
                  fp32 ? m->xd32 : nullptr, fp32 ? m->mat32 : nullptr, m->ncomp, m->nn, m->P, alpha1 ? 0 : 1));
   m->staged_x = st->x;
   m->staged_xa = alpha1 ? st->x : m->xa;
+  ++m->stage_gen;
   return FSI_OK;
 }
 
@@ -193,8 +194,12 @@ int op_jvp(fsi_mesh* m, const BlockInfo& b, const double* dx, double* y, unsigne
       FSI_LAUNCH(m, P_KRY_CONV, to_float_kernel<<<vec_grid(b.n), 256, 0, m->stream>>>(dx, m->dx32, b.n));
   }
   flags &= ~OP_DX32_READY;
-  if (b.kind == 0)
-    return f32 ? launch_ns<float>(m, 1, dx, y, flags) : launch_ns<double>(m, 1, dx, y, flags);
+  if (b.kind == 0) {
+    // recorded (batched) launches take the per-element kernel; single launches the
+    // product from the quadrature-point coefficients
+    if (m->rec) return f32 ? launch_ns<float>(m, 1, dx, y, flags) : launch_ns<double>(m, 1, dx, y, flags);
+    return f32 ? launch_nsq<float>(m, dx, y, flags) : launch_nsq<double>(m, dx, y, flags);
+  }
   if (b.kind == 1)
     return f32 ? launch_ac<float>(m, 1, b.index, dx, y) : launch_ac<double>(m, 1, b.index, dx, y);
   return f32 ? launch_b<float>(m, 1, b.index, dx, y) : launch_b<double>(m, 1, b.index, dx, y);
@@ -316,6 +321,10 @@ int fsi_create_mesh(const fsi_mesh_desc* d, fsi_mesh** out) {
     if (d->phases[i].is_solid) P.solid_phase[s++] = i;
   }
   for (int i = 0; i < MAXP; ++i) m->fixed_gamma[i] = -1.0;
+  m->pin_node = d->pin_node >= 0 ? d->pin_node : -1;
+  m->enclosed = 1;
+  for (int f = 0; f < 6; ++f)
+    if (d->faces[f].kind != FSI_BC_DIRICHLET) m->enclosed = 0;
   std::vector<uint8_t> mask;
   std::vector<double> vD;
   build_bc(d, mask, vD);
@@ -361,6 +370,8 @@ int fsi_destroy_mesh(fsi_mesh* m) {
   cudaFree(m->kry_dev);
   cudaFree(m->dx32);
   cudaFree(m->Z);
+  cudaFree(m->cq64);
+  cudaFree(m->cq32);
   if (m->kry_est) cudaFreeHost(m->kry_est);
   for (cudaEvent_t e : m->kry_ev) cudaEventDestroy(e);
   for (cudaEvent_t e : m->prof.ev) cudaEventDestroy(e);
@@ -471,6 +482,13 @@ int fsi_set_ac_coeffs(fsi_mesh* m, int32_t phase, double gamma, double beta) {
 int fsi_fix_gamma(fsi_mesh* m, int32_t phase, double gamma) {
   if (!m || phase < 0 || phase >= m->N) return set_error(FSI_EINVAL, "fsi_fix_gamma: bad phase");
   m->fixed_gamma[phase] = gamma;
+  return FSI_OK;
+}
+
+int fsi_set_pressure_pin(fsi_mesh* m, int32_t active) {
+  if (!m) return set_error(FSI_EINVAL, "fsi_set_pressure_pin: null mesh");
+  if (active != 0 && active != 1) return set_error(FSI_EINVAL, "fsi_set_pressure_pin: active must be 0 or 1");
+  m->pin_active = active;
   return FSI_OK;
 }
 

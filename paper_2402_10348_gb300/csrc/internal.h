@@ -16,7 +16,7 @@ namespace fsi {
 enum ProfClass {
   P_STAGE, P_NS_RES, P_NS_JVP64, P_NS_JVP32, P_NS_DIAG, P_AC_RES, P_AC_JVP64, P_AC_JVP32,
   P_AC_DIAG, P_B_RES, P_B_JVP64, P_B_JVP32, P_B_DIAG, P_COEF, P_KRYLOV, P_INIT, P_KRY_DOT, P_KRY_UPD,
-  P_KRY_SMALL, P_KRY_CONV, P_PC_CONV, P_PC_WGRAD, P_PC_AUX, P_NCLS
+  P_KRY_SMALL, P_KRY_CONV, P_PC_CONV, P_PC_WGRAD, P_PC_AUX, P_NS_BUILD, P_NCLS
 };
 struct Profiler {
   bool on = false;
@@ -52,6 +52,9 @@ struct fsi_mesh {
   double lx = 0, ly = 0, lz = 0;
   // boundary data
   uint8_t* mask = nullptr;  // [nn]
+  int pin_node = -1;        // node of the pressure pin (mask bit 3), or -1
+  int pin_active = 1;       // 0: NS operators keep the pin node's continuity equation
+  int enclosed = 0;         // every face has a Dirichlet velocity: constant p is a null mode
   double* vD = nullptr;     // [3][nn]
   // staged state (x^{n+alpha}, dx/dt^{n+alpha_m}, blended materials)
   double* xa = nullptr;     // only when alpha != 1
@@ -62,6 +65,13 @@ struct fsi_mesh {
   float* mat32 = nullptr;
   float* dx32 = nullptr;     // float copy of a product's increment (FSI_FP32)
   const double* staged_x = nullptr;  // x^{n+1} of the last staging (p and Dirichlet rows)
+  int64_t stage_gen = 0;             // staging count: coefficients built at another count are stale
+  // quadrature-point coefficients of the NS product (NSBuildOp / NSQOp in ops.cuh)
+  double* cq64 = nullptr;
+  float* cq32 = nullptr;
+  int64_t cq_len = 0;                // allocated coefficients (each array)
+  int64_t cq_gen = -1;               // stage_gen of the last build
+  unsigned cq_flags = 0;             // FSI_ELASTIC_AUG of the last build
   const double* staged_xa = nullptr; // the x^{n+alpha} array in use
   // coefficients
   double gamma[fsi::MAXP] = {0};
@@ -134,6 +144,10 @@ __global__ void coef_finalize(const double* partials, int64_t n, double eta, dou
 
 template <typename T>
 int launch_ns(fsi_mesh* m, int mode, const double* dx, double* y, unsigned flags);
+// NS product from the quadrature-point coefficients (built first when stale)
+int ns_build(fsi_mesh* m, unsigned flags);  // ops_f64.cu
+template <typename T>
+int launch_nsq(fsi_mesh* m, const double* dx, double* y, unsigned flags);
 template <typename T>
 int launch_ac(fsi_mesh* m, int mode, int phase, const double* dx, double* y);
 template <typename T>

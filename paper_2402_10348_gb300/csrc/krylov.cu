@@ -718,7 +718,8 @@ static int gmres_core_t(fsi_mesh* m, const BlockInfo& blk, const double* b, doub
                         fsi_pc* pc, fsi_pc* harvest) {
   constexpr bool F32 = sizeof(VT) == 4;
   const bool alternate = (flags & FSI_PC_ALTERNATE) != 0;
-  flags &= ~FSI_PC_ALTERNATE;
+  const bool stall_stop = (flags & FSI_NO_STALL_STOP) == 0;
+  flags &= ~(FSI_PC_ALTERNATE | FSI_NO_STALL_STOP);
   const int64_t n = blk.n;
   const int M1 = m->kry_m + 1;
   const int G = vgrid(n);
@@ -752,7 +753,7 @@ static int gmres_core_t(fsi_mesh* m, const BlockInfo& blk, const double* b, doub
     if (!std::isfinite(beta2)) return set_error(FSI_ENAN, "GMRES: residual is not finite");
     rel = std::sqrt(beta2) / bnorm;
     if (rel <= rtol || *iters >= max_iter) break;
-    if (!first_cycle && rel > 0.99 * cycle_rel) {
+    if (stall_stop && !first_cycle && rel > 0.99 * cycle_rel) {
       *stalled = 1;
       break;
     }
@@ -881,8 +882,11 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& blk, const double* rhs, double* x,
   if (o.precond == FSI_PC_LEARNED && blk.kind == 0 && !pc)
     return set_error(FSI_EINVAL, "GMRES: FSI_PC_LEARNED without an attached preconditioner (fsi_set_pc)");
   fsi_pc* harvest = ((o.flags & FSI_HARVEST) && blk.kind == 0 && m->pc && m->pc->cap > 0) ? m->pc : nullptr;
-  const unsigned opflags = o.flags & ~(FSI_HARVEST | FSI_PC_ALTERNATE | OP_DX32_READY);
-  const unsigned alt = o.flags & FSI_PC_ALTERNATE;  // read by the flexible solves only
+  const unsigned opflags =
+      o.flags & ~(FSI_HARVEST | FSI_PC_ALTERNATE | FSI_NO_STALL_STOP | FSI_PINNED_SOLVE | OP_DX32_READY);
+  // read by the solver loop only: network/Jacobi alternation, and no stop on stagnation
+  const unsigned alt = o.flags & (FSI_PC_ALTERNATE | FSI_NO_STALL_STOP);
+  const bool stall_stop = (o.flags & FSI_NO_STALL_STOP) == 0;
   if (pc && (m->Z_n < n * mm || !m->Z)) {
     cudaFree(m->Z);
     m->Z = nullptr;
@@ -922,7 +926,8 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& blk, const double* rhs, double* x,
       // Jacobi GMRES solves from scratch
       inf.fallback = 1;
       pc = nullptr;
-      rc = gmres_core(m, blk, rhs, x, mm, o.rtol, o.max_iter - inf.iterations, opflags & ~FSI_FP32,
+      rc = gmres_core(m, blk, rhs, x, mm, o.rtol, o.max_iter - inf.iterations,
+                      (opflags & ~FSI_FP32) | (alt & FSI_NO_STALL_STOP),
                       &inf.iterations, &inf.restarts, &rel, &inf.stalled, nullptr, harvest);
     }
     if (rc) return rc;
@@ -934,7 +939,7 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& blk, const double* rhs, double* x,
       double rel2;
       int st2 = 0;
       rc = gmres_core(m, blk, r, d, mm, o.rtol / std::max(rel, 1e-300), o.max_iter - inf.iterations,
-                      opflags & ~FSI_FP32, &inf.iterations, &inf.restarts, &rel2, &st2, nullptr);
+                      (opflags & ~FSI_FP32) | (alt & FSI_NO_STALL_STOP), &inf.iterations, &inf.restarts, &rel2, &st2, nullptr);
       if (rc) return rc;
       if ((rc = vec_axpy(m, 1.0, d, x, n))) return rc;
       rel *= rel2;
@@ -994,9 +999,9 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& blk, const double* rhs, double* x,
         inf.fallback = 1;
         if (no_gain) continue;
       }
-      if (no_gain) {
+      if (no_gain && stall_stop) {
         // the inner solve reached its tolerance but the float64 residual did not
-        // follow: the attainable accuracy is reached
+        // follow: the refinement has stopped contracting
         inf.stalled = 1;
         break;
       }

@@ -78,6 +78,8 @@ struct OutDesc {
   const double* vD;     // Dirichlet velocity values [3][nn]
   int accumulate;       // add into y instead of writing (later solid passes)
   int dirichlet;        // apply Dirichlet rows
+  int pin;              // NS: the pressure pin row is active (mask bit 3); 0: the node keeps
+                        // its continuity equation (the pressure level is fixed by a shift)
 };
 
 // ----------------------------------------------------------------- NS block
@@ -312,7 +314,7 @@ struct NSOp {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       double* y = out.y + (int64_t)k * nn + nc.n;
-      const bool dir = (m >> k) & 1;
+      const bool dir = ((m >> k) & 1) && (k < 3 || out.pin);
       if (dir) {
         if (!out.dirichlet) continue;
         if (MODE == 0) {
@@ -328,6 +330,252 @@ struct NSOp {
     }
   }
   int64_t nn_;
+};
+
+// ----------------------------------------------- NS product from frozen coefficients
+// Within one NS block solve every coefficient of the product is fixed: the state the
+// Jacobian is taken at does not move.  NSBuildOp evaluates them once per solve, in
+// float64, at every quadrature point of every element; NSQOp then applies the
+// product by interpolating only the increment (dv, dp).  Per quadrature point:
+//   0 rho, 1 mu, 2-4 v, 5-13 L_kj = d_j v_k (k-major), 14-16 R_m,
+//   17 tau_m, 18 tau_c rho, 19 tau_m / rho,
+//   20-25 aB = sum_s a_s B^s, 26-43 aG[c][m] = sum_s a_s d_m B^s_c (c in [11,22,33,12,23,13]),
+//   a_s = alpha^s mu_L^s c_el (the solid-stress linearization of Section 2.4: its
+//   dependence on the solids is linear in these two sums, whatever their number).
+// Layout (one plane of elements per coefficient and quadrature point, x fastest with a
+// padded pitch):  C[((ez * 8 + q) * NCQ + c) * nxyp + ey * nxp + ex].
+constexpr int NCQ = 44;
+constexpr int NCQ_FLUID = 20;
+
+struct CoefArrays {
+  double* c64;   // float64 coefficients (the build writes them)
+  float* c32;    // float32 copy (rounded from float64), or null
+  int nxp;       // x pitch (elements, padded)
+  int64_t nxyp;  // nxp * ny
+};
+
+// Coefficient build: fields as NSOp MODE 0 (v(3), p, dv/dt(3), rho, mu, then alpha^s,
+// B^s(6) per solid of the pass).  Only the CTA that owns an element writes it.  Later
+// solid passes (fluid == 0) add their solids' sums into aB and aG.
+struct NSBuildOp {
+  using T = double;
+  static constexpr int NC = 1;
+  static constexpr int MINB = 1;
+  Fields F;
+  int nf;
+  int s0, s1;
+  int fluid;
+  int elastic_aug;
+  Phys P;
+  double rh[3], W;
+  CoefArrays C;
+
+  __device__ __forceinline__ const T* fptr(int f) const { return field_ptr<T>(F, f); }
+  using Red = NoRed;
+  __device__ __forceinline__ void begin_cta(Red&) const {}
+  __device__ __forceinline__ void end_cta(Red&) const {}
+
+  __device__ __forceinline__ void put(int64_t idx, double v, bool add) const {
+    if (add) v += C.c64[idx];
+    C.c64[idx] = v;
+    if (C.c32) C.c32[idx] = (float)v;
+  }
+
+  __device__ void element(const Corners<T>& cr, const ElemCtx& ec, T (&)[NC][8], Red&) const {
+    if (!ec.owned) return;  // halo copies of this element are built by its owner
+    const T rhx = rh[0], rhy = rh[1], rhz = rh[2];
+    const int fv = 0, fp = 3, fvd = 4, frho = 7, fmu = 8, fsol = 9;
+    const int64_t e0 = (int64_t)ec.ez * 8 * NCQ * C.nxyp + (int64_t)ec.ey * C.nxp + ec.ex;
+    T u[8];
+#pragma unroll 1
+    for (int q = 0; q < 8; ++q) {
+      QW<T> w;
+      w.set(q);
+      const int64_t b = e0 + (int64_t)q * NCQ * C.nxyp;
+      T v[3], L[3][3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        cr.get(fv + k, u);
+        const VG<T> r = interp_vg(u, w, rhx, rhy, rhz);
+        v[k] = r.v; L[k][0] = r.gx; L[k][1] = r.gy; L[k][2] = r.gz;
+      }
+      if (fluid) {
+        cr.get(frho, u); const T rho = interp_v(u, w);
+        cr.get(fmu, u);  const T mu = interp_v(u, w);
+        cr.get(fp, u);
+        const VG<T> pr = interp_vg(u, w, rhx, rhy, rhz);
+        const T gp[3] = {pr.gx, pr.gy, pr.gz};
+        T Rm[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          cr.get(fvd + k, u);
+          const T acc = interp_v(u, w) + v[0] * L[k][0] + v[1] * L[k][1] + v[2] * L[k][2];
+          Rm[k] = rho * acc + gp[k] - rho * P.grav[k];
+        }
+        const T vGv = P.Gd[0] * v[0] * v[0] + P.Gd[1] * v[1] * v[1] + P.Gd[2] * v[2] * v[2];
+        const T nu = mu / rho;
+        const T tau_m = 1.0 / sqrt(4.0 / (P.dt * P.dt) + vGv + P.c_i * nu * nu * P.GG);
+        const T tau_c = 1.0 / (P.trG * tau_m);
+        put(b + 0 * C.nxyp, rho, false);
+        put(b + 1 * C.nxyp, mu, false);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) put(b + (2 + k) * C.nxyp, v[k], false);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) put(b + (5 + 3 * k + j) * C.nxyp, L[k][j], false);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) put(b + (14 + k) * C.nxyp, Rm[k], false);
+        put(b + 17 * C.nxyp, tau_m, false);
+        put(b + 18 * C.nxyp, tau_c * rho, false);
+        put(b + 19 * C.nxyp, tau_m / rho, false);
+      }
+      T aB[6], aG[6][3];
+#pragma unroll
+      for (int cc = 0; cc < 6; ++cc) {
+        aB[cc] = 0.0;
+        aG[cc][0] = aG[cc][1] = aG[cc][2] = 0.0;
+      }
+      if (elastic_aug) {
+        for (int s = s0; s < s1; ++s) {
+          const int fs = fsol + 7 * (s - s0);
+          cr.get(fs, u);
+          const T a = interp_v(u, w) * P.muL[P.solid_phase[s]] * P.c_el;
+#pragma unroll
+          for (int cc = 0; cc < 6; ++cc) {
+            cr.get(fs + 1 + cc, u);
+            const VG<T> r = interp_vg(u, w, rhx, rhy, rhz);
+            aB[cc] += a * r.v;
+            aG[cc][0] += a * r.gx;
+            aG[cc][1] += a * r.gy;
+            aG[cc][2] += a * r.gz;
+          }
+        }
+      }
+      const bool add = !fluid;
+#pragma unroll
+      for (int cc = 0; cc < 6; ++cc) {
+        put(b + (20 + cc) * C.nxyp, aB[cc], add);
+#pragma unroll
+        for (int mm = 0; mm < 3; ++mm) put(b + (26 + 3 * cc + mm) * C.nxyp, aG[cc][mm], add);
+      }
+    }
+  }
+  __device__ __forceinline__ void finish(const NodeCtx&, const T (&)[NC], Red&) const {}
+};
+
+// NS product from the coefficients: fields dv(3), dp of the increment.  The element
+// contributions are accumulated without the quadrature weight W, applied per node.
+template <typename TT>
+struct NSQOp {
+  using T = TT;
+  static constexpr int NC = 4;
+  static constexpr int MINB = MinBlocks<TT>::value;
+  Fields F;
+  int nf;
+  const T* cq;   // coefficients of the compute type
+  int nxp;
+  int64_t nxyp;
+  int elastic;   // 0: aB, aG are zero (no solids or no augmentation) and are not read
+  double alpha, cm;
+  double rh[3], W;
+  OutDesc out;
+  int64_t nn_;
+
+  __device__ __forceinline__ const T* fptr(int f) const { return field_ptr<T>(F, f); }
+  using Red = NoRed;
+  __device__ __forceinline__ void begin_cta(Red&) const {}
+  __device__ __forceinline__ void end_cta(Red&) const {}
+
+  __device__ void element(const Corners<T>& cr, const ElemCtx& ec, T (&c)[NC][8], Red&) const {
+    const T rhx = T(rh[0]), rhy = T(rh[1]), rhz = T(rh[2]);
+    const T al = T(alpha), cmass = T(cm);
+    const T* e0 = cq + (int64_t)ec.ez * 8 * NCQ * nxyp + (int64_t)ec.ey * nxp + ec.ex;
+    const int64_t s = nxyp;
+    T u[8];
+#pragma unroll 1
+    for (int q = 0; q < 8; ++q) {
+      QW<T> w;
+      w.set(q);
+      const T* k = e0 + (int64_t)q * NCQ * s;
+      T kf[NCQ_FLUID];
+#pragma unroll
+      for (int i = 0; i < NCQ_FLUID; ++i) kf[i] = __ldg(k + i * s);
+      const T rho = kf[0], mu = kf[1];
+      const T v[3] = {kf[2], kf[3], kf[4]};
+      const T Rm[3] = {kf[14], kf[15], kf[16]};
+      const T tau_m = kf[17], tc_rho = kf[18], tm_rho = kf[19];
+      T dv[3], dL[3][3];
+#pragma unroll
+      for (int kk = 0; kk < 3; ++kk) {
+        cr.get(kk, u);
+        const VG<T> r = interp_vg(u, w, rhx, rhy, rhz);
+        dv[kk] = r.v; dL[kk][0] = al * r.gx; dL[kk][1] = al * r.gy; dL[kk][2] = al * r.gz;
+      }
+      cr.get(3, u);
+      const VG<T> dpr = interp_vg(u, w, rhx, rhy, rhz);
+      const T dgp[3] = {dpr.gx, dpr.gy, dpr.gz};
+      T vt[3], dRm[3];
+#pragma unroll
+      for (int kk = 0; kk < 3; ++kk) vt[kk] = al * dv[kk];
+#pragma unroll
+      for (int kk = 0; kk < 3; ++kk) {
+        const T* L = kf + 5 + 3 * kk;
+        const T dacc = cmass * dv[kk] + vt[0] * L[0] + vt[1] * L[1] + vt[2] * L[2] + v[0] * dL[kk][0] +
+                       v[1] * dL[kk][1] + v[2] * dL[kk][2];
+        dRm[kk] = rho * dacc;
+      }
+      T dE[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+      if (elastic) {
+        T aB[6];
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) aB[cc] = __ldg(k + (20 + cc) * s);
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) {
+          const int kk = sym_k(cc), l = sym_l(cc);
+          T pkl = T(0), plk = T(0);
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            pkl += dL[kk][m] * aB[sym_idx(m, l)];
+            plk += dL[l][m] * aB[sym_idx(m, kk)];
+          }
+          const T dd = vt[0] * __ldg(k + (26 + 3 * cc) * s) + vt[1] * __ldg(k + (27 + 3 * cc) * s) +
+                       vt[2] * __ldg(k + (28 + 3 * cc) * s);
+          dE[cc] = pkl + plk - dd;
+        }
+      }
+      const T dRc = dL[0][0] + dL[1][1] + dL[2][2];
+#pragma unroll
+      for (int kk = 0; kk < 3; ++kk) {
+        const T sk = tau_m * (dRm[kk] + dgp[kk]);
+        const T rk = tau_m * Rm[kk];
+        T gk[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          T sj = dE[sym_idx(kk, j)] + mu * (dL[kk][j] + dL[j][kk]) + vt[j] * rk + v[j] * sk;
+          if (j == kk) sj += -dpr.v + tc_rho * dRc;
+          gk[j] = sj;
+        }
+        scatter_vg(c[kk], w, dRm[kk], gk[0], gk[1], gk[2], rhx, rhy, rhz);
+      }
+      scatter_vg(c[3], w, dRc, tm_rho * (dRm[0] + dgp[0]), tm_rho * (dRm[1] + dgp[1]), tm_rho * (dRm[2] + dgp[2]),
+                 rhx, rhy, rhz);
+    }
+  }
+
+  __device__ __forceinline__ void finish(const NodeCtx& nc, const T (&acc)[NC], Red&) const {
+    const int64_t nn = nn_;
+    const uint8_t m = out.mask ? out.mask[nc.n] : 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      double* y = out.y + (int64_t)k * nn + nc.n;
+      if (((m >> k) & 1) && (k < 3 || out.pin)) {
+        *y = out.dx ? out.dx[(int64_t)k * nn + nc.n] : (double)out.dx32[(int64_t)k * nn + nc.n];
+      } else {
+        *y = W * (double)acc[k];
+      }
+    }
+  }
 };
 
 // ----------------------------------------------------------------- AC block

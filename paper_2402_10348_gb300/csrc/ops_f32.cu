@@ -5,6 +5,7 @@
 namespace fsi {
 
 template int launch_ns<float>(fsi_mesh*, int, const double*, double*, unsigned);
+template int launch_nsq<float>(fsi_mesh*, const double*, double*, unsigned);
 template int launch_ac<float>(fsi_mesh*, int, int, const double*, double*);
 template int launch_b<float>(fsi_mesh*, int, int, const double*, double*);
 

@@ -4,6 +4,67 @@
 namespace fsi {
 
 template int launch_ns<double>(fsi_mesh*, int, const double*, double*, unsigned);
+template int launch_nsq<double>(fsi_mesh*, const double*, double*, unsigned);
+
+// Builds the quadrature-point coefficients of the NS product at the staged state, in
+// float64, with their float32 copy; solids beyond one pass's shared memory are added
+// by further passes.
+int ns_build(fsi_mesh* m, unsigned flags) {
+  const int nxp = cq_pitch(m);
+  const int64_t len = (int64_t)m->g.nz * 8 * NCQ * nxp * m->g.ny;
+  if (m->cq_len < len) {
+    cudaFree(m->cq64);
+    cudaFree(m->cq32);
+    m->cq64 = nullptr;
+    m->cq32 = nullptr;
+    m->cq_len = 0;
+    FSI_CUDA(cudaMalloc(&m->cq64, sizeof(double) * (size_t)len));
+    FSI_CUDA(cudaMalloc(&m->cq32, sizeof(float) * (size_t)len));
+    m->cq_len = len;
+  }
+  const bool aug = (flags & FSI_ELASTIC_AUG) != 0;
+  const int ns = aug ? m->ns : 0;
+  const int fixed = 9;
+  const int per = std::min(solids_per_pass<double>(fixed), (MAXF - fixed) / 7);
+  if (per < 1 && ns > 0) return set_error(FSI_EINVAL, "NS coefficients: shared memory too small for one solid");
+  const double* xa = m->staged_xa;
+  const int64_t nn = m->nn;
+  int s0 = 0;
+  bool first = true;
+  do {
+    const int s1 = ns == 0 ? 0 : std::min(ns, s0 + per);
+    NSBuildOp op;
+    memset(&op, 0, sizeof(op));
+    int f = 0;
+    for (int k = 0; k < 3; ++k) put<double>(op.F, f++, xa + k * nn);  // v
+    put<double>(op.F, f++, xa + 3 * nn);                                 // p^{n+1}
+    for (int k = 0; k < 3; ++k) put<double>(op.F, f++, m->xd + k * nn); // dv/dt
+    put<double>(op.F, f++, m->mat);                                      // rho
+    put<double>(op.F, f++, m->mat + nn);                                 // mu
+    for (int s = s0; s < s1; ++s) {
+      put<double>(op.F, f++, m->mat + (2 + s) * nn);                     // alpha^s
+      const int c0 = 4 + m->N + 6 * s;
+      for (int c = 0; c < 6; ++c) put<double>(op.F, f++, xa + (c0 + c) * nn);
+    }
+    op.nf = f;
+    op.s0 = s0;
+    op.s1 = s1;
+    op.fluid = first ? 1 : 0;
+    op.elastic_aug = aug ? 1 : 0;
+    op.P = m->P;
+    fill_common(m, op.rh, &op.W);
+    op.C.c64 = m->cq64;
+    op.C.c32 = m->cq32;
+    op.C.nxp = nxp;
+    op.C.nxyp = (int64_t)nxp * m->g.ny;
+    if (int rc = run_tile(m, op, P_NS_BUILD)) return rc;
+    first = false;
+    s0 = s1;
+  } while (s0 < ns);
+  m->cq_gen = m->stage_gen;
+  m->cq_flags = flags & FSI_ELASTIC_AUG;
+  return FSI_OK;
+}
 template int launch_ac<double>(fsi_mesh*, int, int, const double*, double*);
 template int launch_b<double>(fsi_mesh*, int, int, const double*, double*);
 

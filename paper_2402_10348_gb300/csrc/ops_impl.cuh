@@ -152,6 +152,7 @@ int ns_pass(fsi_mesh* m, const double* dx, double* y, unsigned flags, int s0, in
   op.out.vD = m->vD;
   op.out.accumulate = first ? 0 : 1;
   op.out.dirichlet = first ? 1 : 0;
+  op.out.pin = m->pin_active;
   op.nn_ = nn;
   return run_tile(m, op, op_class<T, MODE>(0));
 }
@@ -177,6 +178,43 @@ int launch_ns(fsi_mesh* m, int mode, const double* dx, double* y, unsigned flags
     s0 = s1;
   } while (s0 < ns);
   return FSI_OK;
+}
+
+// x pitch of the coefficient planes: a multiple of 16 bytes for either compute type
+inline int cq_pitch(const fsi_mesh* m) { return (m->g.nx + 3) & ~3; }
+
+template <typename T>
+int launch_nsq(fsi_mesh* m, const double* dx, double* y, unsigned flags) {
+  const unsigned eflags = flags & FSI_ELASTIC_AUG;
+  if (m->cq_gen != m->stage_gen || m->cq_flags != eflags || !m->cq64) {
+    if (int rc = ns_build(m, flags)) return rc;
+  }
+  NSQOp<T> op;
+  memset(&op, 0, sizeof(op));
+  const int64_t nn = m->nn;
+  for (int k = 0; k < 4; ++k) put_dx<T>(op.F, k, m, dx, k * nn);
+  op.nf = 4;
+  if constexpr (sizeof(T) == 8) op.cq = reinterpret_cast<const T*>(m->cq64);
+  else op.cq = reinterpret_cast<const T*>(m->cq32);
+  op.nxp = cq_pitch(m);
+  op.nxyp = (int64_t)op.nxp * m->g.ny;
+  op.elastic = (eflags && m->ns > 0) ? 1 : 0;
+  op.alpha = m->P.alpha;
+  op.cm = m->P.c_mass;
+  fill_common(m, op.rh, &op.W);
+  op.out.y = y;
+  op.out.dx = dx;
+  op.out.dx32 = sizeof(T) == 4 ? m->dx32 : nullptr;
+  op.out.mask = m->mask;
+  op.out.dirichlet = 1;
+  op.out.pin = m->pin_active;
+  op.nn_ = nn;
+  // algorithmic bytes: the coefficient planes once per element, the increment read and
+  // the product written once per node, the Dirichlet mask
+  const int64_t ne = (int64_t)m->g.nx * m->g.ny * m->g.nz;
+  prof_bytes(m, jvp_class<T>(0),
+             (double)ne * 8.0 * (op.elastic ? NCQ : NCQ_FLUID) * sizeof(T) + (double)nn * (4.0 * sizeof(T) + 32.0 + 1.0));
+  return run_tile(m, op, jvp_class<T>(0));
 }
 
 template <typename T, int MODE>

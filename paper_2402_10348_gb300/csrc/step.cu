@@ -33,6 +33,27 @@ __global__ void corrector_kernel(const double* x, double* xn, double* xdn, doubl
 
 static int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8)); }
 
+// Pressure level after an NS solve with the pin node's continuity equation kept: the
+// update of the pinned formulation is the computed one minus the constant that brings
+// p^{n+1} at the pin node to zero, s = x_p[pin] + dx_p[pin] (constant pressure is a null
+// mode of the enclosed domain's system, so the shifted update solves it as well).
+__global__ void pin_shift_value(const double* xp, const double* dxp, int pin, double* s) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *s = xp[pin] + dxp[pin];
+}
+__global__ void pin_shift_apply(double* dxp, const double* s, int64_t nn) {
+  const double v = *s;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < nn; n += stride) dxp[n] -= v;
+}
+
+// Restores the pressure pin of a mesh when a block solve leaves (also on errors).
+struct PinGuard {
+  fsi_mesh* m;
+  int saved;
+  PinGuard(fsi_mesh* mm, int active) : m(mm), saved(mm->pin_active) { m->pin_active = active; }
+  ~PinGuard() { m->pin_active = saved; }
+};
+
 }  // namespace fsi
 
 using namespace fsi;
@@ -82,11 +103,23 @@ int fsi_step(fsi_mesh* m, fsi_state* st, const fsi_step_opts* o, fsi_step_info* 
         m->gamma[b.index] = m->fixed_gamma[b.index] >= 0.0 ? m->fixed_gamma[b.index] : gb[0];
         m->beta[b.index] = gb[1];
       }
-      if ((rc = op_residual(m, b, rhs))) return rc;
-      if ((rc = vec_scale_copy(m, -1.0, rhs, rhs, b.n))) return rc;
+      // NS block of an enclosed domain: the pin node keeps its continuity equation in
+      // the solve and the pressure level is set by the shift below
+      const bool shift = b.kind == 0 && m->pin_node >= 0 && m->enclosed && m->pin_active &&
+                         !(o->solve.flags & FSI_PINNED_SOLVE);
       fsi_solve_info si{};
-      rc = gmres_solve(m, b, rhs, dx, o->solve, &si);
-      if (rc && rc != FSI_ENOCONV) return rc;
+      {
+        PinGuard guard(m, shift ? 0 : m->pin_active);
+        if ((rc = op_residual(m, b, rhs))) return rc;
+        if ((rc = vec_scale_copy(m, -1.0, rhs, rhs, b.n))) return rc;
+        rc = gmres_solve(m, b, rhs, dx, o->solve, &si);
+        if (rc && rc != FSI_ENOCONV) return rc;
+      }
+      if (shift) {
+        FSI_LAUNCH(m, P_STAGE, pin_shift_value<<<1, 32, 0, m->stream>>>(st->x + 3 * nn, dx + 3 * nn, m->pin_node,
+                                                                         m->red + 8));
+        FSI_LAUNCH(m, P_STAGE, pin_shift_apply<<<grid_for(nn), 256, 0, m->stream>>>(dx + 3 * nn, m->red + 8, nn));
+      }
       inf.worst_rel_res = std::max(inf.worst_rel_res, si.rel_res);
       if (si.stalled) inf.stalled_solves++;
       if (si.fallback) inf.fallback_solves++;

@@ -21,6 +21,8 @@ FSI_FP32 = 0x2
 FSI_PC_NONE, FSI_PC_JACOBI, FSI_PC_LEARNED = 0, 1, 2
 FSI_HARVEST = 0x10
 FSI_PC_ALTERNATE = 0x20
+FSI_NO_STALL_STOP = 0x40
+FSI_PINNED_SOLVE = 0x80
 FSI_PREC_FP64, FSI_PREC_FP32_IR = 0, 1
 FSI_BC_NATURAL, FSI_BC_DIRICHLET = 0, 1
 FSI_RULE_SURFACE, FSI_RULE_COMPLEMENT = 0, 1
@@ -102,17 +104,18 @@ class fsi_profile_entry(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("ms", C.c_double), ("bytes", C.c_double)]
 
 
-FSI_PROF_CLASSES = 23
+FSI_PROF_CLASSES = 24
 
 EXPORTS = ["fsi_create_mesh", "fsi_destroy_mesh", "fsi_set_stream", "fsi_mesh_info", "fsi_residual",
            "fsi_jvp", "fsi_diag", "fsi_update_ac_coeffs", "fsi_set_ac_coeffs", "fsi_fix_gamma",
+           "fsi_set_pressure_pin",
            "fsi_gmres", "fsi_step", "fsi_init_phases", "fsi_gamma_beta_noalloc", "fsi_profile",
            "fsi_profile_read", "fsi_pc_create", "fsi_pc_destroy", "fsi_pc_layout", "fsi_pc_set_weights",
            "fsi_pc_get_weights", "fsi_pc_set_norm", "fsi_pc_get_norm", "fsi_pc_forward", "fsi_pc_grad",
            "fsi_pc_apply", "fsi_pc_add_pair", "fsi_pc_pairs", "fsi_pc_fit_norm", "fsi_pc_train", "fsi_set_pc",
            "fsi_batch_create", "fsi_batch_destroy", "fsi_batch_layout", "fsi_batch_jvp", "fsi_batch_gmres",
            "fsi_batch_autotune", "fsi_batch_set_graph", "fsi_center_of_mass", "fsi_track_points",
-           "fsi_last_error"]
+           "fsi_probe_peaks", "fsi_last_error"]
 
 _lib = None
 
@@ -244,6 +247,10 @@ def fsi_fix_gamma(mesh: Mesh, phase: int, gamma: float):
     _check(lib().fsi_fix_gamma(mesh.handle, C.c_int32(phase), C.c_double(gamma)))
 
 
+def fsi_set_pressure_pin(mesh: Mesh, active: bool):
+    _check(lib().fsi_set_pressure_pin(mesh.handle, C.c_int32(1 if active else 0)))
+
+
 def solve_opts(m=30, max_iter=2000, rtol=1e-8, precond=FSI_PC_JACOBI, precision=FSI_PREC_FP64,
                flags=FSI_ELASTIC_AUG, ir_max=10, ir_inner_rtol=1e-3) -> fsi_solve_opts:
     return fsi_solve_opts(m, max_iter, rtol, precond, precision, flags, ir_max, ir_inner_rtol)
@@ -328,6 +335,13 @@ def fsi_gamma_beta_noalloc(nx, ny, nz, lx, ly, lz, eta, v, phi, gamma_beta, stre
     _check(lib().fsi_gamma_beta_noalloc(C.c_int32(nx), C.c_int32(ny), C.c_int32(nz), C.c_double(lx),
                                         C.c_double(ly), C.c_double(lz), C.c_double(eta), _dptr(v), _dptr(phi),
                                         _dptr(gamma_beta), C.c_void_p(st.cuda_stream)))
+
+
+def fsi_probe_peaks() -> dict:
+    """Measured float32/float64 FMA rates (TFLOP/s) and read/copy bandwidth (GB/s)."""
+    v = [C.c_double() for _ in range(4)]
+    _check(lib().fsi_probe_peaks(*[C.byref(x) for x in v]))
+    return {"fp32_tflops": v[0].value, "fp64_tflops": v[1].value, "read_gbs": v[2].value, "copy_gbs": v[3].value}
 
 
 def fsi_profile(mesh: Mesh, enable: bool):

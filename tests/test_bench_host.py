@@ -29,10 +29,24 @@ def test_roofline_hbm_and_alu():
     # a float32 basis (the inner solves of refinement) has no float64 roof
     assert "alu_fp64" not in bench.roofline("krylov_dot", 10, 2.0, 13.55e9, d, pk, basis_f64=False)
     r = bench.roofline("ns_jvp_f32", 4, 1.0, 0.0, d, pk)
-    flops = 8 * (858 + 407 * d.n_solid) * d.ne
+    flops = 8 * (486 + 114) * d.ne
     assert r["bound"] == "alu"
     assert r["achieved"] == pytest.approx(flops / 250e-6 / 1e12, rel=1e-3)
     assert bench.roofline("stage", 0, 0.0, 0.0, d, pk) is None
+
+
+def test_roofline_picks_the_binding_roof():
+    """The NS product declares its coefficient stream: the float32 product is bound by
+    HBM (1.26 GFLOP against 80 TFLOP/s takes less than 0.38 GB against 6.8 TB/s), the
+    float64 one by the float64 FMA rate; the other roof is reported beside it."""
+    d = cavity64().desc
+    pk = {"hbm_gbs": 6775.3, "hbm_src": "measured", "fp32_tflops": 80.5, "fp64_tflops": 1.26,
+          "alu_src": "test"}
+    r32 = bench.roofline("ns_jvp_f32", 10, 1.0, 10 * 383e6, d, pk)
+    assert r32["bound"] == "hbm" and r32["other_roof"]["bound"] == "alu"
+    assert r32["achieved"] == pytest.approx(383e6 / 100e-6 / 1e9, rel=1e-3)
+    r64 = bench.roofline("ns_jvp_f64", 10, 10.0, 10 * 760e6, d, pk)
+    assert r64["bound"] == "alu" and r64["other_roof"]["bound"] == "hbm"
 
 
 def test_traffic_record_requires_matching_source(tmp_path, monkeypatch):

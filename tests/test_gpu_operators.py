@@ -143,3 +143,19 @@ def test_invalid_arguments_rejected():
     bad.nx = 0
     with pytest.raises(fsi.FsiError):
         fsi.fsi_create_mesh(bad)
+
+
+def test_ns_operators_with_independent_indicators():
+    """Three phases whose fractions do not sum to one (each indicator its own sphere
+    profile, as the indicators of N > 2 phases evolve independently): float64 residual
+    and product against the oracle, float32 product within TOL32."""
+    d = desc_small(n=(16, 13, 11), n_fluid=1, n_solid=2)
+    x1, xn, xdn = random_state(d, 5, independent=True)
+    alpha_sum = sum((1.0 + x1[4 + i]) / 2.0 for i in range(d.n_phase))
+    assert np.abs(alpha_sum - 1.0).max() > 0.5  # not a partition of unity
+    pb, st, g = Problem(d), State(x1, xn, xdn), Gpu(d, x1, xn, xdn)
+    assert relmax(g.residual(fsi.FSI_BLOCK_NS, 4 * d.nn), ns.ns_residual(pb, st).ravel()) <= TOL64
+    dx = np.random.default_rng(2).normal(size=(4, d.nn))
+    ref = ns.ns_jvp(pb, st, dx).ravel()
+    assert relmax(g.jvp(fsi.FSI_BLOCK_NS, dx), ref) <= TOL64
+    assert relmax(g.jvp(fsi.FSI_BLOCK_NS, dx, fsi.FSI_ELASTIC_AUG | fsi.FSI_FP32), ref) <= TOL32

@@ -316,12 +316,16 @@ def node_coords(desc: MeshDesc) -> np.ndarray:
 
 
 def random_state(desc: MeshDesc, seed: int, amp_v: float = 1.0, amp_B: float = 0.05,
-                 noise: float = 0.05, phi_range: float = 1.0):
+                 noise: float = 0.05, phi_range: float = 1.0, independent: bool = False):
     """Seeded smooth random state (x^{n+1}, x^n, xdot^n), each (ncomp, nn) float64.
 
     Velocities and pressure: a few random Fourier modes plus nodal noise.
     Phase indicators: tanh profiles of random spheres (values in [-1,1] scaled by
     phi_range) plus noise.  B: identity plus a small random symmetric perturbation.
+    By default the phase fractions sum to one; with `independent` every phase i >= 1
+    is its own sphere profile and phase 0 is 1 - s/2 for a further sphere profile s,
+    so the fractions overlap (their sum ranges over about [0.5, 2.5]) while phase 0
+    never drops below one half (the independently evolved indicators of N > 2 phases).
     """
     rng = np.random.default_rng(seed)
     X = node_coords(desc)
@@ -355,9 +359,14 @@ def random_state(desc: MeshDesc, seed: int, amp_v: float = 1.0, amp_B: float = 0
             r = rng.uniform(0.15, 0.3) * float(L.min())
             d = r - np.sqrt(((X - c[:, None]) ** 2).sum(0))
             s = (1.0 + phi_range * np.tanh(d / (math.sqrt(2.0) * eps))) / 2.0
-            alphas[i] = s * remaining
+            alphas[i] = s if independent else s * remaining
             remaining = remaining - alphas[i]
         alphas[0] = remaining
+        if independent:
+            c = rng.uniform(0.3, 0.7, size=3) * L[:, 0]
+            r = rng.uniform(0.15, 0.3) * float(L.min())
+            d = r - np.sqrt(((X - c[:, None]) ** 2).sum(0))
+            alphas[0] = 1.0 - 0.25 * (1.0 + np.tanh(d / (math.sqrt(2.0) * eps)))
         for i in range(desc.n_phase):
             x[4 + i] = 2.0 * alphas[i] - 1.0 + 0.4 * noise * rng.normal(size=nn)
         base = 4 + desc.n_phase
