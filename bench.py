@@ -41,7 +41,10 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="fsi", choices=["fsi", "reference"])
-    p.add_argument("--precision", default="fp32ir", choices=["fp32ir", "fp64"])
+    p.add_argument("--precision", default="fp64", choices=["fp32ir", "fp64"],
+                   help="the headline arm's arithmetic; the other one runs as a second arm from the same state")
+    p.add_argument("--no-other", action="store_true", help="skip the second-precision arm")
+    p.add_argument("--no-operators", action="store_true", help="skip the ship/ice per-apply operator rates")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner arm")
@@ -256,73 +259,86 @@ def run_batch_case(count: int = 64, reps: int = 5):
     print(json.dumps(out), flush=True)
 
 
-def run_operators_case(reps: int = 3):
-    """Per-apply GDoF/s of every element operator (residual, float64 JVP, float32 JVP of
-    each block) at the three single-mesh sizes: the 64^3 cavity, the falling sphere
-    (96x96x192, 3 phases, 2 solids) and ship/ice (256x128x64, 11 phases, 9 solids).  The
-    states are drawn on the device (phase fractions a partition of unity, B near I);
-    per-apply times come from the library's CUDA-event profiler (staging excluded)."""
+def operator_rates_of(wl, fsi, torch, dev, reps: int = 3) -> dict:
+    """Per-apply GDoF/s of every element operator (residual, float64 and float32 product
+    of each block) on one workload's mesh, from a state drawn on the device (phase
+    fractions a partition of unity, B near I).  Times come from the library's CUDA-event
+    profiler; the NS products stream quadrature-point coefficients built once per state
+    (their build, `ns_coeffs`, is reported apart)."""
     import collections
+    d = wl.desc
+    nn, N, ns = d.nn, d.n_phase, d.n_solid
+    g = torch.Generator(device=dev).manual_seed(0)
+
+    def rnd(*shape):
+        return torch.rand(*shape, dtype=torch.float64, device=dev, generator=g)
+
+    x = torch.empty(d.ncomp, nn, dtype=torch.float64, device=dev)
+    x[0:3] = 0.2 * (rnd(3, nn) - 0.5)
+    x[3] = rnd(nn)
+    a = rnd(N, nn) + 0.05
+    x[4:4 + N] = 2.0 * a / a.sum(0) - 1.0
+    for s in range(ns):
+        b0 = 4 + N + 6 * s
+        x[b0:b0 + 3] = 1.0 + 0.05 * (rnd(3, nn) - 0.5)
+        x[b0 + 3:b0 + 6] = 0.05 * (rnd(3, nn) - 0.5)
+    x = x.reshape(-1).contiguous()
+    xn = (x + 0.01 * (rnd(x.numel()) - 0.5)).contiguous()
+    xdn = (0.1 * (rnd(x.numel()) - 0.5)).contiguous()
+    del a
+    mesh = fsi.fsi_create_mesh(d)
+    fsi.fsi_set_stream(mesh)
+    for i in range(N):
+        fsi.fsi_set_ac_coeffs(mesh, i, 0.5, 0.1)
+    blocks = [("ns", fsi.FSI_BLOCK_NS, 4 * nn)] + [("ac", fsi.FSI_BLOCK_AC(i), nn) for i in range(N)] + \
+             [("b", fsi.FSI_BLOCK_B(s), 6 * nn) for s in range(ns)]
+    applies, dofs = collections.Counter(), {}
+    for profiled in (False, True):  # one untimed pass, then the profiled ones
+        if profiled:
+            fsi.fsi_profile(mesh, True)
+        for kind, blk, n in blocks:
+            r = torch.empty(n, dtype=torch.float64, device=dev)
+            y = torch.empty(n, dtype=torch.float64, device=dev)
+            dx = (rnd(n) - 0.5).contiguous()
+            fsi.fsi_residual(mesh, blk, x, xn, xdn, r)
+            for _ in range(reps if profiled else 1):
+                fsi.fsi_jvp(mesh, blk, x, xn, xdn, dx, y)
+            fsi.fsi_residual(mesh, blk, x, xn, xdn, r)
+            for _ in range(reps if profiled else 1):
+                fsi.fsi_jvp(mesh, blk, x, xn, xdn, dx, y, fsi.FSI_ELASTIC_AUG | fsi.FSI_FP32)
+            if profiled:
+                applies[f"{kind}_residual"] += 2
+                dofs[f"{kind}_residual"] = n
+                for cls in (f"{kind}_jvp_f64", f"{kind}_jvp_f32"):
+                    applies[cls] += reps
+                    dofs[cls] = n
+    prof = fsi.fsi_profile_read(mesh)
+    fsi.fsi_profile(mesh, False)
+    torch.cuda.synchronize()
+    ops = {}
+    for cls, k in applies.items():
+        launches, ms = prof[cls][0], prof[cls][1]
+        if ms > 0:
+            ops[cls] = {"gdofs": round(dofs[cls] * k / (ms / 1e3) / 1e9, 3),
+                        "us_per_apply": round(ms / k * 1e3, 2), "launches_per_apply": launches / k}
+    if prof.get("ns_coeffs", (0, 0))[0] > 0:
+        ops["ns_coeffs"] = {"us_per_build": round(prof["ns_coeffs"][1] / prof["ns_coeffs"][0] * 1e3, 2),
+                            "launches": prof["ns_coeffs"][0]}
+    del mesh, x, xn, xdn
+    torch.cuda.empty_cache()
+    return {"workload": wl.name, "nodes": nn, "phases": N, "solids": ns, "dof_per_node": d.ncomp,
+            "unit": "GDoF/s per apply", "ops": ops}
+
+
+def run_operators_case(reps: int = 3):
+    """Per-apply GDoF/s of every element operator at the three single-mesh sizes: the
+    64^3 cavity, the falling sphere (96x96x192, 3 phases, 2 solids) and ship/ice
+    (256x128x64, 11 phases, 9 solids)."""
     import torch
     from paper_2402_10348_gb300 import fsi
     from workloads import cavity64, falling, shipice
     dev = torch.device("cuda", 0)
-    out = {}
-    for wl in (cavity64(), falling(), shipice()):
-        d = wl.desc
-        nn, N, ns = d.nn, d.n_phase, d.n_solid
-        g = torch.Generator(device=dev).manual_seed(0)
-
-        def rnd(*shape):
-            return torch.rand(*shape, dtype=torch.float64, device=dev, generator=g)
-
-        x = torch.empty(d.ncomp, nn, dtype=torch.float64, device=dev)
-        x[0:3] = 0.2 * (rnd(3, nn) - 0.5)
-        x[3] = rnd(nn)
-        a = rnd(N, nn) + 0.05
-        x[4:4 + N] = 2.0 * a / a.sum(0) - 1.0
-        for s in range(ns):
-            b0 = 4 + N + 6 * s
-            x[b0:b0 + 3] = 1.0 + 0.05 * (rnd(3, nn) - 0.5)
-            x[b0 + 3:b0 + 6] = 0.05 * (rnd(3, nn) - 0.5)
-        x = x.reshape(-1).contiguous()
-        xn = (x + 0.01 * (rnd(x.numel()) - 0.5)).contiguous()
-        xdn = (0.1 * (rnd(x.numel()) - 0.5)).contiguous()
-        del a
-        mesh = fsi.fsi_create_mesh(d)
-        fsi.fsi_set_stream(mesh)
-        for i in range(N):
-            fsi.fsi_set_ac_coeffs(mesh, i, 0.5, 0.1)
-        blocks = [("ns", fsi.FSI_BLOCK_NS, 4 * nn)] + [("ac", fsi.FSI_BLOCK_AC(i), nn) for i in range(N)] + \
-                 [("b", fsi.FSI_BLOCK_B(s), 6 * nn) for s in range(ns)]
-        applies, dofs = collections.Counter(), {}
-        for profiled in (False, True):  # one untimed pass, then the profiled ones
-            if profiled:
-                fsi.fsi_profile(mesh, True)
-            for kind, blk, n in blocks:
-                r = torch.empty(n, dtype=torch.float64, device=dev)
-                y = torch.empty(n, dtype=torch.float64, device=dev)
-                dx = (rnd(n) - 0.5).contiguous()
-                for _ in range(reps if profiled else 1):
-                    fsi.fsi_residual(mesh, blk, x, xn, xdn, r)
-                    fsi.fsi_jvp(mesh, blk, x, xn, xdn, dx, y)
-                    fsi.fsi_jvp(mesh, blk, x, xn, xdn, dx, y, fsi.FSI_ELASTIC_AUG | fsi.FSI_FP32)
-                if profiled:
-                    for cls in (f"{kind}_residual", f"{kind}_jvp_f64", f"{kind}_jvp_f32"):
-                        applies[cls] += reps
-                        dofs[cls] = n
-        prof = fsi.fsi_profile_read(mesh)
-        fsi.fsi_profile(mesh, False)
-        torch.cuda.synchronize()
-        ops = {}
-        for cls, k in applies.items():
-            launches, ms = prof[cls][0], prof[cls][1]
-            if ms > 0:
-                ops[cls] = {"gdofs": round(dofs[cls] * k / (ms / 1e3) / 1e9, 3),
-                            "us_per_apply": round(ms / k * 1e3, 2), "launches_per_apply": launches / k}
-        out[wl.name] = {"nodes": nn, "phases": N, "solids": ns, "dof_per_node": d.ncomp, "ops": ops}
-        del mesh, x, xn, xdn
-        torch.cuda.empty_cache()
+    out = {wl.name: operator_rates_of(wl, fsi, torch, dev, reps) for wl in (cavity64(), falling(), shipice())}
     print(json.dumps({"case": "operators", "reps": reps, "unit": "GDoF/s per apply", "configs": out}), flush=True)
 
 
@@ -486,13 +502,16 @@ class Clocks:
 
 # ---------------------------------------------------------------- roofline data
 # Algorithmic float operations per element of one element evaluation (no halo
-# recomputation), counted from the arithmetic of the kernels' element functions
-# (see the count table in the design doc); multiply by the elements of one launch.
+# recomputation), counted from the arithmetic of the kernels' element functions;
+# multiply by the elements of one launch.
 def flops_per_element(kernel: str, n_solid: int) -> float:
-    """Per quadrature point: NS JVP 858 + 407 per solid (elastic linearization),
-    NS residual 635 + 167 per solid, AC JVP 247, B JVP 892; 8 points per element."""
-    per_qp = {"ns_jvp": 858 + 407 * n_solid, "ns_residual": 635 + 167 * n_solid,
-              "ac_jvp": 247, "b_jvp": 892}
+    """Per quadrature point: the NS product from frozen coefficients 486 + 114 with solids
+    (interpolation of dv, dp: 172; convective and mass terms 54; stresses 92; the
+    elastic linearization 114; test-function scatter 166), its coefficient build
+    635 + 167 per solid, NS residual 635 + 167 per solid, AC JVP 247, B JVP 892; 8
+    points per element."""
+    per_qp = {"ns_jvp": 486 + (114 if n_solid > 0 else 0), "ns_coeffs": 635 + 167 * n_solid,
+              "ns_residual": 635 + 167 * n_solid, "ac_jvp": 247, "b_jvp": 892}
     for k, v in per_qp.items():
         if kernel.startswith(k):
             return 8.0 * v
@@ -515,22 +534,29 @@ def operator_rates(prof: dict, nn: int) -> dict:
     return out
 
 
-def peaks():
+def peaks(measured=None):
+    """Roofline denominators: HBM from MEASURED_PEAKS.json (the driver's copy figure),
+    float32 / float64 FMA rates from fsi_probe_peaks on this GPU in the same run (else
+    derived from unit counts: 152 SMs x 128 FP32 lanes, 2 DFMA per clock, x 2 flop x
+    the maximum SM clock)."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     pk = {}
     if os.path.exists(path):
         pk = json.load(open(path))
-    # float32 / float64 FMA peaks from unit counts and the maximum SM clock:
-    # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz; FP64: 152 x 2 DFMA/clk x 2 x 2.07 GHz
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    return {
+    out = {
         "hbm_gbs": pk.get("hbm_gbs", 6800.0),
         "hbm_src": "measured" if "hbm_gbs" in pk else "fallback",
         "fp32_tflops": 152 * 128 * 2 * sm_mhz * 1e6 / 1e12,
         "fp64_tflops": 152 * 2 * 2 * sm_mhz * 1e6 / 1e12,
+        "alu_src": "derived: 152 SMs x FMA lanes per SM x 2 flop x max SM clock",
         "bf16_tflops": pk.get("bf16_tflops", 1900.0),
         "bf16_src": "measured (cuBLAS bf16 burst)" if "bf16_tflops" in pk else "fallback",
     }
+    if measured:
+        out.update(fp32_tflops=measured["fp32_tflops"], fp64_tflops=measured["fp64_tflops"],
+                   alu_src="measured in this run (fsi_probe_peaks: 8 independent FMA chains per thread)")
+    return out
 
 
 def traffic_record(kernel: str):
@@ -553,43 +579,50 @@ def traffic_record(kernel: str):
 
 
 def roofline(name, launches, ms, nbytes, d, pk, basis_f64=True):
-    """Roofline of one kernel class over the timed region: HBM-bound classes from the
-    algorithmic bytes their launch sites declare, ALU-bound element operators from
-    the flop count of one element evaluation times the elements of a launch."""
+    """Roofline of one kernel class over the timed region.  Vector (Krylov) classes:
+    the algorithmic bytes their launch sites declare against the HBM peak.  Element
+    operators: the flop count of one element evaluation times the elements of a launch
+    against the FMA peak of their precision and, where the launch declares its bytes
+    (the NS product streams its coefficients), those bytes against the HBM peak; the
+    roof with the longer minimum time binds and is the one reported."""
     if launches <= 0 or ms <= 0:
         return None
     out = {"kernel": name, "launches": launches, "avg_launch_us": round(ms / launches * 1e3, 2)}
-    if nbytes > 0:
-        achieved = nbytes / (ms / 1e3) / 1e9
-        rec = traffic_record(name)
-        out.update(bound="hbm", achieved=round(achieved, 1), peak=pk["hbm_gbs"], unit="GB/s",
-                   frac=round(achieved / pk["hbm_gbs"], 4),
-                   traffic=None if rec is None else round(rec["traffic_ratio"] * nbytes / launches),
-                   algorithmic_bytes_per_launch=round(nbytes / launches),
-                   peak_src=pk["hbm_src"] + " (MEASURED_PEAKS.json copy, read+write)")
-        if rec is not None:
-            out["traffic_note"] = rec["note"]
-        if basis_f64 and (name.startswith("krylov_dot") or name.startswith("krylov_update")):
-            # the second roof of the float64 projections and updates: one float64 FMA per
-            # float64 the launch reads (GB300 issues ~0.63 T DFMA/s, one per 8 bytes at
-            # 5 TB/s); a float32 basis has no such roof
-            tf = nbytes / 8.0 * 2.0 / (ms / 1e3) / 1e12
-            out["alu_fp64"] = {"achieved": round(tf, 3), "peak": round(pk["fp64_tflops"], 3), "unit": "TFLOP/s",
-                               "frac": round(tf / pk["fp64_tflops"], 4),
-                               "note": "2 flop per algorithmic float64 element; peak derived from 152 SMs x 2 "
-                                       "DFMA/clk x 2 flop x max SM clock"}
-        return out
+    t = ms / launches / 1e3  # s per launch
     fpe = flops_per_element(name, d.n_solid)
+    rec = traffic_record(name)
+    hbm = alu = None
+    if nbytes > 0:
+        b = nbytes / launches
+        hbm = {"bound": "hbm", "achieved": round(b / t / 1e9, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+               "frac": round(b / t / 1e9 / pk["hbm_gbs"], 4), "algorithmic_bytes_per_launch": round(b),
+               "t_min_us": b / (pk["hbm_gbs"] * 1e9) * 1e6,
+               "peak_src": pk["hbm_src"] + " (MEASURED_PEAKS.json copy, read+write)"}
     if fpe > 0:
         flops = fpe * d.ne
-        achieved = flops / (ms / launches / 1e3) / 1e12
         peak = pk["fp32_tflops"] if name.endswith("f32") else pk["fp64_tflops"]
-        rec = traffic_record(name)
-        out.update(bound="alu", achieved=round(achieved, 3), peak=round(peak, 2), unit="TFLOP/s",
-                   frac=round(achieved / peak, 4), traffic=None if rec is None else rec["traffic_per_launch"],
-                   algorithmic_flops_per_launch=flops,
-                   peak_src="derived: 152 SMs x FMA lanes per SM x 2 flop x max SM clock")
+        alu = {"bound": "alu", "achieved": round(flops / t / 1e12, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+               "frac": round(flops / t / 1e12 / peak, 4), "algorithmic_flops_per_launch": flops,
+               "t_min_us": flops / (peak * 1e12) * 1e6, "peak_src": pk.get("alu_src", "derived")}
+    elif hbm is not None and basis_f64 and (name.startswith("krylov_dot") or name.startswith("krylov_update")):
+        # float64 projections and updates do one float64 FMA per float64 element read
+        tf = nbytes / launches / 8.0 * 2.0 / t / 1e12
+        out["alu_fp64"] = {"achieved": round(tf, 3), "peak": round(pk["fp64_tflops"], 3), "unit": "TFLOP/s",
+                           "frac": round(tf / pk["fp64_tflops"], 4), "peak_src": pk.get("alu_src", "derived")}
+    bind = max([r for r in (hbm, alu) if r is not None], key=lambda r: r["t_min_us"], default=None)
+    if bind is None:
         return out
+    other = alu if bind is hbm else hbm
+    out.update({k: v for k, v in bind.items() if k != "t_min_us"})
+    if other is not None:
+        out["other_roof"] = {k: v for k, v in other.items() if k != "t_min_us"}
+    traffic = None
+    if rec is not None:
+        traffic = rec.get("traffic_per_launch")
+        if traffic is None and "traffic_ratio" in rec and nbytes > 0:
+            traffic = round(rec["traffic_ratio"] * nbytes / launches)
+        out["traffic_note"] = rec["note"]
+    out["traffic"] = traffic
     return out
 
 
@@ -607,6 +640,29 @@ def initial_state(fsi, mesh, wl, torch, dev):
     return x, x.clone(), torch.zeros_like(x)
 
 
+FIELDS_OF = lambda d: {"v": (0, 3), "p": (3, 4), "phi": (4, 4 + d.n_phase), "B": (4 + d.n_phase, d.ncomp)}
+
+
+def field_errors(d, got, ref):
+    """Relative L2 distance per field (v, p, phi, B) of two state vectors."""
+    import torch
+    nn = d.nn
+    out = {}
+    for k, (c0, c1) in FIELDS_OF(d).items():
+        r = ref[c0 * nn:c1 * nn]
+        out[k] = float(f"{float(torch.linalg.norm(got[c0 * nn:c1 * nn] - r) / torch.linalg.norm(r)):.3e}")
+    return out
+
+
+def step_stats(infos):
+    return {"nl_iters": [i.nl_iters for i in infos],
+            "gmres_iters_ns": [i.gmres_iters_ns for i in infos],
+            "gmres_iters_ac": [i.gmres_iters_ac for i in infos],
+            "gmres_iters_b": [i.gmres_iters_b for i in infos],
+            "worst_rel_res": max(i.worst_rel_res for i in infos),
+            "stalled_solves": sum(i.stalled_solves for i in infos)}
+
+
 def run_gpu(args):
     import torch
     from paper_2402_10348_gb300 import fsi
@@ -620,17 +676,22 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=dev)
     wl = cavity64()
     d = wl.desc
+    measured = fsi.fsi_probe_peaks()  # FMA rates and bandwidths of this GPU, before the run
     mesh = fsi.fsi_create_mesh(d, device=local)
     stream = torch.cuda.current_stream()
     fsi.fsi_set_stream(mesh, stream)
-    prec = fsi.FSI_PREC_FP32_IR if args.precision == "fp32ir" else fsi.FSI_PREC_FP64
-    solve = fsi.solve_opts(m=args.restart, rtol=1e-8, max_iter=3000, precision=prec, ir_inner_rtol=args.ir_inner_rtol,
-                           ir_max=30)
+    f64 = args.precision == "fp64"
+    prec = fsi.FSI_PREC_FP64 if f64 else fsi.FSI_PREC_FP32_IR
 
+    def opts(p):
+        return fsi.solve_opts(m=args.restart, rtol=1e-8, max_iter=6000, precision=p,
+                              ir_inner_rtol=args.ir_inner_rtol, ir_max=30)
+
+    solve = opts(prec)
     x, xn, xdn = initial_state(fsi, mesh, wl, torch, dev)
 
-    def step(opts=solve):
-        return fsi.fsi_step(mesh, x, xn, xdn, k_max=wl.k_max, nl_tol=5e-4, solve=opts)
+    def step(o=solve):
+        return fsi.fsi_step(mesh, x, xn, xdn, k_max=wl.k_max, nl_tol=5e-4, solve=o)
 
     # the learned preconditioner of the NS block: training pairs are harvested from the
     # (untimed) Jacobi warm-up steps
@@ -640,14 +701,18 @@ def run_gpu(args):
         pc = fsi.fsi_pc_create(mesh, n_pairs_cap=512, linear=True, modulate=True)
         fsi.fsi_pc_set_weights(pc, he_normal_weights(pc.fan, 3))
         fsi.fsi_set_pc(mesh, pc)
-        harvest = fsi.solve_opts(m=args.restart, rtol=1e-8, max_iter=3000, precision=prec,
-                                 ir_inner_rtol=args.ir_inner_rtol,
-                                 ir_max=30)
+        harvest = opts(prec)
         harvest.flags |= fsi.FSI_HARVEST
     for _ in range(args.warmup):
         step(harvest if pc is not None else solve)
     torch.cuda.synchronize()
     snapshot = (x.clone(), xn.clone(), xdn.clone())
+
+    def restore():
+        for a, b in zip((x, xn, xdn), snapshot):
+            a.copy_(b)
+        torch.cuda.synchronize()
+
     clocks = Clocks(local)
     clocks.start()
     if world > 1:
@@ -670,9 +735,7 @@ def run_gpu(args):
     # events (the library's profiler): per-class launch counts and device times.  The
     # solver is deterministic, so the replay runs the timed region's launches; the
     # events cost host time per launch and are kept out of the timed region itself.
-    for a, b in zip((x, xn, xdn), snapshot):
-        a.copy_(b)
-    torch.cuda.synchronize()
+    restore()
     fsi.fsi_profile(mesh, True)
     r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     r0.record(stream)
@@ -695,14 +758,36 @@ def run_gpu(args):
 
     # dominant kernel class (largest summed event time) and its roofline; the
     # dominant operator kernel is reported beside it
-    pk = peaks()
+    pk = peaks(measured)
     dom = max(prof.items(), key=lambda kv: kv[1][1])
-    roof = roofline(dom[0], *dom[1], d, pk, basis_f64=prec == fsi.FSI_PREC_FP64)
+    roof = roofline(dom[0], *dom[1], d, pk, basis_f64=f64)
     ops = {k: v for k, v in prof.items() if flops_per_element(k, d.n_solid) > 0 and v[0] > 0}
     roof_op = None
     if ops:
         oname, ov = max(ops.items(), key=lambda kv: kv[1][1])
-        roof_op = roofline(oname, *ov, d, pk, basis_f64=prec == fsi.FSI_PREC_FP64)
+        roof_op = roofline(oname, *ov, d, pk, basis_f64=f64)
+
+    # the other precision from the same state: float32 operators inside float64
+    # refinement against the float64 headline (or the reverse), same steps
+    other = None
+    if rank == 0 and not args.no_other:
+        oprec = fsi.FSI_PREC_FP32_IR if f64 else fsi.FSI_PREC_FP64
+        restore()
+        oo = opts(oprec)
+        step(oo)  # first use allocates the float32 staging
+        restore()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        oinfos = [step(oo) for _ in range(args.steps)]
+        q1.record(stream)
+        torch.cuda.synchronize()
+        oms = q0.elapsed_time(q1)
+        odof = sum(i.dof_applied for i in oinfos)
+        other = {"precision": "fp32ir" if f64 else "fp64",
+                 "value": round(odof / (oms / 1e3) / 1e9, 5), "unit": UNIT,
+                 "s_per_timestep": round(oms / args.steps / 1e3, 5),
+                 "step_stats": step_stats(oinfos),
+                 ("error_vs_fp64" if f64 else "error_vs_fp32ir"): field_errors(d, xn, final[1])}
 
     learned = None
     if pc is not None:
@@ -710,46 +795,54 @@ def run_gpu(args):
         learned["jacobi_s_per_timestep"] = round(ms / args.steps / 1e3, 5)
         learned["jacobi_ns_iters"] = [i.gmres_iters_ns for i in infos]
         learned["jacobi_nl_iters"] = [i.nl_iters for i in infos]
-        learned["jacobi_max_ratio"] = [i.max_ratio for i in infos]
+        learned["jacobi_worst_rel_res"] = max(i.worst_rel_res for i in infos)
+        learned["faster_than_jacobi"] = learned["s_per_timestep"] < learned["jacobi_s_per_timestep"]
 
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(fsi, mesh, wl, torch, dev, stream, step_fn=lambda xs: fsi.fsi_step(
             mesh, *xs, k_max=wl.k_max, nl_tol=5e-4, solve=solve), steps=max(1, min(args.steps, 2)), world=world)
+    del mesh, pc
+    torch.cuda.empty_cache()
+    shipice_ops = None
+    if rank == 0 and not args.no_operators:
+        from workloads import shipice
+        shipice_ops = operator_rates_of(shipice(), fsi, torch, dev, reps=2)
 
     line = {
         "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if prec == fsi.FSI_PREC_FP32_IR else "f64",
-        "precision": ("float32 operator applies and float32 Arnoldi basis inside float64 iterative "
-                      "refinement; float64 residuals, reductions, Hessenberg and Givens"
-                      if prec == fsi.FSI_PREC_FP32_IR else "float64 throughout"),
+        "dtype": "f64" if f64 else "f32",
+        "precision": ("float64 throughout (operators, Arnoldi basis, reductions, Hessenberg and Givens)" if f64 else
+                      "float32 operator applies and float32 Arnoldi basis inside float64 iterative "
+                      "refinement; float64 residuals, reductions, Hessenberg and Givens"),
         "data": "synthetic (seeded icosphere surface, initial phases by the grid-cell method)",
         "config": {"workload": WORKLOAD, "nodes": d.nn, "dof_per_node": d.ncomp, "dt": d.dt,
-                   "nl_iters_max": wl.k_max, "gmres": f"Jacobi GMRES({args.restart}) rtol 1e-8, stop on stagnation"
-                   + (f"; inner solves to {args.ir_inner_rtol:g}" if prec == fsi.FSI_PREC_FP32_IR else ""),
-                   "l2": ("inputs larger than L2: a time step streams the 64^3 state, the float64 "
-                          "refinement vectors and the (m+1) x 1.1M Krylov basis of the NS block "
-                          f"({(args.restart + 1) * 4 * d.nn * (4 if prec == fsi.FSI_PREC_FP32_IR else 8) / 1e6:.0f}"
-                          " MB) every restart cycle, against a 129 MB L2"),
+                   "nl_iters_max": wl.k_max,
+                   "gmres": f"Jacobi GMRES({args.restart}) rtol 1e-8 (NS block of the enclosed cavity: the pin "
+                            "node keeps its continuity equation, pressure shifted to p = 0 there after the solve)"
+                   + (f"; inner solves to {args.ir_inner_rtol:g}" if not f64 else ""),
+                   "l2": ("inputs larger than L2: a time step streams the 64^3 state, the quadrature-point "
+                          "coefficients of the NS product "
+                          f"({d.ne * 8 * 44 * (8 if f64 else 4) / 1e6:.0f} MB) and the (m+1) x 1.1M Krylov basis "
+                          f"({(args.restart + 1) * 4 * d.nn * (8 if f64 else 4) / 1e6:.0f} MB) every restart cycle, "
+                          "against a 129 MB L2"),
                    "parallelism": f"replicas x{world}"},
         "s_per_timestep": round(ms / args.steps / 1e3, 5),
-        "step_stats": {"nl_iters": [i.nl_iters for i in infos],
-                       "gmres_iters_ns": [i.gmres_iters_ns for i in infos],
-                       "gmres_iters_ac": [i.gmres_iters_ac for i in infos],
-                       "gmres_iters_b": [i.gmres_iters_b for i in infos],
-                       "worst_rel_res": max(i.worst_rel_res for i in infos),
-                       "stalled_solves": [i.stalled_solves for i in infos]},
+        "step_stats": step_stats(infos),
         "gpu_launches": launches,
         "profiled_replay": profiled,
         "kernel_ms": {k: [v[0], round(v[1], 3)] for k, v in prof.items() if v[0] > 0},
         "operator_gdofs": operator_rates({k: (v[0], v[1]) for k, v in prof.items()}, d.nn),
         "roofline": roof,
         "roofline_operator": roof_op,
+        "measured_peaks": {k: round(v, 2) for k, v in measured.items()},
         "clocks": clk,
         "e2e": e2e,
+        "other_precision": other,
         "learned_pc": learned,
+        "shipice_operators": shipice_ops,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
@@ -849,26 +942,63 @@ def _oracle_sample(nz_slab: int, seed: int = 0):
     return d, (x1, xn, xdn)
 
 
-def cpu_baseline(budget_s: float = 12.0):
-    """The oracle's NS Jacobian-vector product (the dominant apply of a step) on a
-    64 x 64 x 16-element slab of the workload, repeated for about budget_s."""
-    from oracle import ns
+def _cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(budget_s: float = 3.0):
+    """The oracle on the host cores.  Per-apply rates of its NS, AC and B products on a
+    64 x 64 x 16-element slab of the workload (about budget_s each; `value` is the NS
+    product's, the dominant apply of a step), and the wall time of one nonlinear
+    iteration of the 16^3 cavity's first time step (NS, both AC and the B block solved
+    by the oracle's Jacobi GMRES(30) to 1e-8, the NS block without the pin row plus the
+    pressure shift)."""
+    from oracle import blocks, step
     from oracle.fields import Problem, State
+    from oracle.gridcell import apply_rules, signed_distance_phi
+    from workloads import cavity16
     d, (x1, xn, xdn) = _oracle_sample(16)
     pb, st = Problem(d), State(x1, xn, xdn)
-    dx = np.random.default_rng(1).normal(size=(4, d.nn))
+    rng = np.random.default_rng(1)
+    coeffs = {"gamma": {i: 0.5 for i in range(d.n_phase)}, "beta": {i: 0.1 for i in range(d.n_phase)}}
+    rates = {}
+    for name, blk, ncomp in (("ns", "ns", 4), ("ac", ("ac", 1), 1), ("b", ("b", 0), 6)):
+        dx = rng.normal(size=ncomp * d.nn)
+        t0 = time.perf_counter()
+        reps = 0
+        while True:
+            blocks.jvp(pb, st, blk, dx, coeffs)
+            reps += 1
+            if time.perf_counter() - t0 > budget_s:
+                break
+        dt = time.perf_counter() - t0
+        rates[name + "_jvp"] = {"gdofs": round(reps * ncomp * d.nn / dt / 1e9, 7), "applies": reps,
+                                "s_per_apply": round(dt / reps, 3)}
+    wl = cavity16()
+    dd = wl.desc
+    phi, _ = signed_distance_phi(dd, wl.surfaces[0], dd.eps, wl.grid_cells)
+    x = np.zeros((dd.ncomp, dd.nn))
+    x[4:4 + dd.n_phase] = apply_rules(dd, {0: phi}, wl.rules, dd.eps)
+    x[4 + dd.n_phase: 4 + dd.n_phase + 3] = 1.0
+    s16 = State(x.copy(), x.copy(), np.zeros_like(x))
     t0 = time.perf_counter()
-    reps = 0
-    while True:
-        ns.ns_jvp(pb, st, dx)
-        reps += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": round(reps * 4 * d.nn / dt / 1e9, 7), "unit": UNIT, "cores": os.cpu_count(),
+    info = step.time_step(Problem(dd), s16, step.StepOptions(k_max=1, rtol=1e-8, max_iter=3000, pin_shift=True))
+    it_s = time.perf_counter() - t0
+    return {"value": rates["ns_jvp"]["gdofs"], "unit": UNIT, "cores": os.cpu_count(), "cpu_model": _cpu_model(),
             "kind": "oracle",
-            "sample": f"{reps} float64 NS Jacobian-vector products on a 64x64x16-element slab of the 64^3 cavity "
-                      f"({4 * d.nn} DoF each, numpy; BLAS may use all {os.cpu_count()} cores), {dt:.1f} s"}
+            "sample": f"float64 numpy oracle (BLAS may use all {os.cpu_count()} cores): NS, AC and B products on "
+                      f"a 64x64x16-element slab of the 64^3 cavity (about {budget_s:.0f} s each; value = NS); one "
+                      "nonlinear iteration of the 16^3 cavity's first step",
+            "per_apply": rates,
+            "cavity16_one_nonlinear_iteration_s": round(it_s, 2),
+            "cavity16_gmres_iters": {k: v[0] for k, v in info.gmres_iters.items()}}
 
 
 def run_reference(args):
