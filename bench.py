@@ -944,6 +944,13 @@ def _oracle_sample(nz_slab: int, seed: int = 0):
 
 def _cpu_model() -> str:
     try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
         for line in open("/proc/cpuinfo"):
             if line.lower().startswith(("model name", "cpu part")):
                 return line.split(":", 1)[1].strip()

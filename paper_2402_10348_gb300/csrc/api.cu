@@ -372,6 +372,7 @@ int fsi_destroy_mesh(fsi_mesh* m) {
   cudaFree(m->Z);
   cudaFree(m->cq64);
   cudaFree(m->cq32);
+  cudaFree(m->ke64);
   if (m->kry_est) cudaFreeHost(m->kry_est);
   for (cudaEvent_t e : m->kry_ev) cudaEventDestroy(e);
   for (cudaEvent_t e : m->prof.ev) cudaEventDestroy(e);

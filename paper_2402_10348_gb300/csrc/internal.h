@@ -72,6 +72,13 @@ struct fsi_mesh {
   int64_t cq_len = 0;                // allocated coefficients (each array)
   int64_t cq_gen = -1;               // stage_gen of the last build
   unsigned cq_flags = 0;             // FSI_ELASTIC_AUG of the last build
+  // float64 element matrices of the NS product (NSEOp), built from the coefficients once
+  // a state has taken NSE_AFTER float64 products
+  double* ke64 = nullptr;
+  int64_t ke_len = 0;
+  int64_t ke_gen = -1;               // cq_gen they were built from
+  int64_t f64_gen = -1, f64_count = 0;  // float64 NS products applied at coefficient build f64_gen
+  int64_t cq_builds = 0;             // coefficient builds so far (a new build invalidates ke64)
   const double* staged_xa = nullptr; // the x^{n+alpha} array in use
   // coefficients
   double gamma[fsi::MAXP] = {0};
@@ -146,6 +153,9 @@ template <typename T>
 int launch_ns(fsi_mesh* m, int mode, const double* dx, double* y, unsigned flags);
 // NS product from the quadrature-point coefficients (built first when stale)
 int ns_build(fsi_mesh* m, unsigned flags);  // ops_f64.cu
+// float64 NS product through element matrices (built first when stale), ops_f64.cu
+int launch_nse(fsi_mesh* m, const double* dx, double* y, unsigned flags);
+constexpr int NSE_AFTER = 8;  // float64 products on one coefficient build before the matrices pay
 template <typename T>
 int launch_nsq(fsi_mesh* m, const double* dx, double* y, unsigned flags);
 template <typename T>

@@ -464,6 +464,75 @@ struct NSBuildOp {
   __device__ __forceinline__ void finish(const NodeCtx&, const T (&)[NC], Red&) const {}
 };
 
+// The product's arithmetic at one quadrature point, from the interpolated increment
+// (dv, its gradient gd[k][j] = d_j dv_k, dp and its gradient dgp) and the point's
+// coefficients k (`stride` apart): accumulates the unweighted contributions of the four
+// equations into c[eq][corner].
+template <typename T, class Coef>
+__device__ __forceinline__ void nsq_point(const Coef& k, bool elastic, const T (&dv)[3], const T (&gd)[3][3], T dp,
+                                          const T (&dgp)[3], T al, T cmass, const QW<T>& w, T rhx, T rhy, T rhz,
+                                          T (&c)[4][8]) {
+  const T rho = k(0), mu = k(1);
+  const T v[3] = {k(2), k(3), k(4)};
+  const T Rm[3] = {k(14), k(15), k(16)};
+  const T tau_m = k(17), tc_rho = k(18), tm_rho = k(19);
+  T dL[3][3], vt[3], dRm[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    vt[a] = al * dv[a];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) dL[a][b] = al * gd[a][b];
+  }
+#pragma unroll
+  for (int kk = 0; kk < 3; ++kk) {
+    const T dacc = cmass * dv[kk] + vt[0] * k(5 + 3 * kk) + vt[1] * k(6 + 3 * kk) + vt[2] * k(7 + 3 * kk) +
+                   v[0] * dL[kk][0] + v[1] * dL[kk][1] + v[2] * dL[kk][2];
+    dRm[kk] = rho * dacc;
+  }
+  T dE[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  if (elastic) {
+    T aB[6];
+#pragma unroll
+    for (int cc = 0; cc < 6; ++cc) aB[cc] = k(20 + cc);
+#pragma unroll
+    for (int cc = 0; cc < 6; ++cc) {
+      const int kk = sym_k(cc), l = sym_l(cc);
+      T pkl = T(0), plk = T(0);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        pkl += dL[kk][m] * aB[sym_idx(m, l)];
+        plk += dL[l][m] * aB[sym_idx(m, kk)];
+      }
+      const T dd = vt[0] * k(26 + 3 * cc) + vt[1] * k(27 + 3 * cc) + vt[2] * k(28 + 3 * cc);
+      dE[cc] = pkl + plk - dd;
+    }
+  }
+  const T dRc = dL[0][0] + dL[1][1] + dL[2][2];
+#pragma unroll
+  for (int kk = 0; kk < 3; ++kk) {
+    const T sk = tau_m * (dRm[kk] + dgp[kk]);
+    const T rk = tau_m * Rm[kk];
+    T gk[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      T sj = dE[sym_idx(kk, j)] + mu * (dL[kk][j] + dL[j][kk]) + vt[j] * rk + v[j] * sk;
+      if (j == kk) sj += -dp + tc_rho * dRc;
+      gk[j] = sj;
+    }
+    scatter_vg(c[kk], w, dRm[kk], gk[0], gk[1], gk[2], rhx, rhy, rhz);
+  }
+  scatter_vg(c[3], w, dRc, tm_rho * (dRm[0] + dgp[0]), tm_rho * (dRm[1] + dgp[1]), tm_rho * (dRm[2] + dgp[2]), rhx,
+             rhy, rhz);
+}
+
+// Coefficient accessor over a strided plane layout (loads through the read-only path).
+template <typename T>
+struct CoefRef {
+  const T* p;
+  int64_t s;
+  __device__ __forceinline__ T operator()(int i) const { return __ldg(p + i * s); }
+};
+
 // NS product from the coefficients: fields dv(3), dp of the increment.  The element
 // contributions are accumulated without the quadrature weight W, applied per node.
 template <typename TT>
@@ -491,75 +560,23 @@ struct NSQOp {
     const T rhx = T(rh[0]), rhy = T(rh[1]), rhz = T(rh[2]);
     const T al = T(alpha), cmass = T(cm);
     const T* e0 = cq + (int64_t)ec.ez * 8 * NCQ * nxyp + (int64_t)ec.ey * nxp + ec.ex;
-    const int64_t s = nxyp;
     T u[8];
 #pragma unroll 1
     for (int q = 0; q < 8; ++q) {
       QW<T> w;
       w.set(q);
-      const T* k = e0 + (int64_t)q * NCQ * s;
-      T kf[NCQ_FLUID];
-#pragma unroll
-      for (int i = 0; i < NCQ_FLUID; ++i) kf[i] = __ldg(k + i * s);
-      const T rho = kf[0], mu = kf[1];
-      const T v[3] = {kf[2], kf[3], kf[4]};
-      const T Rm[3] = {kf[14], kf[15], kf[16]};
-      const T tau_m = kf[17], tc_rho = kf[18], tm_rho = kf[19];
-      T dv[3], dL[3][3];
+      T dv[3], gd[3][3];
 #pragma unroll
       for (int kk = 0; kk < 3; ++kk) {
         cr.get(kk, u);
         const VG<T> r = interp_vg(u, w, rhx, rhy, rhz);
-        dv[kk] = r.v; dL[kk][0] = al * r.gx; dL[kk][1] = al * r.gy; dL[kk][2] = al * r.gz;
+        dv[kk] = r.v; gd[kk][0] = r.gx; gd[kk][1] = r.gy; gd[kk][2] = r.gz;
       }
       cr.get(3, u);
       const VG<T> dpr = interp_vg(u, w, rhx, rhy, rhz);
       const T dgp[3] = {dpr.gx, dpr.gy, dpr.gz};
-      T vt[3], dRm[3];
-#pragma unroll
-      for (int kk = 0; kk < 3; ++kk) vt[kk] = al * dv[kk];
-#pragma unroll
-      for (int kk = 0; kk < 3; ++kk) {
-        const T* L = kf + 5 + 3 * kk;
-        const T dacc = cmass * dv[kk] + vt[0] * L[0] + vt[1] * L[1] + vt[2] * L[2] + v[0] * dL[kk][0] +
-                       v[1] * dL[kk][1] + v[2] * dL[kk][2];
-        dRm[kk] = rho * dacc;
-      }
-      T dE[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-      if (elastic) {
-        T aB[6];
-#pragma unroll
-        for (int cc = 0; cc < 6; ++cc) aB[cc] = __ldg(k + (20 + cc) * s);
-#pragma unroll
-        for (int cc = 0; cc < 6; ++cc) {
-          const int kk = sym_k(cc), l = sym_l(cc);
-          T pkl = T(0), plk = T(0);
-#pragma unroll
-          for (int m = 0; m < 3; ++m) {
-            pkl += dL[kk][m] * aB[sym_idx(m, l)];
-            plk += dL[l][m] * aB[sym_idx(m, kk)];
-          }
-          const T dd = vt[0] * __ldg(k + (26 + 3 * cc) * s) + vt[1] * __ldg(k + (27 + 3 * cc) * s) +
-                       vt[2] * __ldg(k + (28 + 3 * cc) * s);
-          dE[cc] = pkl + plk - dd;
-        }
-      }
-      const T dRc = dL[0][0] + dL[1][1] + dL[2][2];
-#pragma unroll
-      for (int kk = 0; kk < 3; ++kk) {
-        const T sk = tau_m * (dRm[kk] + dgp[kk]);
-        const T rk = tau_m * Rm[kk];
-        T gk[3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          T sj = dE[sym_idx(kk, j)] + mu * (dL[kk][j] + dL[j][kk]) + vt[j] * rk + v[j] * sk;
-          if (j == kk) sj += -dpr.v + tc_rho * dRc;
-          gk[j] = sj;
-        }
-        scatter_vg(c[kk], w, dRm[kk], gk[0], gk[1], gk[2], rhx, rhy, rhz);
-      }
-      scatter_vg(c[3], w, dRc, tm_rho * (dRm[0] + dgp[0]), tm_rho * (dRm[1] + dgp[1]), tm_rho * (dRm[2] + dgp[2]),
-                 rhx, rhy, rhz);
+      nsq_point<T>(CoefRef<T>{e0 + (int64_t)q * NCQ * nxyp, nxyp}, elastic != 0, dv, gd, dpr.v, dgp, al, cmass, w,
+                   rhx, rhy, rhz, c);
     }
   }
 
@@ -574,6 +591,67 @@ struct NSQOp {
       } else {
         *y = W * (double)acc[k];
       }
+    }
+  }
+};
+
+// ------------------------------------------- float64 NS product from element matrices
+// GB300 issues float64 FMAs at 1/64 of the float32 rate, so a float64 solve that
+// applies the product hundreds of times on one state stores each element's 32 x 32
+// matrix (rows and columns ordered field-major: 8 corners of dv_x, dv_y, dv_z, dp) once
+// and applies it with 1024 FMAs per element, against about 2400 for the coefficient
+// form.  Layout: K[((ez * 1024 + i * 32 + j) * nxyp + ey * nxp + ex], unweighted (W
+// per node as above).  Column j is the coefficient product of the unit increment j, so
+// both forms are the same operator up to summation order.
+constexpr int NKE = 32 * 32;
+
+// Product: fields dv(3), dp of the increment (float64).
+struct NSEOp {
+  using T = double;
+  static constexpr int NC = 4;
+  static constexpr int MINB = 1;
+  Fields F;
+  int nf;
+  const double* K;
+  int nxp;
+  int64_t nxyp;
+  double W;
+  OutDesc out;
+  int64_t nn_;
+
+  __device__ __forceinline__ const T* fptr(int f) const { return field_ptr<T>(F, f); }
+  using Red = NoRed;
+  __device__ __forceinline__ void begin_cta(Red&) const {}
+  __device__ __forceinline__ void end_cta(Red&) const {}
+
+  __device__ void element(const Corners<T>& cr, const ElemCtx& ec, T (&c)[NC][8], Red&) const {
+    T x[32];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      T u[8];
+      cr.get(f, u);
+#pragma unroll
+      for (int a = 0; a < 8; ++a) x[8 * f + a] = u[a];
+    }
+    const double* k = K + (int64_t)ec.ez * NKE * nxyp + (int64_t)ec.ey * nxp + ec.ex;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const double* row = k + (int64_t)i * 32 * nxyp;
+      T acc = 0.0;
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) acc += __ldg(row + jj * nxyp) * x[jj];
+      c[i >> 3][i & 7] = acc;
+    }
+  }
+
+  __device__ __forceinline__ void finish(const NodeCtx& nc, const T (&acc)[NC], Red&) const {
+    const int64_t nn = nn_;
+    const uint8_t m = out.mask ? out.mask[nc.n] : 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      double* y = out.y + (int64_t)k * nn + nc.n;
+      if (((m >> k) & 1) && (k < 3 || out.pin)) *y = out.dx[(int64_t)k * nn + nc.n];
+      else *y = W * acc[k];
     }
   }
 };

@@ -63,7 +63,92 @@ int ns_build(fsi_mesh* m, unsigned flags) {
   } while (s0 < ns);
   m->cq_gen = m->stage_gen;
   m->cq_flags = flags & FSI_ELASTIC_AUG;
+  ++m->cq_builds;
   return FSI_OK;
+}
+
+// Build: one thread per (element, column); threadIdx.x runs along x (coalesced
+// coefficient loads and matrix stores), threadIdx.y and blockIdx.z over columns.
+__global__ void __launch_bounds__(256) nse_build_kernel(const double* __restrict__ cq, double* __restrict__ K,
+                                                        int nx, int ny, int nz, int nxp, int64_t nxyp, int elastic,
+                                                        double alpha, double cm, double rhx, double rhy, double rhz) {
+  const int ex = blockIdx.x * 32 + threadIdx.x;
+  const int eyz = blockIdx.y;
+  const int ey = eyz % ny, ez = eyz / ny;
+  const int j = blockIdx.z * 8 + threadIdx.y;  // column: field j / 8, corner j % 8
+  if (ex >= nx || ez >= nz) return;
+  const int f = j >> 3, a = j & 7;
+  const int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
+  const double* e0 = cq + (int64_t)ez * 8 * NCQ * nxyp + (int64_t)ey * nxp + ex;
+  double c[4][8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) c[q][b] = 0.0;
+#pragma unroll 1
+  for (int q = 0; q < 8; ++q) {
+    QW<double> w;
+    w.set(q);
+    // the unit increment at corner a, interpolated: N_a and grad N_a at the point
+    const double N = w.wx[ax] * w.wy[ay] * w.wz[az];
+    const double g[3] = {(ax ? 1.0 : -1.0) * rhx * w.wy[ay] * w.wz[az], (ay ? 1.0 : -1.0) * rhy * w.wx[ax] * w.wz[az],
+                         (az ? 1.0 : -1.0) * rhz * w.wx[ax] * w.wy[ay]};
+    double dv[3], gd[3][3], dgp[3];
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) {
+      const bool on = f == kk;
+      dv[kk] = on ? N : 0.0;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) gd[kk][b] = on ? g[b] : 0.0;
+      dgp[kk] = f == 3 ? g[kk] : 0.0;
+    }
+    const double dp = f == 3 ? N : 0.0;
+    nsq_point<double>(CoefRef<double>{e0 + (int64_t)q * NCQ * nxyp, nxyp}, elastic != 0, dv, gd, dp, dgp, alpha, cm,
+                      w, rhx, rhy, rhz, c);
+  }
+  double* out = K + ((int64_t)ez * NKE + j) * nxyp + (int64_t)ey * nxp + ex;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) out[(int64_t)i * 32 * nxyp] = c[i >> 3][i & 7];
+}
+
+int launch_nse(fsi_mesh* m, const double* dx, double* y, unsigned flags) {
+  const int nxp = cq_pitch(m);
+  const int64_t nxyp = (int64_t)nxp * m->g.ny;
+  const int elastic = ((flags & FSI_ELASTIC_AUG) && m->ns > 0) ? 1 : 0;
+  if (m->ke_gen != m->cq_builds) {
+    const int64_t len = (int64_t)m->g.nz * NKE * nxyp;
+    if (m->ke_len < len) {
+      cudaFree(m->ke64);
+      m->ke64 = nullptr;
+      m->ke_len = 0;
+      FSI_CUDA(cudaMalloc(&m->ke64, sizeof(double) * (size_t)len));
+      m->ke_len = len;
+    }
+    const dim3 grid((m->g.nx + 31) / 32, (unsigned)((int64_t)m->g.ny * m->g.nz), 4);
+    FSI_LAUNCH(m, P_NS_BUILD,
+               nse_build_kernel<<<grid, dim3(32, 8), 0, m->stream>>>(m->cq64, m->ke64, m->g.nx, m->g.ny, m->g.nz, nxp,
+                                                                     nxyp, elastic, m->P.alpha, m->P.c_mass,
+                                                                     1.0 / m->g.hx, 1.0 / m->g.hy, 1.0 / m->g.hz));
+    m->ke_gen = m->cq_builds;
+  }
+  NSEOp op;
+  memset(&op, 0, sizeof(op));
+  const int64_t nn = m->nn;
+  for (int k = 0; k < 4; ++k) put<double>(op.F, k, dx + k * nn);
+  op.nf = 4;
+  op.K = m->ke64;
+  op.nxp = nxp;
+  op.nxyp = nxyp;
+  op.W = m->g.hx * m->g.hy * m->g.hz / 8.0;
+  op.out.y = y;
+  op.out.dx = dx;
+  op.out.mask = m->mask;
+  op.out.dirichlet = 1;
+  op.out.pin = m->pin_active;
+  op.nn_ = nn;
+  const int64_t ne = (int64_t)m->g.nx * m->g.ny * m->g.nz;
+  prof_bytes(m, P_NS_JVP64, (double)ne * NKE * 8.0 + (double)nn * (4.0 * 8.0 + 32.0 + 1.0));
+  return run_tile(m, op, P_NS_JVP64);
 }
 template int launch_ac<double>(fsi_mesh*, int, int, const double*, double*);
 template int launch_b<double>(fsi_mesh*, int, int, const double*, double*);

@@ -189,6 +189,14 @@ int launch_nsq(fsi_mesh* m, const double* dx, double* y, unsigned flags) {
   if (m->cq_gen != m->stage_gen || m->cq_flags != eflags || !m->cq64) {
     if (int rc = ns_build(m, flags)) return rc;
   }
+  if constexpr (sizeof(T) == 8) {
+    // a float64 solve on this state: after NSE_AFTER products switch to element matrices
+    if (m->f64_gen != m->cq_builds) {
+      m->f64_gen = m->cq_builds;
+      m->f64_count = 0;
+    }
+    if (++m->f64_count > NSE_AFTER) return launch_nse(m, dx, y, flags);
+  }
   NSQOp<T> op;
   memset(&op, 0, sizeof(op));
   const int64_t nn = m->nn;
