@@ -65,9 +65,11 @@ def parse():
     return p.parse_args()
 
 
-def run_solve_case():
-    """Forty Arnoldi steps of the NS block of the 64^3 cavity with the float32 operator:
-    the launch sequence the profiles under profiles/ were captured on."""
+def run_solve_case(precision: str = "fp32ir"):
+    """Forty Arnoldi steps of the NS block of the 64^3 cavity, float32 operator inside
+    float64 refinement (fp32ir: the coefficient product in float32) or float64 (the first
+    8 products from the coefficients, the rest through element matrices): the launch
+    sequences the profiles under profiles/ were captured on."""
     import torch
     from paper_2402_10348_gb300 import fsi
     from workloads import cavity64
@@ -80,11 +82,12 @@ def run_solve_case():
     g = torch.Generator(device=dev).manual_seed(0)
     rhs = torch.randn(4 * d.nn, dtype=torch.float64, device=dev, generator=g)
     sol = torch.zeros_like(rhs)
-    info = fsi.fsi_gmres(mesh, fsi.FSI_BLOCK_NS, x, xn, xdn, rhs, sol,
-                         fsi.solve_opts(m=64, rtol=1e-30, max_iter=40, precision=fsi.FSI_PREC_FP32_IR, ir_max=1,
-                                        ir_inner_rtol=1e-30), allow_noconv=True)
+    prec = fsi.FSI_PREC_FP32_IR if precision == "fp32ir" else fsi.FSI_PREC_FP64
+    o = fsi.solve_opts(m=64, rtol=1e-30, max_iter=40, precision=prec, ir_max=1, ir_inner_rtol=1e-30)
+    o.flags |= fsi.FSI_NO_STALL_STOP
+    info = fsi.fsi_gmres(mesh, fsi.FSI_BLOCK_NS, x, xn, xdn, rhs, sol, o, allow_noconv=True)
     torch.cuda.synchronize()
-    print(f"solve case: {info.iterations} iterations")
+    print(f"solve case ({precision}): {info.iterations} iterations")
 
 
 def pc_flops_per_forward(grids, fan):
@@ -505,11 +508,14 @@ class Clocks:
 # recomputation), counted from the arithmetic of the kernels' element functions;
 # multiply by the elements of one launch.
 def flops_per_element(kernel: str, n_solid: int) -> float:
-    """Per quadrature point: the NS product from frozen coefficients 486 + 114 with solids
+    """The float64 NS product through element matrices: 2 x 32 x 32 per element.  Per
+    quadrature point: the NS product from frozen coefficients 486 + 114 with solids
     (interpolation of dv, dp: 172; convective and mass terms 54; stresses 92; the
     elastic linearization 114; test-function scatter 166), its coefficient build
     635 + 167 per solid, NS residual 635 + 167 per solid, AC JVP 247, B JVP 892; 8
     points per element."""
+    if kernel == "ns_jvp_f64_em":
+        return 2.0 * 32 * 32  # the element matrix applied: 1024 FMAs per element
     per_qp = {"ns_jvp": 486 + (114 if n_solid > 0 else 0), "ns_coeffs": 635 + 167 * n_solid,
               "ns_residual": 635 + 167 * n_solid, "ac_jvp": 247, "b_jvp": 892}
     for k, v in per_qp.items():
@@ -1051,7 +1057,7 @@ def main():
     elif args.case == "diagnostics":
         run_diagnostics_case()
     elif args.case == "solve":
-        run_solve_case()
+        run_solve_case(args.precision if "--precision" in sys.argv else "fp32ir")
     else:
         run_gpu(args)
 

@@ -436,7 +436,7 @@ int fsi_batch_set_graph(fsi_batch* batch, int32_t use_graph);
  * launches.  Allocates and frees 4 GiB of device memory; synchronises the device. */
 int fsi_probe_peaks(double* fp32_tflops, double* fp64_tflops, double* read_gbs, double* copy_gbs);
 
-#define FSI_PROF_CLASSES 24
+#define FSI_PROF_CLASSES 25
 typedef struct {
   char name[24];
   int64_t launches;

@@ -147,8 +147,8 @@ int launch_nse(fsi_mesh* m, const double* dx, double* y, unsigned flags) {
   op.out.pin = m->pin_active;
   op.nn_ = nn;
   const int64_t ne = (int64_t)m->g.nx * m->g.ny * m->g.nz;
-  prof_bytes(m, P_NS_JVP64, (double)ne * NKE * 8.0 + (double)nn * (4.0 * 8.0 + 32.0 + 1.0));
-  return run_tile(m, op, P_NS_JVP64);
+  prof_bytes(m, P_NS_JVP64E, (double)ne * NKE * 8.0 + (double)nn * (4.0 * 8.0 + 32.0 + 1.0));
+  return run_tile(m, op, P_NS_JVP64E);
 }
 template int launch_ac<double>(fsi_mesh*, int, int, const double*, double*);
 template int launch_b<double>(fsi_mesh*, int, int, const double*, double*);
