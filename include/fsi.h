@@ -423,6 +423,24 @@ int fsi_batch_autotune(fsi_batch* batch, const fsi_state* states, uint32_t flags
                        int32_t* grid_mult, double* best_us);
 /* 0: launch the restart cycles directly instead of through the captured graph */
 int fsi_batch_set_graph(fsi_batch* batch, int32_t use_graph);
+/* As fsi_batch_create with a block per entry: entry i solves block blocks[i] of
+ * meshes[i]; a mesh may appear in several entries (e.g. every phase of it).  Entries
+ * need one operator type: all NS, all AC or all B blocks. */
+int fsi_batch_create_blocks(fsi_mesh* const* meshes, const int32_t* blocks, int32_t n, int32_t m,
+                            fsi_batch** out);
+
+/* Batched partitioned time steps (Section 2.5) of n independent instances (one device,
+ * one stream): each nonlinear iteration solves the NS blocks of all live instances in
+ * one batched GMRES, the Allen-Cahn blocks of all phases of all instances in one (the
+ * phases' equations do not depend on each other), and the B blocks of all solids in
+ * one; the pressure of enclosed domains is fixed as in fsi_step.  An instance stops
+ * iterating once all its blocks meet nl_tol (unless fixed_iters).  states: n host
+ * structs of device pointers, advanced in place; infos: n results.  opts.solve.m is the
+ * stepper's restart length; Jacobi or no preconditioner.  Synchronises. */
+typedef struct fsi_batch_stepper fsi_batch_stepper;
+int fsi_batch_stepper_create(fsi_mesh* const* meshes, int32_t n, int32_t m, fsi_batch_stepper** out);
+int fsi_batch_stepper_destroy(fsi_batch_stepper* stepper);
+int fsi_batch_step(fsi_batch_stepper* stepper, fsi_state* states, const fsi_step_opts* opts, fsi_step_info* infos);
 
 /* --------------------------------------------------------------- measurement
  * (no counterpart in the paper: timing support for the benchmark)

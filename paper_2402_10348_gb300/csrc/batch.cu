@@ -66,10 +66,12 @@ struct OpSet {
 }  // namespace fsi
 
 struct fsi_batch {
-  std::vector<fsi_mesh*> meshes;
+  std::vector<fsi_mesh*> meshes;  // per entry (a mesh may appear once per block of it)
+  std::vector<int> blocks;        // per entry: the block id
   int n = 0;
   fsi::BlockInfo blk0{};
   int block = 0;
+  float* dx32_own = nullptr;      // float increments of all entries (concatenated like the block vectors)
   cudaStream_t stream = nullptr;
   std::vector<int64_t> off;  // [n + 1]
   int64_t ntot = 0;
@@ -526,14 +528,18 @@ int record_set(fsi_batch* b, OpSet* set, unsigned flags, const double* dx_base, 
   for (int i = 0; i < b->n; ++i) {
     fsi_mesh* m = b->meshes[i];
     BlockInfo bi;
-    int rc = block_info(m, b->block, &bi);
+    int rc = block_info(m, b->blocks[i], &bi);
     if (rc) return rc;
     m->rec = &rec;
+    // the entry's own float increment (a mesh with several entries must not share one)
+    float* mesh_dx32 = m->dx32;
+    m->dx32 = b->dx32_own + b->off[i];
     const double* dx = dx_base + b->off[i];
     double* y = y_base + b->off[i];
     if (bi.kind == 0) rc = f32 ? launch_ns<float>(m, 1, dx, y, flags) : launch_ns<double>(m, 1, dx, y, flags);
     else if (bi.kind == 1) rc = f32 ? launch_ac<float>(m, 1, bi.index, dx, y) : launch_ac<double>(m, 1, bi.index, dx, y);
     else rc = f32 ? launch_b<float>(m, 1, bi.index, dx, y) : launch_b<double>(m, 1, bi.index, dx, y);
+    m->dx32 = mesh_dx32;
     m->rec = nullptr;
     if (rc) return rc;
   }
@@ -716,11 +722,13 @@ int stage_all(fsi_batch* b, const fsi_state* states, bool f32) {
 }
 
 int ensure_dx32(fsi_batch* b) {
+  if (!b->dx32_own) FSI_CUDA(cudaMalloc(&b->dx32_own, sizeof(float) * (size_t)std::max<int64_t>(b->ntot, 4)));
   std::vector<float*> p(b->n);
   for (int i = 0; i < b->n; ++i) {
     fsi_mesh* m = b->meshes[i];
+    // the mesh's own copy is still needed by its single-mesh float32 launches
     if (!m->dx32) FSI_CUDA(cudaMalloc(&m->dx32, sizeof(float) * 6 * (size_t)m->nn));
-    p[i] = m->dx32;
+    p[i] = b->dx32_own + b->off[i];
   }
   FSI_CUDA(cudaMemcpy(b->dx32_dev, p.data(), sizeof(float*) * b->n, cudaMemcpyHostToDevice));
   return FSI_OK;
@@ -792,6 +800,7 @@ int fsi_batch_destroy(fsi_batch* b) {
   cudaFree(b->w), cudaFree(b->z), cudaFree(b->r), cudaFree(b->t), cudaFree(b->dinv), cudaFree(b->d);
   cudaFree(b->rin), cudaFree(b->rout), cudaFree(b->part), cudaFree(b->K), cudaFree(b->act), cudaFree(b->live);
   cudaFree(b->out_dev);
+  cudaFree(b->dx32_own);
   if (b->host_out) cudaFreeHost(b->host_out);
   if (b->host_live) cudaFreeHost(b->host_live);
   delete b;
@@ -799,7 +808,13 @@ int fsi_batch_destroy(fsi_batch* b) {
 }
 
 int fsi_batch_create(fsi_mesh* const* meshes, int32_t n, int32_t block, int32_t m, fsi_batch** out) {
-  if (!meshes || !out || n < 1) return set_error(FSI_EINVAL, "fsi_batch_create: bad arguments");
+  if (n < 1) return set_error(FSI_EINVAL, "fsi_batch_create: bad arguments");
+  std::vector<int32_t> blocks(n, block);
+  return fsi_batch_create_blocks(meshes, blocks.data(), n, m, out);
+}
+
+int fsi_batch_create_blocks(fsi_mesh* const* meshes, const int32_t* blocks, int32_t n, int32_t m, fsi_batch** out) {
+  if (!meshes || !blocks || !out || n < 1) return set_error(FSI_EINVAL, "fsi_batch_create: bad arguments");
   if (m < 1 || m > BMMAX) return set_error(FSI_EINVAL, "fsi_batch_create: restart length must be in 1..64");
   *out = nullptr;
   for (int i = 0; i < n; ++i) {
@@ -813,8 +828,9 @@ int fsi_batch_create(fsi_mesh* const* meshes, int32_t n, int32_t block, int32_t 
     return rc;
   };
   b->meshes.assign(meshes, meshes + n);
+  b->blocks.assign(blocks, blocks + n);
   b->n = n;
-  b->block = block;
+  b->block = blocks[0];
   b->stream = meshes[0]->stream;
   b->mm = m;
   b->M1 = m + 1;
@@ -824,7 +840,7 @@ int fsi_batch_create(fsi_mesh* const* meshes, int32_t n, int32_t block, int32_t 
   int64_t vtot = 0;
   for (int i = 0; i < n; ++i) {
     BlockInfo bi;
-    int rc = block_info(meshes[i], block, &bi);
+    int rc = block_info(meshes[i], blocks[i], &bi);
     if (rc) return fail(rc);
     if (i == 0) b->blk0 = bi;
     if (bi.kind != b->blk0.kind) return fail(set_error(FSI_EINVAL, "fsi_batch_create: block kinds differ"));
@@ -913,7 +929,7 @@ int fsi_batch_gmres(fsi_batch* b, const fsi_state* states, const double* rhs, do
   // Jacobi diagonal of the inner operator, one launch per instance (once per solve)
   for (int i = 0; i < nb; ++i) {
     BlockInfo bi;
-    if ((rc = block_info(b->meshes[i], b->block, &bi))) return rc;
+    if ((rc = block_info(b->meshes[i], b->blocks[i], &bi))) return rc;
     if (o->precond == FSI_PC_JACOBI) {
       if ((rc = op_diag(b->meshes[i], bi, b->dinv + b->off[i], f32 ? (base | FSI_FP32) : base))) return rc;
     } else {
@@ -1041,6 +1057,210 @@ int fsi_batch_autotune(fsi_batch* b, const fsi_state* states, uint32_t flags, in
 int fsi_batch_set_graph(fsi_batch* b, int32_t use_graph) {
   if (!b) return set_error(FSI_EINVAL, "fsi_batch_set_graph: null handle");
   b->use_graph = use_graph ? 1 : 0;
+  return FSI_OK;
+}
+
+}  // extern "C"
+
+// ================================================================ batched time steps
+// Partitioned time steps (Section 2.5) of many independent instances at once: every
+// block solve of a nonlinear iteration is one batched solve over all instances (NS),
+// over all (instance, phase) pairs (the Allen-Cahn blocks of different phases do not
+// depend on each other, so all N phases of all instances are one batch), and over all
+// (instance, solid) pairs (B).  An instance whose blocks have all met the nonlinear
+// tolerance gets a zero right-hand side from then on and drops out of the solves.
+struct fsi_batch_stepper {
+  std::vector<fsi_mesh*> meshes;
+  int n = 0;
+  fsi_batch* ns = nullptr;
+  fsi_batch* ac = nullptr;
+  fsi_batch* bb = nullptr;
+  std::vector<int> ac_inst, b_inst;  // instance of each AC / B entry
+  double* rhs = nullptr;             // largest concatenated block vector
+  double* dx = nullptr;
+};
+
+namespace fsi {
+namespace {
+
+// rhs segment of every entry: -R_block of a live instance, zero otherwise
+int batch_rhs(fsi_batch* b, const std::vector<int>& inst, const std::vector<int>& live, fsi_state* states, bool f32,
+              double* rhs, bool ns_unpinned, unsigned flags) {
+  int last = -1;
+  for (int e = 0; e < b->n; ++e) {
+    fsi_mesh* m = b->meshes[e];
+    const int i = inst[e];
+    BlockInfo bi;
+    int rc = block_info(m, b->blocks[e], &bi);
+    if (rc) return rc;
+    double* r = rhs + b->off[e];
+    if (!live[i]) {
+      FSI_CUDA(cudaMemsetAsync(r, 0, sizeof(double) * bi.n, m->stream));
+      continue;
+    }
+    if (i != last && (rc = stage(m, &states[i], f32))) return rc;
+    last = i;
+    if (bi.kind == 1) {
+      double gb[2];
+      if ((rc = op_coeffs(m, bi.index, gb))) return rc;
+      m->gamma[bi.index] = m->fixed_gamma[bi.index] >= 0.0 ? m->fixed_gamma[bi.index] : gb[0];
+      m->beta[bi.index] = gb[1];
+    }
+    PinGuard guard(m, (ns_unpinned && bi.kind == 0 && shifts_pressure(m, flags)) ? 0 : m->pin_active);
+    if ((rc = op_residual(m, bi, r))) return rc;
+    if ((rc = vec_scale_copy(m, -1.0, r, r, bi.n))) return rc;
+  }
+  return FSI_OK;
+}
+
+// x_block += dx of every live entry (NS: after the pressure shift), and the largest
+// |dx_blk| / |x_blk| of each instance
+int batch_update(fsi_batch* b, const std::vector<int>& inst, const std::vector<int>& live, fsi_state* states,
+                 double* dx, std::vector<double>& ratio, unsigned flags) {
+  for (int e = 0; e < b->n; ++e) {
+    const int i = inst[e];
+    if (!live[i]) continue;
+    fsi_mesh* m = b->meshes[e];
+    BlockInfo bi;
+    int rc = block_info(m, b->blocks[e], &bi);
+    if (rc) return rc;
+    double* d = dx + b->off[e];
+    if (bi.kind == 0 && shifts_pressure(m, flags) && (rc = pin_shift(m, states[i].x, d))) return rc;
+    double* xb = states[i].x + (int64_t)bi.c0 * m->nn;
+    if ((rc = vec_axpy(m, 1.0, d, xb, bi.n))) return rc;
+    double d2, x2;
+    if ((rc = vec_dot(m, d, d, bi.n, &d2)) || (rc = vec_dot(m, xb, xb, bi.n, &x2))) return rc;
+    if (!std::isfinite(d2) || !std::isfinite(x2)) return set_error(FSI_ENAN, "fsi_batch_step: solution is not finite");
+    ratio[i] = std::max(ratio[i], x2 > 0.0 ? std::sqrt(d2 / x2) : std::sqrt(d2));
+  }
+  return FSI_OK;
+}
+
+// one batched block solve of the live instances; per-instance statistics into infos
+int batch_block(fsi_batch* b, const std::vector<int>& inst, const std::vector<int>& live, fsi_state* states,
+                const fsi_solve_opts& o, double* rhs, double* dx, std::vector<double>& ratio, fsi_step_info* infos,
+                int kind) {
+  if (!b) return FSI_OK;
+  const bool f32 = o.precision == FSI_PREC_FP32_IR;
+  int rc;
+  if ((rc = batch_rhs(b, inst, live, states, f32, rhs, kind == 0, o.flags))) return rc;
+  std::vector<fsi_state> est(b->n);
+  for (int e = 0; e < b->n; ++e) est[e] = states[inst[e]];
+  std::vector<fsi_solve_info> si(b->n);
+  {
+    // the NS entries keep their pin node's continuity equation for the whole solve
+    std::vector<PinGuard*> guards;
+    for (int e = 0; e < b->n; ++e)
+      if (kind == 0 && shifts_pressure(b->meshes[e], o.flags)) guards.push_back(new PinGuard(b->meshes[e], 0));
+    rc = fsi_batch_gmres(b, est.data(), rhs, dx, &o, si.data());
+    for (PinGuard* g : guards) delete g;
+    if (rc && rc != FSI_ENOCONV) return rc;
+  }
+  for (int e = 0; e < b->n; ++e) {
+    const int i = inst[e];
+    if (!live[i]) continue;
+    fsi_step_info& inf = infos[i];
+    inf.worst_rel_res = std::max(inf.worst_rel_res, si[e].rel_res);
+    if (si[e].stalled) inf.stalled_solves++;
+    if (kind == 0) inf.gmres_iters_ns += si[e].iterations;
+    else if (kind == 1) inf.gmres_iters_ac += si[e].iterations;
+    else inf.gmres_iters_b += si[e].iterations;
+    // the batched products of this entry, counted on its mesh like single-mesh applies
+    b->meshes[e]->applies += si[e].applies;
+    b->meshes[e]->dof_applied += (int64_t)si[e].applies * (b->off[e + 1] - b->off[e]);
+  }
+  return batch_update(b, inst, live, states, dx, ratio, o.flags);
+}
+
+}  // namespace
+}  // namespace fsi
+
+extern "C" {
+
+int fsi_batch_stepper_destroy(fsi_batch_stepper* s) {
+  if (!s) return FSI_OK;
+  fsi_batch_destroy(s->ns);
+  fsi_batch_destroy(s->ac);
+  fsi_batch_destroy(s->bb);
+  cudaFree(s->rhs);
+  cudaFree(s->dx);
+  delete s;
+  return FSI_OK;
+}
+
+int fsi_batch_stepper_create(fsi_mesh* const* meshes, int32_t n, int32_t m, fsi_batch_stepper** out) {
+  if (!meshes || !out || n < 1) return set_error(FSI_EINVAL, "fsi_batch_stepper_create: bad arguments");
+  *out = nullptr;
+  auto* s = new fsi_batch_stepper();
+  s->meshes.assign(meshes, meshes + n);
+  s->n = n;
+  int rc = fsi_batch_create(meshes, n, FSI_BLOCK_NS, m, &s->ns);
+  std::vector<fsi_mesh*> am, bm;
+  std::vector<int32_t> ab, bbk;
+  for (int i = 0; i < n && !rc; ++i) {
+    if (!meshes[i]) rc = set_error(FSI_EINVAL, "fsi_batch_stepper_create: null mesh");
+    else {
+      for (int p = 0; p < meshes[i]->N; ++p) am.push_back(meshes[i]), ab.push_back(FSI_BLOCK_AC(p)), s->ac_inst.push_back(i);
+      for (int q = 0; q < meshes[i]->ns; ++q) bm.push_back(meshes[i]), bbk.push_back(FSI_BLOCK_B(q)), s->b_inst.push_back(i);
+    }
+  }
+  if (!rc && !am.empty()) rc = fsi_batch_create_blocks(am.data(), ab.data(), (int32_t)am.size(), m, &s->ac);
+  if (!rc && !bm.empty()) rc = fsi_batch_create_blocks(bm.data(), bbk.data(), (int32_t)bm.size(), m, &s->bb);
+  if (!rc) {
+    int64_t cap = s->ns->ntot;
+    if (s->ac) cap = std::max(cap, s->ac->ntot);
+    if (s->bb) cap = std::max(cap, s->bb->ntot);
+    if (cudaMalloc(&s->rhs, sizeof(double) * cap) != cudaSuccess || cudaMalloc(&s->dx, sizeof(double) * cap) != cudaSuccess)
+      rc = set_error(FSI_ECUDA, "fsi_batch_stepper_create: work vectors");
+  }
+  if (rc) {
+    fsi_batch_stepper_destroy(s);
+    return rc;
+  }
+  *out = s;
+  return FSI_OK;
+}
+
+int fsi_batch_step(fsi_batch_stepper* s, fsi_state* states, const fsi_step_opts* o, fsi_step_info* infos) {
+  if (!s || !states || !o || !infos) return set_error(FSI_EINVAL, "fsi_batch_step: null argument");
+  if (o->k_max < 1) return set_error(FSI_EINVAL, "fsi_batch_step: k_max must be >= 1");
+  if (o->solve.precond != FSI_PC_JACOBI && o->solve.precond != FSI_PC_NONE)
+    return set_error(FSI_EINVAL, "fsi_batch_step: Jacobi or no preconditioner");
+  const int n = s->n;
+  std::vector<int64_t> a0(n), d0(n);
+  int rc;
+  for (int i = 0; i < n; ++i) {
+    infos[i] = fsi_step_info{};
+    a0[i] = s->meshes[i]->applies;
+    d0[i] = s->meshes[i]->dof_applied;
+    if (!states[i].x || !states[i].xn || !states[i].xdn) return set_error(FSI_EINVAL, "fsi_batch_step: null state");
+    if ((rc = step_predict(s->meshes[i], &states[i]))) return rc;
+  }
+  std::vector<int> live(n, 1), ns_inst(n);
+  for (int i = 0; i < n; ++i) ns_inst[i] = i;
+  for (int k = 0; k < o->k_max; ++k) {
+    std::vector<double> ratio(n, 0.0);
+    if ((rc = batch_block(s->ns, ns_inst, live, states, o->solve, s->rhs, s->dx, ratio, infos, 0)) ||
+        (rc = batch_block(s->ac, s->ac_inst, live, states, o->solve, s->rhs, s->dx, ratio, infos, 1)) ||
+        (rc = batch_block(s->bb, s->b_inst, live, states, o->solve, s->rhs, s->dx, ratio, infos, 2)))
+      return rc;
+    int nlive = 0;
+    for (int i = 0; i < n; ++i) {
+      if (!live[i]) continue;
+      infos[i].nl_iters = k + 1;
+      infos[i].max_ratio = ratio[i];
+      if (!o->fixed_iters && ratio[i] < o->nl_tol) live[i] = 0;
+      nlive += live[i];
+    }
+    if (!nlive) break;
+  }
+  for (int i = 0; i < n; ++i)
+    if ((rc = step_correct(s->meshes[i], &states[i]))) return rc;
+  FSI_CUDA(cudaStreamSynchronize(s->ns->stream));
+  for (int i = 0; i < n; ++i) {
+    infos[i].applies = (int)(s->meshes[i]->applies - a0[i]);
+    infos[i].dof_applied = s->meshes[i]->dof_applied - d0[i];
+  }
   return FSI_OK;
 }
 

@@ -175,6 +175,20 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& b, const double* rhs, double* x, c
 // tile launch geometry
 void tile_grid(const fsi_mesh* m, dim3* grid);
 
+// time-step pieces (step.cu): predictor and corrector launches, the pressure shift of
+// enclosed domains after an NS solve that kept the pin node's continuity equation
+int step_predict(fsi_mesh* m, fsi_state* st);
+int step_correct(fsi_mesh* m, fsi_state* st);
+bool shifts_pressure(const fsi_mesh* m, unsigned solve_flags);
+int pin_shift(fsi_mesh* m, const double* x, double* dx);
+// Sets the pressure pin of a mesh for a scope and restores it on leaving (also on errors).
+struct PinGuard {
+  fsi_mesh* m;
+  int saved;
+  PinGuard(fsi_mesh* mm, int active) : m(mm), saved(mm->pin_active) { m->pin_active = active; }
+  ~PinGuard() { m->pin_active = saved; }
+};
+
 // Raises a kernel's cudaFuncAttributeMaxDynamicSharedMemorySize to at least `bytes` on
 // the current device, once per (kernel, device, size); safe from several host threads.
 int ensure_smem_attr(const void* func, size_t bytes);

@@ -46,13 +46,29 @@ __global__ void pin_shift_apply(double* dxp, const double* s, int64_t nn) {
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < nn; n += stride) dxp[n] -= v;
 }
 
-// Restores the pressure pin of a mesh when a block solve leaves (also on errors).
-struct PinGuard {
-  fsi_mesh* m;
-  int saved;
-  PinGuard(fsi_mesh* mm, int active) : m(mm), saved(mm->pin_active) { m->pin_active = active; }
-  ~PinGuard() { m->pin_active = saved; }
-};
+int step_predict(fsi_mesh* m, fsi_state* st) {
+  FSI_LAUNCH(m, P_STAGE, predictor_kernel<<<grid_for(m->nn), 256, 0, m->stream>>>(st->x, st->xn, m->mask, m->vD,
+                                                                                   m->ncomp, m->nn));
+  return FSI_OK;
+}
+
+int step_correct(fsi_mesh* m, fsi_state* st) {
+  const int64_t n = m->nn * m->ncomp;
+  FSI_LAUNCH(m, P_STAGE, corrector_kernel<<<grid_for(n), 256, 0, m->stream>>>(st->x, st->xn, st->xdn, m->P.dt,
+                                                                                 m->P.vs, n));
+  return FSI_OK;
+}
+
+bool shifts_pressure(const fsi_mesh* m, unsigned solve_flags) {
+  return m->pin_node >= 0 && m->enclosed && m->pin_active && !(solve_flags & FSI_PINNED_SOLVE);
+}
+
+int pin_shift(fsi_mesh* m, const double* x, double* dx) {
+  const int64_t nn = m->nn;
+  FSI_LAUNCH(m, P_STAGE, pin_shift_value<<<1, 32, 0, m->stream>>>(x + 3 * nn, dx + 3 * nn, m->pin_node, m->red + 8));
+  FSI_LAUNCH(m, P_STAGE, pin_shift_apply<<<grid_for(nn), 256, 0, m->stream>>>(dx + 3 * nn, m->red + 8, nn));
+  return FSI_OK;
+}
 
 }  // namespace fsi
 
@@ -86,9 +102,8 @@ int fsi_step(fsi_mesh* m, fsi_state* st, const fsi_step_opts* o, fsi_step_info* 
   const bool fp32 = o->solve.precision == FSI_PREC_FP32_IR;
   fsi_step_info inf{};
   const int64_t a0 = m->applies, d0 = m->dof_applied;
-  FSI_LAUNCH(m, P_STAGE,
-             predictor_kernel<<<grid_for(nn), 256, 0, m->stream>>>(st->x, st->xn, m->mask, m->vD, m->ncomp, nn));
   int rc;
+  if ((rc = step_predict(m, st))) return rc;
   const int nblocks = 1 + m->N + m->ns;
   for (int k = 0; k < o->k_max; ++k) {
     double max_ratio = 0.0;
@@ -105,8 +120,7 @@ int fsi_step(fsi_mesh* m, fsi_state* st, const fsi_step_opts* o, fsi_step_info* 
       }
       // NS block of an enclosed domain: the pin node keeps its continuity equation in
       // the solve and the pressure level is set by the shift below
-      const bool shift = b.kind == 0 && m->pin_node >= 0 && m->enclosed && m->pin_active &&
-                         !(o->solve.flags & FSI_PINNED_SOLVE);
+      const bool shift = b.kind == 0 && shifts_pressure(m, o->solve.flags);
       fsi_solve_info si{};
       {
         PinGuard guard(m, shift ? 0 : m->pin_active);
@@ -115,11 +129,7 @@ int fsi_step(fsi_mesh* m, fsi_state* st, const fsi_step_opts* o, fsi_step_info* 
         rc = gmres_solve(m, b, rhs, dx, o->solve, &si);
         if (rc && rc != FSI_ENOCONV) return rc;
       }
-      if (shift) {
-        FSI_LAUNCH(m, P_STAGE, pin_shift_value<<<1, 32, 0, m->stream>>>(st->x + 3 * nn, dx + 3 * nn, m->pin_node,
-                                                                         m->red + 8));
-        FSI_LAUNCH(m, P_STAGE, pin_shift_apply<<<grid_for(nn), 256, 0, m->stream>>>(dx + 3 * nn, m->red + 8, nn));
-      }
+      if (shift && (rc = pin_shift(m, st->x, dx))) return rc;
       inf.worst_rel_res = std::max(inf.worst_rel_res, si.rel_res);
       if (si.stalled) inf.stalled_solves++;
       if (si.fallback) inf.fallback_solves++;
@@ -139,9 +149,7 @@ int fsi_step(fsi_mesh* m, fsi_state* st, const fsi_step_opts* o, fsi_step_info* 
     inf.max_ratio = max_ratio;
     if (!o->fixed_iters && max_ratio < o->nl_tol) break;
   }
-  FSI_LAUNCH(m, P_STAGE,
-             corrector_kernel<<<grid_for(nn * m->ncomp), 256, 0, m->stream>>>(st->x, st->xn, st->xdn, m->P.dt,
-                                                                              m->P.vs, nn * m->ncomp));
+  if ((rc = step_correct(m, st))) return rc;
   FSI_CUDA(cudaStreamSynchronize(m->stream));
   inf.applies = (int)(m->applies - a0);
   inf.dof_applied = m->dof_applied - d0;

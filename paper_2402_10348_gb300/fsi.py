@@ -115,7 +115,8 @@ EXPORTS = ["fsi_create_mesh", "fsi_destroy_mesh", "fsi_set_stream", "fsi_mesh_in
            "fsi_pc_apply", "fsi_pc_add_pair", "fsi_pc_pairs", "fsi_pc_fit_norm", "fsi_pc_train", "fsi_set_pc",
            "fsi_batch_create", "fsi_batch_destroy", "fsi_batch_layout", "fsi_batch_jvp", "fsi_batch_gmres",
            "fsi_batch_autotune", "fsi_batch_set_graph", "fsi_center_of_mass", "fsi_track_points",
-           "fsi_probe_peaks", "fsi_last_error"]
+           "fsi_probe_peaks", "fsi_batch_create_blocks", "fsi_batch_stepper_create", "fsi_batch_stepper_destroy",
+           "fsi_batch_step", "fsi_last_error"]
 
 _lib = None
 
@@ -508,6 +509,52 @@ def fsi_batch_create(meshes, block: int = 0, m: int = 64) -> Batch:
     h = C.c_void_p()
     _check(lib().fsi_batch_create(arr, C.c_int32(len(meshes)), C.c_int32(block), C.c_int32(m), C.byref(h)))
     return Batch(h, meshes)
+
+
+def fsi_batch_create_blocks(meshes, blocks, m: int = 64) -> Batch:
+    """A batch whose entry i solves block blocks[i] of meshes[i] (a mesh may repeat)."""
+    arr = (C.c_void_p * len(meshes))(*[mm.handle.value if hasattr(mm.handle, "value") else mm.handle
+                                       for mm in meshes])
+    blk = (C.c_int32 * len(blocks))(*blocks)
+    h = C.c_void_p()
+    _check(lib().fsi_batch_create_blocks(arr, blk, C.c_int32(len(meshes)), C.c_int32(m), C.byref(h)))
+    return Batch(h, meshes)
+
+
+class BatchStepper:
+    """Owns an fsi_batch_stepper handle; keeps its meshes alive."""
+
+    def __init__(self, handle, meshes, m):
+        self.handle = handle
+        self.meshes = list(meshes)
+        self.n = len(self.meshes)
+        self.m = m
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.fsi_batch_stepper_destroy(h)
+            self.handle = None
+
+
+def fsi_batch_stepper_create(meshes, m: int = 30) -> BatchStepper:
+    arr = (C.c_void_p * len(meshes))(*[mm.handle.value if hasattr(mm.handle, "value") else mm.handle
+                                       for mm in meshes])
+    h = C.c_void_p()
+    _check(lib().fsi_batch_stepper_create(arr, C.c_int32(len(meshes)), C.c_int32(m), C.byref(h)))
+    return BatchStepper(h, meshes, m)
+
+
+def fsi_batch_step(stepper: BatchStepper, states, k_max=5, nl_tol=5e-4, fixed_iters=False,
+                   solve: fsi_solve_opts | None = None):
+    """One batched time step of every instance; states: list of (x, xn, xdn) device
+    tensors advanced in place.  Returns the per-instance fsi_step_info list."""
+    st = _states(states)
+    o = fsi_step_opts(k_max, 1 if fixed_iters else 0, nl_tol,
+                      solve if solve is not None else solve_opts(m=stepper.m))
+    infos = (fsi_step_info * stepper.n)()
+    _check(lib().fsi_batch_step(stepper.handle, st, C.byref(o), infos))
+    return list(infos)
 
 
 def fsi_batch_jvp(batch: Batch, states, dx, y, flags: int = FSI_ELASTIC_AUG):

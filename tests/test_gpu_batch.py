@@ -119,3 +119,104 @@ def test_autotuner_picks_a_shape_and_caches_it(tmp_path, monkeypatch):
     assert (int(line[1]), int(line[2])) == (tm, gm)
     b2 = fsi.fsi_batch_create(meshes, block=fsi.FSI_BLOCK_NS, m=30)  # the cache is read at creation
     assert b2.layout()[:2] == (tm, gm)
+
+
+def test_batched_products_and_solves_against_the_oracle():
+    """Each instance of a batch of uneven meshes against the oracle: the batched NS, AC
+    and B products (float64, 1e-10 of max) and the batched float64 NS solve (rel-res
+    1e-12) against the oracle's exact solve of the same system (sparse LU of the probed
+    Jacobian): residual with the oracle's operator <= 1e-11, solution within 1e-6."""
+    from oracle import blocks
+    from oracle.assemble import assemble, direct_solve
+    from oracle.fields import Problem, State
+    descs, meshes, states, stream = _instances([5, 7], seed=9)
+    host = [tuple(a.cpu().numpy() for a in st) for st in states]
+    coeffs = {"gamma": {1: 0.37}, "beta": {1: 0.11}}
+    for block, name in ((fsi.FSI_BLOCK_NS, "ns"), (fsi.FSI_BLOCK_AC(1), ("ac", 1)), (fsi.FSI_BLOCK_B(0), ("b", 0))):
+        b = fsi.fsi_batch_create(meshes, block=block, m=30)
+        rng = np.random.default_rng(7)
+        dxs = [rng.normal(size=b.offsets[i + 1] - b.offsets[i]) for i in range(b.n)]
+        yb = torch.zeros(b.offsets[-1], dtype=torch.float64, device=DEV)
+        with torch.cuda.stream(stream):
+            for m in meshes:
+                fsi.fsi_set_ac_coeffs(m, 1, 0.37, 0.11)
+            fsi.fsi_batch_jvp(b, states, T(np.concatenate(dxs)), yb, fsi.FSI_ELASTIC_AUG)
+        torch.cuda.synchronize()
+        for i, d in enumerate(descs):
+            pb, st = Problem(d), State(*host[i])
+            ref = blocks.jvp(pb, st, name, dxs[i], coeffs)
+            got = yb[b.offsets[i]:b.offsets[i + 1]].cpu().numpy()
+            assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max(), (name, i)
+    b = fsi.fsi_batch_create(meshes, block=fsi.FSI_BLOCK_NS, m=30)
+    rhs = [-blocks.residual(Problem(d), State(*host[i]), "ns") for i, d in enumerate(descs)]
+    o = fsi.solve_opts(m=30, rtol=1e-12, max_iter=8000)
+    xb = torch.zeros(b.offsets[-1], dtype=torch.float64, device=DEV)
+    with torch.cuda.stream(stream):
+        infos = fsi.fsi_batch_gmres(b, states, T(np.concatenate(rhs)), xb, o)
+    torch.cuda.synchronize()
+    for i, d in enumerate(descs):
+        pb, st = Problem(d), State(*host[i])
+        A = assemble(pb, st, "ns")
+        exact = direct_solve(A, rhs[i])
+        got = xb[b.offsets[i]:b.offsets[i + 1]].cpu().numpy()
+        assert infos[i].rel_res <= 1e-12
+        assert np.linalg.norm(rhs[i] - blocks.jvp(pb, st, "ns", got)) <= 1e-11 * np.linalg.norm(rhs[i])
+        assert np.linalg.norm(got - exact) <= 1e-6 * np.linalg.norm(exact), i
+
+
+def _cavity_states(sizes):
+    from oracle.gridcell import apply_rules, signed_distance_phi
+    descs, xs = [], []
+    for n in sizes:
+        wl = cavity(n)
+        d = wl.desc
+        phi, _ = signed_distance_phi(d, wl.surfaces[0], d.eps, wl.grid_cells)
+        x = np.zeros((d.ncomp, d.nn))
+        x[4:4 + d.n_phase] = apply_rules(d, {0: phi}, wl.rules, d.eps)
+        x[4 + d.n_phase: 4 + d.n_phase + 3] = 1.0
+        descs.append(d)
+        xs.append(x)
+    return descs, xs
+
+
+@pytest.mark.parametrize("precision", [fsi.FSI_PREC_FP64, fsi.FSI_PREC_FP32_IR])
+def test_batched_time_steps_match_per_instance_steps_and_the_oracle(precision):
+    """Three uneven cavities advanced by batched partitioned steps (one batched solve per
+    block kind and nonlinear iteration; the Allen-Cahn blocks of both phases of every
+    instance in one batch) against per-instance fsi_step, two steps of three fixed
+    nonlinear iterations, every solve to rel-res 1e-12: the fields agree to 1e-9
+    (float64) and 1e-6 (float32 refinement).  The 5^3 instance is also held to the
+    oracle's steps with exact block solves (1e-10 in float64)."""
+    from oracle import step as ostep
+    from oracle.fields import Problem, State
+    descs, xs = _cavity_states([5, 7, 6])
+    stream = torch.cuda.Stream()
+    o = fsi.solve_opts(m=30, rtol=1e-12, max_iter=6000, precision=precision, ir_inner_rtol=1e-3, ir_max=60)
+    singles, batched, meshes_b = [], [], []
+    for d, x in zip(descs, xs):
+        ms = fsi.fsi_create_mesh(d)
+        fsi.fsi_set_stream(ms, stream)
+        mb = fsi.fsi_create_mesh(d)
+        fsi.fsi_set_stream(mb, stream)
+        singles.append((ms, [T(x), T(x), T(np.zeros_like(x))]))
+        batched.append([T(x), T(x), T(np.zeros_like(x))])
+        meshes_b.append(mb)
+    stepper = fsi.fsi_batch_stepper_create(meshes_b, m=30)
+    ref = State(xs[0].copy(), xs[0].copy(), np.zeros_like(xs[0]))
+    for s in range(2):
+        with torch.cuda.stream(stream):
+            for ms, st in singles:
+                fsi.fsi_step(ms, *st, k_max=3, fixed_iters=True, solve=o)
+            infos = fsi.fsi_batch_step(stepper, batched, k_max=3, fixed_iters=True, solve=o)
+        torch.cuda.synchronize()
+        ostep.time_step(Problem(descs[0]), ref, ostep.StepOptions(k_max=3, fixed_nl_iters=True, direct=True))
+        for i, d in enumerate(descs):
+            assert infos[i].nl_iters == 3
+            a = batched[i][1].cpu().numpy().reshape(d.ncomp, d.nn)
+            b = singles[i][1][1].cpu().numpy().reshape(d.ncomp, d.nn)
+            for sl in (slice(0, 3), slice(3, 4), slice(4, 6), slice(6, 12)):
+                e = np.linalg.norm(a[sl] - b[sl]) / np.linalg.norm(b[sl])
+                assert e <= (1e-9 if precision == fsi.FSI_PREC_FP64 else 1e-6), (s, i, sl, e)
+                if i == 0 and precision == fsi.FSI_PREC_FP64:
+                    eo = np.linalg.norm(a[sl] - ref.xn[sl]) / np.linalg.norm(ref.xn[sl])
+                    assert eo <= 1e-10, (s, sl, eo)
