@@ -25,6 +25,8 @@ the steps in the order the paper states them:
   gmres.py     restarted right-preconditioned GMRES with modified Gram-Schmidt.
   assemble.py  sparse block Jacobians by 27-colour probing and the exact (sparse LU)
                linear solve.
+  tet.py       linear tetrahedra (six per box cell, optionally jittered nodes) with
+               the same interface, so the weak forms above evaluate on them.
   step.py      partitioned block Newton time step (Section 2.5).
   gridcell.py  grid-cell distance and ray-casting sign with non-duplicated plane
                partitioning (Section 3, Algorithms 1 and 2).
