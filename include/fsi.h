@@ -141,6 +141,21 @@ int fsi_update_ac_coeffs(fsi_mesh* mesh, int32_t phase, const fsi_state* st, dou
 int fsi_set_ac_coeffs(fsi_mesh* mesh, int32_t phase, double gamma, double beta);
 /* Fixes gamma^i for the time step (gamma >= 0), or restores the mobility model (< 0). */
 int fsi_fix_gamma(fsi_mesh* mesh, int32_t phase, double gamma);
+/* Linear (P1) tetrahedral mesh, the paper's element for its falling-sphere and ship-ice
+ * runs (Sections 5.3, 6).  d describes the physics and a box grid whose nodes
+ * (nn = (nx+1)(ny+1)(nz+1), numbered as for the hexahedral mesh) and face boundary
+ * conditions the tetrahedral mesh keeps; coords: host [3][nn] node coordinates (the
+ * box faces' nodes on their faces); conn: host [ne][4] node indices of each element,
+ * positively oriented (det(x1-x0, x2-x0, x3-x0) > 0), forming a conforming mesh.
+ * Geometry (barycentric gradients, volumes, the stabilisation metric G = sum_k
+ * grad(xi_k) grad(xi_k)^T) and the node-to-element lists are built here; the caller's
+ * arrays are not kept.  Such a mesh carries the float64 NS residual, product, diagonal
+ * and GMRES (fsi_residual, fsi_jvp, fsi_diag, fsi_gmres with FSI_BLOCK_NS); the other
+ * calls return FSI_EINVAL on it.  Errors: FSI_EINVAL for an index out of range or an
+ * element of non-positive volume. */
+int fsi_create_tet_mesh(const fsi_mesh_desc* desc, const double* coords, const int32_t* conn, int64_t ne,
+                        fsi_mesh** out);
+
 /* Pressure level of an enclosed domain (every face with a Dirichlet velocity; the
  * pressure is then determined up to a constant, Section 2.1.2's momentum/continuity
  * system has constant pressure in its null space).  active = 1 (default): the NS

@@ -819,6 +819,7 @@ int fsi_batch_create_blocks(fsi_mesh* const* meshes, const int32_t* blocks, int3
   *out = nullptr;
   for (int i = 0; i < n; ++i) {
     if (!meshes[i]) return set_error(FSI_EINVAL, "fsi_batch_create: null mesh");
+    if (meshes[i]->tet) return set_error(FSI_EINVAL, "fsi_batch_create: not on tetrahedral meshes");
     if (meshes[i]->stream != meshes[0]->stream || meshes[i]->dev != meshes[0]->dev)
       return set_error(FSI_EINVAL, "fsi_batch_create: all instances need one device and one stream (fsi_set_stream)");
   }

@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(DB) track_kernel(const double* __restrict__ v,
 using namespace fsi;
 
 int fsi_center_of_mass(fsi_mesh* m, const double* x, int32_t solid, double* out) {
+  if (m && m->tet) return set_error(FSI_EINVAL, "diagnostics: not on tetrahedral meshes");
   if (!m || !x || !out) return set_error(FSI_EINVAL, "fsi_center_of_mass: null argument");
   if (solid < 0 || solid >= m->ns) return set_error(FSI_EINVAL, "fsi_center_of_mass: bad solid index");
   const double* phi = x + (int64_t)(4 + m->P.solid_phase[solid]) * m->nn;
@@ -122,6 +123,7 @@ int fsi_center_of_mass(fsi_mesh* m, const double* x, int32_t solid, double* out)
 }
 
 int fsi_track_points(fsi_mesh* m, const double* x, int64_t n, double* points) {
+  if (m && m->tet) return set_error(FSI_EINVAL, "diagnostics: not on tetrahedral meshes");
   if (!m || n < 0) return set_error(FSI_EINVAL, "fsi_track_points: bad argument");
   if (n == 0) return FSI_OK;
   if (!x || !points) return set_error(FSI_EINVAL, "fsi_track_points: null argument");

@@ -247,6 +247,7 @@ using namespace fsi;
 
 extern "C" int fsi_init_phases(fsi_mesh* m, const fsi_surface* surfs, int32_t n_surf, const fsi_phase_rule* rules,
                                int32_t gx, int32_t gy, int32_t gz, double* phi_out, int32_t* tags_out) {
+  if (m && m->tet) return set_error(FSI_EINVAL, "fsi_init_phases: not on tetrahedral meshes");
   if (!m || !phi_out || (n_surf > 0 && !surfs) || !rules) return set_error(FSI_EINVAL, "fsi_init_phases: null argument");
   if (gx < 1 || gy < 1 || gz < 1) return set_error(FSI_EINVAL, "fsi_init_phases: grid cells must be >= 1");
   for (int r = 0; r < m->N; ++r)

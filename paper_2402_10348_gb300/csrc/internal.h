@@ -10,6 +10,9 @@
 #include "ops.cuh"
 
 struct fsi_batch;
+namespace fsi {
+struct TetData;  // tet.cu
+}
 
 namespace fsi {
 // Kernel classes of the event profiler (fsi_profile).
@@ -105,6 +108,7 @@ struct fsi_mesh {
   double* Z = nullptr;       // [m][n] FGMRES preconditioned directions
   int64_t Z_n = 0;
   fsi_pc* pc = nullptr;      // attached learned preconditioner (NS block), not owned
+  fsi::TetData* tet = nullptr;  // linear tetrahedra (fsi_create_tet_mesh): NS operators by connectivity
   fsi::BatchRec* rec = nullptr;  // non-null: operator launches are recorded, not run
   // counters (step info)
   int64_t applies = 0;
@@ -174,6 +178,10 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& b, const double* rhs, double* x, c
 
 // tile launch geometry
 void tile_grid(const fsi_mesh* m, dim3* grid);
+
+// linear tetrahedra (tet.cu): NS residual (mode 0), product (1), diagonal (2)
+int tet_ns(fsi_mesh* m, int mode, const double* dx, double* y, unsigned flags);
+void tet_free(TetData* t);
 
 // time-step pieces (step.cu): predictor and corrector launches, the pressure shift of
 // enclosed domains after an NS solve that kept the pin node's continuity equation

@@ -466,12 +466,11 @@ struct NSBuildOp {
 
 // The product's arithmetic at one quadrature point, from the interpolated increment
 // (dv, its gradient gd[k][j] = d_j dv_k, dp and its gradient dgp) and the point's
-// coefficients k (`stride` apart): accumulates the unweighted contributions of the four
-// equations into c[eq][corner].
+// coefficients k (the 44 above): the coefficients of the test functions, f[eq] of N_a and
+// g[eq][j] of d_j N_a, for the three momentum equations and continuity (unweighted).
 template <typename T, class Coef>
-__device__ __forceinline__ void nsq_point(const Coef& k, bool elastic, const T (&dv)[3], const T (&gd)[3][3], T dp,
-                                          const T (&dgp)[3], T al, T cmass, const QW<T>& w, T rhx, T rhy, T rhz,
-                                          T (&c)[4][8]) {
+__device__ __forceinline__ void nsq_point_fg(const Coef& k, bool elastic, const T (&dv)[3], const T (&gd)[3][3],
+                                             T dp, const T (&dgp)[3], T al, T cmass, T (&f)[4], T (&g)[4][3]) {
   const T rho = k(0), mu = k(1);
   const T v[3] = {k(2), k(3), k(4)};
   const T Rm[3] = {k(14), k(15), k(16)};
@@ -512,17 +511,28 @@ __device__ __forceinline__ void nsq_point(const Coef& k, bool elastic, const T (
   for (int kk = 0; kk < 3; ++kk) {
     const T sk = tau_m * (dRm[kk] + dgp[kk]);
     const T rk = tau_m * Rm[kk];
-    T gk[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       T sj = dE[sym_idx(kk, j)] + mu * (dL[kk][j] + dL[j][kk]) + vt[j] * rk + v[j] * sk;
       if (j == kk) sj += -dp + tc_rho * dRc;
-      gk[j] = sj;
+      g[kk][j] = sj;
     }
-    scatter_vg(c[kk], w, dRm[kk], gk[0], gk[1], gk[2], rhx, rhy, rhz);
+    f[kk] = dRm[kk];
   }
-  scatter_vg(c[3], w, dRc, tm_rho * (dRm[0] + dgp[0]), tm_rho * (dRm[1] + dgp[1]), tm_rho * (dRm[2] + dgp[2]), rhx,
-             rhy, rhz);
+  f[3] = dRc;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) g[3][j] = tm_rho * (dRm[j] + dgp[j]);
+}
+
+// The same, scattered to the 8 corners of a hex quadrature point (sum-factorised).
+template <typename T, class Coef>
+__device__ __forceinline__ void nsq_point(const Coef& k, bool elastic, const T (&dv)[3], const T (&gd)[3][3], T dp,
+                                          const T (&dgp)[3], T al, T cmass, const QW<T>& w, T rhx, T rhy, T rhz,
+                                          T (&c)[4][8]) {
+  T f[4], g[4][3];
+  nsq_point_fg<T>(k, elastic, dv, gd, dp, dgp, al, cmass, f, g);
+#pragma unroll
+  for (int eq = 0; eq < 4; ++eq) scatter_vg(c[eq], w, f[eq], g[eq][0], g[eq][1], g[eq][2], rhx, rhy, rhz);
 }
 
 // Coefficient accessor over a strided plane layout (loads through the read-only path).

@@ -1,0 +1,398 @@
+// Linear (P1) tetrahedral meshes: the paper's element for its falling-sphere and
+// ship-ice meshes (Sections 5.3 and 6).  The momentum/continuity residual, Jacobian-
+// vector product and Jacobi diagonal of Eq. PG_NS evaluated element by element through
+// the mesh connectivity.
+//
+// Node set, node numbering and boundary conditions are those of the description's box
+// grid; coordinates and connectivity are the caller's (any conforming tetrahedral mesh of
+// those nodes).  Quadrature: the symmetric 4-point rule (barycentric points
+// (a, b, b, b) and permutations, weights |T|/4), exact for quadratics.  Stabilisation
+// metric per element: G = sum_k grad(xi_k) grad(xi_k)^T over the reference coordinates.
+//
+// Assembly is atomics-free and deterministic: the element kernel writes each element's
+// 4 corners x 4 equations into E (one slot per element and corner), and the node kernel
+// sums, for every node, the slots of its elements in increasing element order (a CSR
+// list built once at creation), then applies the Dirichlet rows.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace fsi {
+
+struct TetData {
+  int64_t ne = 0;
+  int32_t* conn = nullptr;  // [4][ne] node of corner a of element e at conn[a * ne + e]
+  double* geo = nullptr;    // [TG][ne]: grad lambda_a (12, a-major), quadrature weight |T|/4, G (6 sym)
+  int64_t* nptr = nullptr;  // [nn + 1]
+  int32_t* nlist = nullptr; // 4 e + a of every (element, corner) at a node, by element
+  double* E = nullptr;      // [16][ne] element contributions, slot (a * 4 + eq)
+};
+
+constexpr int TG = 19;
+#define FSI_TA 0.58541019662496845446  // (5 + 3 sqrt5) / 20
+#define FSI_TB 0.13819660112501051518  // (5 - sqrt5) / 20
+
+void tet_free(TetData* t) {
+  if (!t) return;
+  cudaFree(t->conn);
+  cudaFree(t->geo);
+  cudaFree(t->nptr);
+  cudaFree(t->nlist);
+  cudaFree(t->E);
+  delete t;
+}
+
+struct TetArgs {
+  const int32_t* conn;
+  const double* geo;
+  int64_t ne;
+  const double* xa;   // x^{n+alpha} (pressure plane: p^{n+1})
+  const double* xd;   // dx/dt^{n+alpha_m}
+  const double* mat;  // rho, mu, alpha^s
+  const double* dx;   // JVP increment (dv, dp) [4][nn]
+  double* E;
+  int64_t nn;
+  int elastic;
+  Phys P;
+};
+
+// nodal values of field f at the 4 corners
+__device__ __forceinline__ void tet_gather(const double* f, const int (&nd)[4], double (&u)[4]) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a) u[a] = f[nd[a]];
+}
+__device__ __forceinline__ double tet_val(const double (&u)[4], int q) {
+  const double wa = FSI_TA, wb = FSI_TB;
+  double s = 0.0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) s += (a == q ? wa : wb) * u[a];
+  return s;
+}
+__device__ __forceinline__ void tet_grad(const double (&u)[4], const double (&dN)[4][3], double (&g)[3]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) g[d] = dN[0][d] * u[0] + dN[1][d] * u[1] + dN[2][d] * u[2] + dN[3][d] * u[3];
+}
+
+// The 44 frozen coefficients of the product at quadrature point q of one element
+// (the layout of NSBuildOp: rho, mu, v, grad v, R_m, tau_m, tau_c rho, tau_m / rho,
+// sum a_s B^s, sum a_s grad B^s), and for the residual the elastic stress sum.
+struct TetPoint {
+  double k[NCQ];
+  double p;        // p^{n+1}
+  double acc[3];   // dv/dt + v.grad v
+  double E[6];     // sum_s alpha^s mu_L^s (B^s - I)
+};
+
+__device__ void tet_point(const TetArgs& A, const int (&nd)[4], const double (&dN)[4][3], const double (&G)[6], int q,
+                          bool with_elastic, TetPoint& o) {
+  const Phys& P = A.P;
+  const int64_t nn = A.nn;
+  double u[4], gr[3];
+  double v[3], L[3][3];
+  for (int kk = 0; kk < 3; ++kk) {
+    tet_gather(A.xa + kk * nn, nd, u);
+    v[kk] = tet_val(u, q);
+    tet_grad(u, dN, gr);
+    L[kk][0] = gr[0]; L[kk][1] = gr[1]; L[kk][2] = gr[2];
+  }
+  tet_gather(A.mat, nd, u);
+  const double rho = tet_val(u, q);
+  tet_gather(A.mat + nn, nd, u);
+  const double mu = tet_val(u, q);
+  tet_gather(A.xa + 3 * nn, nd, u);
+  o.p = tet_val(u, q);
+  double gp[3];
+  tet_grad(u, dN, gp);
+  double Rm[3];
+  for (int kk = 0; kk < 3; ++kk) {
+    tet_gather(A.xd + kk * nn, nd, u);
+    o.acc[kk] = tet_val(u, q) + v[0] * L[kk][0] + v[1] * L[kk][1] + v[2] * L[kk][2];
+    Rm[kk] = rho * o.acc[kk] + gp[kk] - rho * P.grav[kk];
+  }
+  // v.G v, G:G and tr G with the element's full metric
+  const double Gm[3][3] = {{G[0], G[3], G[5]}, {G[3], G[1], G[4]}, {G[5], G[4], G[2]}};
+  double vGv = 0.0, GG = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      vGv += v[i] * Gm[i][j] * v[j];
+      GG += Gm[i][j] * Gm[i][j];
+    }
+  const double trG = G[0] + G[1] + G[2];
+  const double nu = mu / rho;
+  const double tau_m = 1.0 / sqrt(4.0 / (P.dt * P.dt) + vGv + P.c_i * nu * nu * GG);
+  const double tau_c = 1.0 / (trG * tau_m);
+  o.k[0] = rho;
+  o.k[1] = mu;
+  for (int kk = 0; kk < 3; ++kk) o.k[2 + kk] = v[kk];
+  for (int kk = 0; kk < 3; ++kk)
+    for (int j = 0; j < 3; ++j) o.k[5 + 3 * kk + j] = L[kk][j];
+  for (int kk = 0; kk < 3; ++kk) o.k[14 + kk] = Rm[kk];
+  o.k[17] = tau_m;
+  o.k[18] = tau_c * rho;
+  o.k[19] = tau_m / rho;
+  for (int c = 0; c < 24; ++c) o.k[20 + c] = 0.0;
+  for (int c = 0; c < 6; ++c) o.E[c] = 0.0;
+  for (int s = 0; s < P.ns; ++s) {
+    tet_gather(A.mat + (2 + s) * nn, nd, u);
+    const double al = tet_val(u, q);
+    const double muL = P.muL[P.solid_phase[s]];
+    const double a = al * muL * P.c_el;
+    const int c0 = 4 + P.N + 6 * s;
+    for (int c = 0; c < 6; ++c) {
+      tet_gather(A.xa + (int64_t)(c0 + c) * nn, nd, u);
+      const double B = tet_val(u, q);
+      o.E[c] += al * muL * (B - (c < 3 ? 1.0 : 0.0));
+      if (with_elastic) {
+        tet_grad(u, dN, gr);
+        o.k[20 + c] += a * B;
+        for (int d = 0; d < 3; ++d) o.k[26 + 3 * c + d] += a * gr[d];
+      }
+    }
+  }
+}
+
+struct LocalCoef {
+  const double* k;
+  __device__ __forceinline__ double operator()(int i) const { return k[i]; }
+};
+
+__device__ __forceinline__ void tet_load_geo(const TetArgs& A, int64_t e, int (&nd)[4], double (&dN)[4][3],
+                                             double& w, double (&G)[6]) {
+  for (int a = 0; a < 4; ++a) nd[a] = A.conn[a * A.ne + e];
+  for (int a = 0; a < 4; ++a)
+    for (int d = 0; d < 3; ++d) dN[a][d] = A.geo[(3 * a + d) * A.ne + e];
+  w = A.geo[12 * A.ne + e];
+  for (int c = 0; c < 6; ++c) G[c] = A.geo[(13 + c) * A.ne + e];
+}
+
+// MODE 0 residual, 1 product, 2 diagonal of the product: element contributions into E
+template <int MODE>
+__global__ void __launch_bounds__(128) tet_ns_elem(const TetArgs A) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= A.ne) return;
+  int nd[4];
+  double dN[4][3], w, G[6];
+  tet_load_geo(A, e, nd, dN, w, G);
+  double c[4][4];  // [corner][equation]
+  for (int a = 0; a < 4; ++a)
+    for (int q = 0; q < 4; ++q) c[a][q] = 0.0;
+  // the increment at the corners (product) and its constant gradient
+  double du[4][4], dg[4][3];
+  if (MODE == 1) {
+    for (int f = 0; f < 4; ++f) {
+      double u[4];
+      tet_gather(A.dx + f * A.nn, nd, u);
+      for (int a = 0; a < 4; ++a) du[f][a] = u[a];
+      tet_grad(u, dN, dg[f]);
+    }
+  }
+  for (int q = 0; q < 4; ++q) {
+    TetPoint pt;
+    tet_point(A, nd, dN, G, q, MODE != 0 && A.elastic, pt);
+    double Nq[4];
+    for (int a = 0; a < 4; ++a) Nq[a] = a == q ? FSI_TA : FSI_TB;
+    if (MODE == 0) {
+      const double* k = pt.k;
+      const double rho = k[0], mu = k[1], tau_m = k[17], tc_rho = k[18], tm_rho = k[19];
+      const double Rc = k[5] + k[9] + k[13];
+      double f[4], g[4][3];
+      for (int kk = 0; kk < 3; ++kk) {
+        for (int j = 0; j < 3; ++j) {
+          double s = pt.E[sym_idx(kk, j)] + mu * (k[5 + 3 * kk + j] + k[5 + 3 * j + kk]) + tau_m * k[2 + j] * k[14 + kk];
+          if (j == kk) s += -pt.p + tc_rho * Rc;
+          g[kk][j] = s;
+        }
+        f[kk] = rho * (pt.acc[kk] - A.P.grav[kk]);
+      }
+      f[3] = Rc;
+      for (int j = 0; j < 3; ++j) g[3][j] = tm_rho * k[14 + j];
+      for (int a = 0; a < 4; ++a)
+        for (int eq = 0; eq < 4; ++eq)
+          c[a][eq] += w * (Nq[a] * f[eq] + dN[a][0] * g[eq][0] + dN[a][1] * g[eq][1] + dN[a][2] * g[eq][2]);
+    } else if (MODE == 1) {
+      double dv[3], gd[3][3], dgp[3];
+      for (int kk = 0; kk < 3; ++kk) {
+        dv[kk] = Nq[0] * du[kk][0] + Nq[1] * du[kk][1] + Nq[2] * du[kk][2] + Nq[3] * du[kk][3];
+        for (int d = 0; d < 3; ++d) gd[kk][d] = dg[kk][d];
+        dgp[kk] = dg[3][kk];
+      }
+      const double dp = Nq[0] * du[3][0] + Nq[1] * du[3][1] + Nq[2] * du[3][2] + Nq[3] * du[3][3];
+      double f[4], g[4][3];
+      nsq_point_fg<double>(LocalCoef{pt.k}, A.elastic != 0, dv, gd, dp, dgp, A.P.alpha, A.P.c_mass, f, g);
+      for (int a = 0; a < 4; ++a)
+        for (int eq = 0; eq < 4; ++eq)
+          c[a][eq] += w * (Nq[a] * f[eq] + dN[a][0] * g[eq][0] + dN[a][1] * g[eq][1] + dN[a][2] * g[eq][2]);
+    } else {
+      // diagonal: trial = test = (corner a, equation eq)
+      for (int a = 0; a < 4; ++a)
+        for (int fq = 0; fq < 4; ++fq) {
+          double dv[3] = {0.0, 0.0, 0.0}, gd[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+          double dgp[3] = {0.0, 0.0, 0.0}, dp = 0.0;
+          if (fq < 3) {
+            dv[fq] = Nq[a];
+            for (int d = 0; d < 3; ++d) gd[fq][d] = dN[a][d];
+          } else {
+            dp = Nq[a];
+            for (int d = 0; d < 3; ++d) dgp[d] = dN[a][d];
+          }
+          double f[4], g[4][3];
+          nsq_point_fg<double>(LocalCoef{pt.k}, A.elastic != 0, dv, gd, dp, dgp, A.P.alpha, A.P.c_mass, f, g);
+          c[a][fq] += w * (Nq[a] * f[fq] + dN[a][0] * g[fq][0] + dN[a][1] * g[fq][1] + dN[a][2] * g[fq][2]);
+        }
+    }
+  }
+  for (int a = 0; a < 4; ++a)
+    for (int eq = 0; eq < 4; ++eq) A.E[(int64_t)(a * 4 + eq) * A.ne + e] = c[a][eq];
+}
+
+// node sums in element order, then the Dirichlet rows (as the hexahedral operators)
+template <int MODE>
+__global__ void __launch_bounds__(256) tet_ns_node(const int64_t* __restrict__ nptr, const int32_t* __restrict__ nlist,
+                                                   const double* __restrict__ E, int64_t ne, int64_t nn,
+                                                   const uint8_t* mask, int pin, const double* x, const double* vD,
+                                                   const double* dx, double* y) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = nptr[n]; i < nptr[n + 1]; ++i) {
+    const int32_t t = nlist[i];
+    const int64_t e = t >> 2;
+    const int a = t & 3;
+    for (int eq = 0; eq < 4; ++eq) s[eq] += E[(int64_t)(a * 4 + eq) * ne + e];
+  }
+  const uint8_t m = mask[n];
+  for (int k = 0; k < 4; ++k) {
+    double v = s[k];
+    if (((m >> k) & 1) && (k < 3 || pin)) {
+      if (MODE == 0) v = x[(int64_t)k * nn + n] - (k < 3 ? vD[(int64_t)k * nn + n] : 0.0);
+      else if (MODE == 1) v = dx[(int64_t)k * nn + n];
+      else v = 1.0;
+    }
+    y[(int64_t)k * nn + n] = v;
+  }
+}
+
+template <int MODE>
+int tet_ns_run(fsi_mesh* m, const double* dx, double* y, unsigned flags) {
+  TetData* t = m->tet;
+  TetArgs A;
+  A.conn = t->conn;
+  A.geo = t->geo;
+  A.ne = t->ne;
+  A.xa = m->staged_xa;
+  A.xd = m->xd;
+  A.mat = m->mat;
+  A.dx = dx;
+  A.E = t->E;
+  A.nn = m->nn;
+  A.elastic = (MODE == 0) ? 0 : ((flags & FSI_ELASTIC_AUG) && m->ns > 0 ? 1 : 0);
+  A.P = m->P;
+  const int cls = MODE == 0 ? P_NS_RES : (MODE == 1 ? P_NS_JVP64 : P_NS_DIAG);
+  FSI_LAUNCH(m, cls, tet_ns_elem<MODE><<<(unsigned)((t->ne + 127) / 128), 128, 0, m->stream>>>(A));
+  FSI_LAUNCH(m, cls, tet_ns_node<MODE><<<(unsigned)((m->nn + 255) / 256), 256, 0, m->stream>>>(
+                         t->nptr, t->nlist, t->E, t->ne, m->nn, m->mask, m->pin_active, m->staged_x, m->vD, dx, y));
+  return FSI_OK;
+}
+
+int tet_ns(fsi_mesh* m, int mode, const double* dx, double* y, unsigned flags) {
+  if (flags & FSI_FP32) return set_error(FSI_EINVAL, "tetrahedral meshes: float64 operators only");
+  if (mode == 0) return tet_ns_run<0>(m, dx, y, flags);
+  if (mode == 1) return tet_ns_run<1>(m, dx, y, flags);
+  return tet_ns_run<2>(m, dx, y, flags);
+}
+
+}  // namespace fsi
+
+using namespace fsi;
+
+extern "C" int fsi_create_tet_mesh(const fsi_mesh_desc* d, const double* coords, const int32_t* conn, int64_t ne,
+                                   fsi_mesh** out) {
+  if (!out) return set_error(FSI_EINVAL, "fsi_create_tet_mesh: null output");
+  *out = nullptr;
+  if (!d || !coords || !conn || ne < 1) return set_error(FSI_EINVAL, "fsi_create_tet_mesh: null argument or no elements");
+  if (ne > (int64_t)1 << 29) return set_error(FSI_EINVAL, "fsi_create_tet_mesh: at most 2^29 elements");
+  fsi_mesh* m = nullptr;
+  int rc = fsi_create_mesh(d, &m);
+  if (rc) return rc;
+  const int64_t nn = m->nn;
+  std::vector<int32_t> cn((size_t)(4 * ne));
+  std::vector<double> geo((size_t)(TG * ne));
+  std::vector<int64_t> ptr(nn + 1, 0);
+  for (int64_t e = 0; e < ne; ++e) {
+    int n[4];
+    for (int a = 0; a < 4; ++a) {
+      n[a] = conn[4 * e + a];
+      if (n[a] < 0 || n[a] >= nn) {
+        fsi_destroy_mesh(m);
+        return set_error(FSI_EINVAL, "fsi_create_tet_mesh: node index out of range");
+      }
+      cn[(size_t)(a * ne + e)] = n[a];
+      ++ptr[n[a] + 1];
+    }
+    double J[3][3];  // columns x_a - x_0
+    for (int a = 1; a < 4; ++a)
+      for (int r = 0; r < 3; ++r) J[r][a - 1] = coords[(int64_t)r * nn + n[a]] - coords[(int64_t)r * nn + n[0]];
+    const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                       J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                       J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    if (!(det > 0.0)) {
+      fsi_destroy_mesh(m);
+      return set_error(FSI_EINVAL, "fsi_create_tet_mesh: an element has non-positive volume (orientation)");
+    }
+    // inverse by cofactors: Jinv[k][j] = d xi_k / d x_j = grad(lambda_{k+1})_j
+    double Ji[3][3];
+    Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+    Ji[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+    Ji[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+    double g[4][3];
+    for (int j = 0; j < 3; ++j) {
+      g[1][j] = Ji[0][j];
+      g[2][j] = Ji[1][j];
+      g[3][j] = Ji[2][j];
+      g[0][j] = -(Ji[0][j] + Ji[1][j] + Ji[2][j]);
+    }
+    for (int a = 0; a < 4; ++a)
+      for (int j = 0; j < 3; ++j) geo[(size_t)((3 * a + j) * ne + e)] = g[a][j];
+    geo[(size_t)(12 * ne + e)] = det / 24.0;  // |T| / 4
+    const int sym[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {1, 2}, {0, 2}};
+    for (int c = 0; c < 6; ++c) {
+      double s = 0.0;
+      for (int k = 0; k < 3; ++k) s += Ji[k][sym[c][0]] * Ji[k][sym[c][1]];
+      geo[(size_t)((13 + c) * ne + e)] = s;
+    }
+  }
+  for (int64_t n = 0; n < nn; ++n) ptr[n + 1] += ptr[n];
+  std::vector<int32_t> list((size_t)ptr[nn]);
+  std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+  for (int64_t e = 0; e < ne; ++e)
+    for (int a = 0; a < 4; ++a) list[(size_t)fill[conn[4 * e + a]]++] = (int32_t)(4 * e + a);
+  auto* t = new TetData();
+  t->ne = ne;
+  m->tet = t;
+  cudaError_t err = cudaSuccess;
+  auto up = [&](void** p, const void* src, size_t bytes) {
+    if (err != cudaSuccess) return;
+    err = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    if (err == cudaSuccess && src) err = cudaMemcpy(*p, src, bytes, cudaMemcpyHostToDevice);
+  };
+  up((void**)&t->conn, cn.data(), sizeof(int32_t) * cn.size());
+  up((void**)&t->geo, geo.data(), sizeof(double) * geo.size());
+  up((void**)&t->nptr, ptr.data(), sizeof(int64_t) * ptr.size());
+  up((void**)&t->nlist, list.data(), sizeof(int32_t) * list.size());
+  up((void**)&t->E, nullptr, sizeof(double) * 16 * (size_t)ne);
+  if (err != cudaSuccess) {
+    rc = cuda_check(err, "fsi_create_tet_mesh: device arrays");
+    fsi_destroy_mesh(m);
+    return rc;
+  }
+  *out = m;
+  return FSI_OK;
+}

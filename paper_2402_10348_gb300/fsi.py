@@ -116,7 +116,7 @@ EXPORTS = ["fsi_create_mesh", "fsi_destroy_mesh", "fsi_set_stream", "fsi_mesh_in
            "fsi_batch_create", "fsi_batch_destroy", "fsi_batch_layout", "fsi_batch_jvp", "fsi_batch_gmres",
            "fsi_batch_autotune", "fsi_batch_set_graph", "fsi_center_of_mass", "fsi_track_points",
            "fsi_probe_peaks", "fsi_batch_create_blocks", "fsi_batch_stepper_create", "fsi_batch_stepper_destroy",
-           "fsi_batch_step", "fsi_last_error"]
+           "fsi_batch_step", "fsi_create_tet_mesh", "fsi_last_error"]
 
 _lib = None
 
@@ -206,6 +206,21 @@ def fsi_create_mesh(d, device: int = 0) -> Mesh:
     s, ph = make_desc(d, device)
     h = C.c_void_p()
     _check(lib().fsi_create_mesh(C.byref(s), C.byref(h)))
+    return Mesh(h, s, ph)
+
+
+def fsi_create_tet_mesh(d, coords, conn, device: int = 0) -> Mesh:
+    """A linear-tetrahedron mesh on the nodes of d's box grid: coords host float64 [3, nn],
+    conn host int [ne, 4] (positively oriented)."""
+    import numpy as np
+    s, ph = make_desc(d, device)
+    X = np.ascontiguousarray(coords, dtype=np.float64)
+    T = np.ascontiguousarray(conn, dtype=np.int32)
+    if X.shape != (3, d.nn) or T.ndim != 2 or T.shape[1] != 4:
+        raise ValueError("coords must be [3, nn] and conn [ne, 4]")
+    h = C.c_void_p()
+    _check(lib().fsi_create_tet_mesh(C.byref(s), X.ctypes.data_as(C.c_void_p), T.ctypes.data_as(C.c_void_p),
+                                     C.c_int64(T.shape[0]), C.byref(h)))
     return Mesh(h, s, ph)
 
 
