@@ -267,7 +267,7 @@ def operator_rates_of(wl, fsi, torch, dev, reps: int = 3) -> dict:
     of each block) on one workload's mesh, from a state drawn on the device (phase
     fractions a partition of unity, B near I).  Times come from the library's CUDA-event
     profiler; the NS products stream quadrature-point coefficients built once per state
-    (their build, `ns_coeffs`, is reported apart)."""
+    (their builds, `op_builds`, are reported apart)."""
     import collections
     d = wl.desc
     nn, N, ns = d.nn, d.n_phase, d.n_solid
@@ -324,9 +324,9 @@ def operator_rates_of(wl, fsi, torch, dev, reps: int = 3) -> dict:
         if ms > 0:
             ops[cls] = {"gdofs": round(dofs[cls] * k / (ms / 1e3) / 1e9, 3),
                         "us_per_apply": round(ms / k * 1e3, 2), "launches_per_apply": launches / k}
-    if prof.get("ns_coeffs", (0, 0))[0] > 0:
-        ops["ns_coeffs"] = {"us_per_build": round(prof["ns_coeffs"][1] / prof["ns_coeffs"][0] * 1e3, 2),
-                            "launches": prof["ns_coeffs"][0]}
+    if prof.get("op_builds", (0, 0))[0] > 0:
+        ops["op_builds"] = {"us_per_build": round(prof["op_builds"][1] / prof["op_builds"][0] * 1e3, 2),
+                            "launches": prof["op_builds"][0]}
     del mesh, x, xn, xdn
     torch.cuda.empty_cache()
     return {"workload": wl.name, "nodes": nn, "phases": N, "solids": ns, "dof_per_node": d.ncomp,
@@ -517,7 +517,7 @@ def flops_per_element(kernel: str, n_solid: int) -> float:
     points per element."""
     if kernel == "ns_jvp_f64_em":
         return 2.0 * 32 * 32  # the element matrix applied: 1024 FMAs per element
-    per_qp = {"ns_jvp": 486 + (114 if n_solid > 0 else 0), "ns_coeffs": 635 + 167 * n_solid,
+    per_qp = {"ns_jvp": 486 + (114 if n_solid > 0 else 0), "op_builds": 0,
               "ns_residual": 635 + 167 * n_solid, "ac_jvp": 247, "b_jvp": 892}
     for k, v in per_qp.items():
         if kernel.startswith(k):

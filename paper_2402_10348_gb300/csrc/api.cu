@@ -39,7 +39,7 @@ int ensure_smem_attr(const void* func, size_t bytes) {
 static const char* kProfNames[P_NCLS] = {
     "stage", "ns_residual", "ns_jvp_f64", "ns_jvp_f32", "ns_diag", "ac_residual", "ac_jvp_f64", "ac_jvp_f32",
     "ac_diag", "b_residual", "b_jvp_f64", "b_jvp_f32", "b_diag", "gamma_beta", "krylov_vector", "init",
-    "krylov_dot", "krylov_update", "krylov_scalar", "to_float", "pc_conv", "pc_wgrad", "pc_aux", "ns_coeffs", "ns_jvp_f64_em"};
+    "krylov_dot", "krylov_update", "krylov_scalar", "to_float", "pc_conv", "pc_wgrad", "pc_aux", "op_builds", "ns_jvp_f64_em"};
 constexpr int PROF_PAIRS = 4096;
 
 int prof_harvest(fsi_mesh* m) {
@@ -385,6 +385,7 @@ int fsi_destroy_mesh(fsi_mesh* m) {
   cudaFree(m->cq64);
   cudaFree(m->cq32);
   cudaFree(m->ke64);
+  cudaFree(m->ake64);
   tet_free(m->tet);
   if (m->kry_est) cudaFreeHost(m->kry_est);
   for (cudaEvent_t e : m->kry_ev) cudaEventDestroy(e);

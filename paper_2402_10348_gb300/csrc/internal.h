@@ -82,6 +82,12 @@ struct fsi_mesh {
   int64_t ke_gen = -1;               // cq_gen they were built from
   int64_t f64_gen = -1, f64_count = 0;  // float64 NS products applied at coefficient build f64_gen
   int64_t cq_builds = 0;             // coefficient builds so far (a new build invalidates ke64)
+  // float64 Allen-Cahn element matrices (ACEOp) of one phase at one staging
+  double* ake64 = nullptr;
+  int64_t ake_len = 0;
+  int64_t ake_gen = -1, ake_count = 0;  // staging the products were counted at / built for
+  int ake_phase = -1, ake_built = 0;
+  double ake_gamma = 0.0, ake_beta = 0.0;
   const double* staged_xa = nullptr; // the x^{n+alpha} array in use
   // coefficients
   double gamma[fsi::MAXP] = {0};
@@ -159,6 +165,8 @@ int launch_ns(fsi_mesh* m, int mode, const double* dx, double* y, unsigned flags
 int ns_build(fsi_mesh* m, unsigned flags);  // ops_f64.cu
 // float64 NS product through element matrices (built first when stale), ops_f64.cu
 int launch_nse(fsi_mesh* m, const double* dx, double* y, unsigned flags);
+// float64 Allen-Cahn product of one phase through element matrices (ops_f64.cu)
+int launch_ace(fsi_mesh* m, int phase, const double* dx, double* y);
 constexpr int NSE_AFTER = 8;  // float64 products on one coefficient build before the matrices pay
 template <typename T>
 int launch_nsq(fsi_mesh* m, const double* dx, double* y, unsigned flags);

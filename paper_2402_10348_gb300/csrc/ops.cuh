@@ -749,6 +749,120 @@ struct ACOp {
   }
 };
 
+// Float64 Allen-Cahn products through element matrices: the 8 x 8 matrix of the product of
+// Eq. PPV_AC's linearization (gamma, beta, tau_phi frozen) per element, weighted,
+//   K[b][a] = sum_q W ( N_b dR_a + khat alpha grad N_b . grad N_a + tau (v . grad N_b) dR_a ),
+//   dR_a = c_m N_a + alpha v . grad N_a + alpha gamma (3 phi^2 - 1 - beta dsqrtF) N_a,
+// layout K[((ez * 64 + b * 8 + a) * nxyp + ey * nxp + ex], built once the solve has taken
+// NSE_AFTER float64 products (64 FMAs per element and product against about 2000 flops).
+// Build fields: v(3), phi.
+struct ACEBuildOp {
+  using T = double;
+  static constexpr int NC = 1;
+  static constexpr int MINB = 1;
+  Fields F;
+  int nf;
+  Phys P;
+  double rh[3], W;
+  double gamma, beta;
+  double* K;
+  int nxp;
+  int64_t nxyp;
+
+  __device__ __forceinline__ const T* fptr(int f) const { return field_ptr<T>(F, f); }
+  using Red = NoRed;
+  __device__ __forceinline__ void begin_cta(Red&) const {}
+  __device__ __forceinline__ void end_cta(Red&) const {}
+
+  __device__ void element(const Corners<T>& cr, const ElemCtx& ec, T (&)[NC][8], Red&) const {
+    if (!ec.owned) return;
+    const double rhx = rh[0], rhy = rh[1], rhz = rh[2];
+    const double alpha = P.alpha, cm = P.c_mass, gam = gamma, bet = beta;
+    const double k_hat = gam * P.eps * P.eps, ka = k_hat * alpha;
+    const double dt2 = 4.0 / (P.dt * P.dt);
+    double Ke[8][8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+#pragma unroll
+      for (int a = 0; a < 8; ++a) Ke[b][a] = 0.0;
+    double u[8];
+#pragma unroll 1
+    for (int q = 0; q < 8; ++q) {
+      QW<double> w;
+      w.set(q);
+      double v[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { cr.get(k, u); v[k] = interp_v(u, w); }
+      cr.get(3, u);
+      const double phi = interp_v(u, w);
+      const double vGv = P.Gd[0] * v[0] * v[0] + P.Gd[1] * v[1] * v[1] + P.Gd[2] * v[2] * v[2];
+      const double s_hat = gam * (3.0 * phi * phi - 1.0);
+      const double tau = 1.0 / sqrt(dt2 + vGv + 9.0 * k_hat * k_hat * P.GG + s_hat * s_hat);
+      const double p2 = phi * phi - 1.0;
+      const double dsF = p2 > 0.0 ? phi : (p2 < 0.0 ? -phi : 0.0);
+      const double rp = gam * (3.0 * phi * phi - 1.0 - bet * dsF);
+      double N[8], gN[8][3], vgN[8], dR[8];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
+        N[a] = w.wx[ax] * w.wy[ay] * w.wz[az];
+        gN[a][0] = (ax ? 1.0 : -1.0) * rhx * w.wy[ay] * w.wz[az];
+        gN[a][1] = (ay ? 1.0 : -1.0) * rhy * w.wx[ax] * w.wz[az];
+        gN[a][2] = (az ? 1.0 : -1.0) * rhz * w.wx[ax] * w.wy[ay];
+        vgN[a] = v[0] * gN[a][0] + v[1] * gN[a][1] + v[2] * gN[a][2];
+        dR[a] = cm * N[a] + alpha * vgN[a] + alpha * rp * N[a];
+      }
+#pragma unroll
+      for (int b = 0; b < 8; ++b)
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+          Ke[b][a] += W * (N[b] * dR[a] + ka * (gN[b][0] * gN[a][0] + gN[b][1] * gN[a][1] + gN[b][2] * gN[a][2]) +
+                           tau * vgN[b] * dR[a]);
+    }
+    double* out = K + (int64_t)ec.ez * 64 * nxyp + (int64_t)ec.ey * nxp + ec.ex;
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+#pragma unroll
+      for (int a = 0; a < 8; ++a) out[(int64_t)(b * 8 + a) * nxyp] = Ke[b][a];
+  }
+  __device__ __forceinline__ void finish(const NodeCtx&, const T (&)[NC], Red&) const {}
+};
+
+// Product: field dphi.
+struct ACEOp {
+  using T = double;
+  static constexpr int NC = 1;
+  static constexpr int MINB = 1;
+  Fields F;
+  int nf;
+  const double* K;
+  int nxp;
+  int64_t nxyp;
+  OutDesc out;
+  int64_t nn_;
+
+  __device__ __forceinline__ const T* fptr(int f) const { return field_ptr<T>(F, f); }
+  using Red = NoRed;
+  __device__ __forceinline__ void begin_cta(Red&) const {}
+  __device__ __forceinline__ void end_cta(Red&) const {}
+
+  __device__ void element(const Corners<T>& cr, const ElemCtx& ec, T (&c)[NC][8], Red&) const {
+    T x[8];
+    cr.get(0, x);
+    const double* k = K + (int64_t)ec.ez * 64 * nxyp + (int64_t)ec.ey * nxp + ec.ex;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      T acc = 0.0;
+#pragma unroll
+      for (int a = 0; a < 8; ++a) acc += __ldg(k + (int64_t)(b * 8 + a) * nxyp) * x[a];
+      c[0][b] = acc;
+    }
+  }
+  __device__ __forceinline__ void finish(const NodeCtx& nc, const T (&acc)[NC], Red&) const {
+    out.y[nc.n] = acc[0];
+  }
+};
+
 // ----------------------------------------------------------------- B block
 // fields: [dB(6) (JVP)], v(3), alpha^s, B(6), dB/dt(6)
 template <typename TT, int MODE>

@@ -111,6 +111,49 @@ __global__ void __launch_bounds__(256) nse_build_kernel(const double* __restrict
   for (int i = 0; i < 32; ++i) out[(int64_t)i * 32 * nxyp] = c[i >> 3][i & 7];
 }
 
+int launch_ace(fsi_mesh* m, int phase, const double* dx, double* y) {
+  const int nxp = cq_pitch(m);
+  const int64_t nxyp = (int64_t)nxp * m->g.ny;
+  const int64_t nn = m->nn;
+  if (!m->ake_built) {
+    const int64_t len = (int64_t)m->g.nz * 64 * nxyp;
+    if (m->ake_len < len) {
+      cudaFree(m->ake64);
+      m->ake64 = nullptr;
+      m->ake_len = 0;
+      FSI_CUDA(cudaMalloc(&m->ake64, sizeof(double) * (size_t)len));
+      m->ake_len = len;
+    }
+    ACEBuildOp b;
+    memset(&b, 0, sizeof(b));
+    const double* xa = m->staged_xa;
+    for (int k = 0; k < 3; ++k) put<double>(b.F, k, xa + k * nn);
+    put<double>(b.F, 3, xa + (4 + phase) * nn);
+    b.nf = 4;
+    b.P = m->P;
+    fill_common(m, b.rh, &b.W);
+    b.gamma = m->gamma[phase];
+    b.beta = m->beta[phase];
+    b.K = m->ake64;
+    b.nxp = nxp;
+    b.nxyp = nxyp;
+    if (int rc = run_tile(m, b, P_NS_BUILD)) return rc;
+    m->ake_built = 1;
+  }
+  ACEOp op;
+  memset(&op, 0, sizeof(op));
+  put<double>(op.F, 0, dx);
+  op.nf = 1;
+  op.K = m->ake64;
+  op.nxp = nxp;
+  op.nxyp = nxyp;
+  op.out.y = y;
+  op.nn_ = nn;
+  const int64_t ne = (int64_t)m->g.nx * m->g.ny * m->g.nz;
+  prof_bytes(m, P_AC_JVP64, (double)ne * 64 * 8.0 + (double)nn * 16.0);
+  return run_tile(m, op, P_AC_JVP64);
+}
+
 int launch_nse(fsi_mesh* m, const double* dx, double* y, unsigned flags) {
   const int nxp = cq_pitch(m);
   const int64_t nxyp = (int64_t)nxp * m->g.ny;

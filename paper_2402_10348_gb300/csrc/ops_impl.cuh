@@ -249,6 +249,22 @@ int ac_run(fsi_mesh* m, int i, const double* dx, double* y) {
 
 template <typename T>
 int launch_ac(fsi_mesh* m, int mode, int i, const double* dx, double* y) {
+  if constexpr (sizeof(T) == 8) {
+    // a float64 solve of this phase at this staging: after NSE_AFTER products switch to the
+    // element matrices (not for recorded batched launches)
+    if (mode == 1 && !m->rec) {
+      if (m->ake_gen != m->stage_gen || m->ake_phase != i || m->ake_gamma != m->gamma[i] ||
+          m->ake_beta != m->beta[i]) {
+        m->ake_gen = m->stage_gen;
+        m->ake_phase = i;
+        m->ake_gamma = m->gamma[i];
+        m->ake_beta = m->beta[i];
+        m->ake_count = 0;
+        m->ake_built = 0;
+      }
+      if (++m->ake_count > NSE_AFTER) return launch_ace(m, i, dx, y);
+    }
+  }
   if (mode == 0) return ac_run<T, 0>(m, i, dx, y);
   if (mode == 1) return ac_run<T, 1>(m, i, dx, y);
   return ac_run<T, 2>(m, i, dx, y);
