@@ -156,11 +156,12 @@ def run_pcnet_case(applies: int = 20, train_steps: int = 20):
     print(json.dumps(out), flush=True)
 
 
-def run_batch_case(count: int = 64, reps: int = 5):
+def run_batch_case(count: int = 64, reps: int = 5, steps: int = 3):
     """64 independent cavities of uneven size (16^3 .. 48^3): the float32 NS operator
     applied to all of them in one persistent launch against one launch per instance,
     and the NS solve (Jacobi GMRES(64), float32 operator in float64 refinement, rel-res
-    1e-8) batched with a captured restart cycle against one fsi_gmres per instance."""
+    1e-8) batched with a captured restart cycle against one fsi_gmres per instance; then
+    `steps` partitioned time steps of all instances, batched against per instance."""
     import torch
     from paper_2402_10348_gb300 import fsi
     from workloads import cavity_batch
@@ -259,7 +260,48 @@ def run_batch_case(count: int = 64, reps: int = 5):
                           "batched_gdofs": round(dof / ms_batch / 1e6, 3), "speedup": round(ms_single / ms_batch, 3),
                           "launches_per_instance_arm": count, "launches_batched": 2},
            "ns_solve_fp32ir_rtol1e-8": res, "max_solution_difference": diff}
+    out["time_steps"] = batch_steps(fsi, torch, dev, wls, meshes, stream, steps)
     print(json.dumps(out), flush=True)
+
+
+def batch_steps(fsi, torch, dev, wls, meshes, stream, steps):
+    """Partitioned time steps of every instance (float32 operators in float64 refinement,
+    Jacobi GMRES(30) to rel-res 1e-8 in every block): one fsi_batch_step per step
+    (a batched solve per block kind and nonlinear iteration) against one fsi_step per
+    instance and step, from the same initial states."""
+    opts = fsi.solve_opts(m=30, rtol=1e-8, max_iter=6000, precision=fsi.FSI_PREC_FP32_IR, ir_inner_rtol=1e-3,
+                          ir_max=30)
+    arms = {}
+    finals = {}
+    for arm in ("per_instance", "batched"):
+        with torch.cuda.stream(stream):
+            sts = [list(initial_state(fsi, m, wl, torch, dev)) for m, wl in zip(meshes, wls)]
+        torch.cuda.synchronize()
+        stepper = fsi.fsi_batch_stepper_create(meshes, m=30) if arm == "batched" else None
+        t0 = time.perf_counter()
+        nl, worst, stalled = [], 0.0, 0
+        with torch.cuda.stream(stream):
+            for _ in range(steps):
+                if stepper is not None:
+                    infos = fsi.fsi_batch_step(stepper, sts, k_max=5, nl_tol=5e-4, solve=opts)
+                else:
+                    infos = [fsi.fsi_step(m, *st, k_max=5, nl_tol=5e-4, solve=opts) for m, st in zip(meshes, sts)]
+                nl.append(max(i.nl_iters for i in infos))
+                worst = max(worst, max(i.worst_rel_res for i in infos))
+                stalled += sum(i.stalled_solves for i in infos)
+            torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        arms[arm] = {"s_per_step_all_instances": round(dt / steps, 4), "max_nl_iters": nl,
+                     "worst_rel_res": worst, "stalled_solves": stalled}
+        finals[arm] = [st[1] for st in sts]
+        del stepper
+    diff = max(float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+               for a, b in zip(finals["batched"], finals["per_instance"]))
+    arms["steps"] = steps
+    arms["speedup"] = round(arms["per_instance"]["s_per_step_all_instances"] /
+                            arms["batched"]["s_per_step_all_instances"], 3)
+    arms["max_state_difference"] = diff
+    return arms
 
 
 def operator_rates_of(wl, fsi, torch, dev, reps: int = 3) -> dict:
@@ -1050,7 +1092,7 @@ def main():
     elif args.case == "pcnet":
         run_pcnet_case()
     elif args.case == "batch":
-        run_batch_case()
+        run_batch_case(steps=args.steps if "--steps" in sys.argv else 3)
     elif args.case == "mixed":
         run_mixed_case(args.steps if "--steps" in sys.argv else 100)
     elif args.case == "operators":

@@ -385,6 +385,7 @@ int fsi_destroy_mesh(fsi_mesh* m) {
   cudaFree(m->cq64);
   cudaFree(m->cq32);
   cudaFree(m->ke64);
+  cudaFree(m->ke_e);
   cudaFree(m->ake64);
   tet_free(m->tet);
   if (m->kry_est) cudaFreeHost(m->kry_est);

@@ -79,6 +79,8 @@ struct fsi_mesh {
   // a state has taken NSE_AFTER float64 products
   double* ke64 = nullptr;
   int64_t ke_len = 0;
+  double* ke_e = nullptr;            // [32][elements] element products of the matrix form
+  int64_t ke_e_len = 0;
   int64_t ke_gen = -1;               // cq_gen they were built from
   int64_t f64_gen = -1, f64_count = 0;  // float64 NS products applied at coefficient build f64_gen
   int64_t cq_builds = 0;             // coefficient builds so far (a new build invalidates ke64)

@@ -549,7 +549,7 @@ template <typename TT>
 struct NSQOp {
   using T = TT;
   static constexpr int NC = 4;
-  static constexpr int MINB = MinBlocks<TT>::value;
+  static constexpr int MINB = sizeof(TT) == 4 ? 2 : 1;  // float32: two CTAs per SM (latency)
   Fields F;
   int nf;
   const T* cq;   // coefficients of the compute type
@@ -615,56 +615,6 @@ struct NSQOp {
 // both forms are the same operator up to summation order.
 constexpr int NKE = 32 * 32;
 
-// Product: fields dv(3), dp of the increment (float64).
-struct NSEOp {
-  using T = double;
-  static constexpr int NC = 4;
-  static constexpr int MINB = 1;
-  Fields F;
-  int nf;
-  const double* K;
-  int nxp;
-  int64_t nxyp;
-  double W;
-  OutDesc out;
-  int64_t nn_;
-
-  __device__ __forceinline__ const T* fptr(int f) const { return field_ptr<T>(F, f); }
-  using Red = NoRed;
-  __device__ __forceinline__ void begin_cta(Red&) const {}
-  __device__ __forceinline__ void end_cta(Red&) const {}
-
-  __device__ void element(const Corners<T>& cr, const ElemCtx& ec, T (&c)[NC][8], Red&) const {
-    T x[32];
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      T u[8];
-      cr.get(f, u);
-#pragma unroll
-      for (int a = 0; a < 8; ++a) x[8 * f + a] = u[a];
-    }
-    const double* k = K + (int64_t)ec.ez * NKE * nxyp + (int64_t)ec.ey * nxp + ec.ex;
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      const double* row = k + (int64_t)i * 32 * nxyp;
-      T acc = 0.0;
-#pragma unroll
-      for (int jj = 0; jj < 32; ++jj) acc += __ldg(row + jj * nxyp) * x[jj];
-      c[i >> 3][i & 7] = acc;
-    }
-  }
-
-  __device__ __forceinline__ void finish(const NodeCtx& nc, const T (&acc)[NC], Red&) const {
-    const int64_t nn = nn_;
-    const uint8_t m = out.mask ? out.mask[nc.n] : 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      double* y = out.y + (int64_t)k * nn + nc.n;
-      if (((m >> k) & 1) && (k < 3 || out.pin)) *y = out.dx[(int64_t)k * nn + nc.n];
-      else *y = W * acc[k];
-    }
-  }
-};
 
 // ----------------------------------------------------------------- AC block
 // fields: [dphi (JVP)], v(3), phi, dphi/dt

@@ -154,6 +154,73 @@ int launch_ace(fsi_mesh* m, int phase, const double* dx, double* y) {
   return run_tile(m, op, P_AC_JVP64);
 }
 
+// Product with element matrices, element-centric: one thread per element (x fastest)
+// gathers its 32 increment values, applies its matrix and writes the 32 products into
+// E[i][element] (each element evaluated once: no halo recomputation); one thread per node
+// then sums the slots of its up to 8 elements in a fixed order (z, y, x) and applies the
+// Dirichlet rows (deterministic, no atomics).
+__global__ void __launch_bounds__(256) nse_elem_kernel(const double* __restrict__ K, const double* __restrict__ dx,
+                                                       double* __restrict__ E, int nx, int ny, int nz, int nxp,
+                                                       int64_t nxyp, int64_t nn) {
+  const int ex = blockIdx.x * blockDim.x + threadIdx.x;
+  const int eyz = blockIdx.y;
+  const int ey = eyz % ny, ez = eyz / ny;
+  if (ex >= nx || ez >= nz) return;
+  const int64_t sx = 1, sy = nx + 1, sz = (int64_t)(nx + 1) * (ny + 1);
+  const int64_t n0 = ex + sy * ey + sz * ez;
+  const int64_t off[8] = {0, sx, sy, sx + sy, sz, sz + sx, sz + sy, sz + sx + sy};
+  double x[32];
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+#pragma unroll
+    for (int a = 0; a < 8; ++a) x[8 * f + a] = __ldg(dx + f * nn + n0 + off[a]);
+  const int64_t e = (int64_t)ez * nxyp + (int64_t)ey * nxp + ex;
+  const double* k = K + (int64_t)ez * NKE * nxyp + (int64_t)ey * nxp + ex;
+  const int64_t es = (int64_t)nz * nxyp;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const double* row = k + (int64_t)i * 32 * nxyp;
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc += __ldg(row + j * nxyp) * x[j];
+    E[i * es + e] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(256) nse_node_kernel(const double* __restrict__ E, int nx, int ny, int nz, int nxp,
+                                                       int64_t nxyp, int64_t nn, double W, const uint8_t* mask,
+                                                       int pin, const double* __restrict__ dx, double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int jk = blockIdx.y;
+  const int j = jk % (ny + 1), k = jk / (ny + 1);
+  if (i > nx || k > nz) return;
+  const int64_t n = i + (int64_t)(nx + 1) * (j + (int64_t)(ny + 1) * k);
+  const int64_t es = (int64_t)nz * nxyp;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int az = 1; az >= 0; --az) {
+    const int ez = k - az;
+    if (ez < 0 || ez >= nz) continue;
+    for (int ay = 1; ay >= 0; --ay) {
+      const int ey = j - ay;
+      if (ey < 0 || ey >= ny) continue;
+      for (int ax = 1; ax >= 0; --ax) {
+        const int ex = i - ax;
+        if (ex < 0 || ex >= nx) continue;
+        const int64_t e = (int64_t)ez * nxyp + (int64_t)ey * nxp + ex;
+        const int a = ax + 2 * ay + 4 * az;  // this node's corner in element (ex, ey, ez)
+#pragma unroll
+        for (int f = 0; f < 4; ++f) s[f] += E[(8 * f + a) * es + e];
+      }
+    }
+  }
+  const uint8_t mk = mask[n];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const bool dir = ((mk >> f) & 1) && (f < 3 || pin);
+    y[f * nn + n] = dir ? dx[f * nn + n] : W * s[f];
+  }
+}
+
 int launch_nse(fsi_mesh* m, const double* dx, double* y, unsigned flags) {
   const int nxp = cq_pitch(m);
   const int64_t nxyp = (int64_t)nxp * m->g.ny;
@@ -174,24 +241,28 @@ int launch_nse(fsi_mesh* m, const double* dx, double* y, unsigned flags) {
                                                                      1.0 / m->g.hx, 1.0 / m->g.hy, 1.0 / m->g.hz));
     m->ke_gen = m->cq_builds;
   }
-  NSEOp op;
-  memset(&op, 0, sizeof(op));
   const int64_t nn = m->nn;
-  for (int k = 0; k < 4; ++k) put<double>(op.F, k, dx + k * nn);
-  op.nf = 4;
-  op.K = m->ke64;
-  op.nxp = nxp;
-  op.nxyp = nxyp;
-  op.W = m->g.hx * m->g.hy * m->g.hz / 8.0;
-  op.out.y = y;
-  op.out.dx = dx;
-  op.out.mask = m->mask;
-  op.out.dirichlet = 1;
-  op.out.pin = m->pin_active;
-  op.nn_ = nn;
-  const int64_t ne = (int64_t)m->g.nx * m->g.ny * m->g.nz;
+  const int64_t elen = 32 * (int64_t)m->g.nz * nxyp;
+  if (m->ke_e_len < elen) {
+    cudaFree(m->ke_e);
+    m->ke_e = nullptr;
+    m->ke_e_len = 0;
+    FSI_CUDA(cudaMalloc(&m->ke_e, sizeof(double) * (size_t)elen));
+    m->ke_e_len = elen;
+  }
+  const Geom& g = m->g;
+  const int64_t ne = (int64_t)g.nx * g.ny * g.nz;
+  // algorithmic bytes: the matrices once, the increment read and the product written once
+  // per node, the mask (the element products' round trip through E is not counted)
   prof_bytes(m, P_NS_JVP64E, (double)ne * NKE * 8.0 + (double)nn * (4.0 * 8.0 + 32.0 + 1.0));
-  return run_tile(m, op, P_NS_JVP64E);
+  FSI_LAUNCH(m, P_NS_JVP64E,
+             nse_elem_kernel<<<dim3((g.nx + 127) / 128, (unsigned)((int64_t)g.ny * g.nz)), 128, 0, m->stream>>>(
+                 m->ke64, dx, m->ke_e, g.nx, g.ny, g.nz, nxp, nxyp, nn));
+  FSI_LAUNCH(m, P_NS_JVP64E,
+             nse_node_kernel<<<dim3((g.nx + 1 + 127) / 128, (unsigned)((int64_t)(g.ny + 1) * (g.nz + 1))), 128, 0,
+                               m->stream>>>(m->ke_e, g.nx, g.ny, g.nz, nxp, nxyp, nn, g.hx * g.hy * g.hz / 8.0,
+                                            m->mask, m->pin_active, dx, y));
+  return FSI_OK;
 }
 template int launch_ac<double>(fsi_mesh*, int, int, const double*, double*);
 template int launch_b<double>(fsi_mesh*, int, int, const double*, double*);
@@ -214,6 +285,7 @@ __global__ void coef_finalize(const double* partials, int64_t n, double eta, dou
 }
 
 int op_coeffs(fsi_mesh* m, int i, double* gb) {
+  static_assert(CoefOp::MINB == 1, "the partial sums are sized for the mesh's own tile grid");
   CoefOp op;
   memset(&op, 0, sizeof(op));
   const int64_t nn = m->nn;

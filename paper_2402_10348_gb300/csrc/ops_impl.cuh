@@ -74,14 +74,28 @@ int launch_batched(fsi_batch* b, const void* ops_dev, size_t smem, int cls, int 
                                  reinterpret_cast<const void*>(&tile_batch_kernel<Op>));
 }
 
+// z-chunking of the tile grid for about `per_sm` x 152 CTAs (the mesh's own geometry
+// targets one CTA per SM; operators that fit more CTAs per SM get shorter z-ranges)
+inline Geom tile_geom(const fsi_mesh* m, int per_sm, dim3* grid) {
+  Geom g = m->g;
+  if (per_sm > 1) {
+    const int cols = g.ncx * g.ncy;
+    const int planes = g.nz + 1;
+    const int chunks = std::max(1, std::min(planes, (152 * per_sm + cols / 2) / cols));
+    g.zc = (planes + chunks - 1) / chunks;
+  }
+  *grid = dim3(g.ncx, g.ncy, (g.nz + 1 + g.zc - 1) / g.zc);
+  return g;
+}
+
 template <class Op>
 int run_tile(fsi_mesh* m, const Op& op, int cls) {
   if (m->rec) return record_op(m->rec, op, cls);
   const size_t smem = tile_smem_bytes<Op>(op.nf);
   if (int rc = ensure_smem_attr(reinterpret_cast<const void*>(&tile_kernel<Op>), smem)) return rc;
   dim3 grid;
-  tile_grid(m, &grid);
-  FSI_LAUNCH(m, cls, tile_kernel<Op><<<grid, NTHREADS, smem, m->stream>>>(op, m->g));
+  const Geom g = tile_geom(m, Op::MINB, &grid);
+  FSI_LAUNCH(m, cls, tile_kernel<Op><<<grid, NTHREADS, smem, m->stream>>>(op, g));
   return FSI_OK;
 }
 
