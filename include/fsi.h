@@ -469,7 +469,7 @@ int fsi_batch_step(fsi_batch_stepper* stepper, fsi_state* states, const fsi_step
  * launches.  Allocates and frees 4 GiB of device memory; synchronises the device. */
 int fsi_probe_peaks(double* fp32_tflops, double* fp64_tflops, double* read_gbs, double* copy_gbs);
 
-#define FSI_PROF_CLASSES 25
+#define FSI_PROF_CLASSES 26
 typedef struct {
   char name[24];
   int64_t launches;

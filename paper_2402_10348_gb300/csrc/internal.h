@@ -19,7 +19,7 @@ namespace fsi {
 enum ProfClass {
   P_STAGE, P_NS_RES, P_NS_JVP64, P_NS_JVP32, P_NS_DIAG, P_AC_RES, P_AC_JVP64, P_AC_JVP32,
   P_AC_DIAG, P_B_RES, P_B_JVP64, P_B_JVP32, P_B_DIAG, P_COEF, P_KRYLOV, P_INIT, P_KRY_DOT, P_KRY_UPD,
-  P_KRY_SMALL, P_KRY_CONV, P_PC_CONV, P_PC_WGRAD, P_PC_AUX, P_NS_BUILD, P_NS_JVP64E, P_NCLS
+  P_KRY_SMALL, P_KRY_CONV, P_PC_CONV, P_PC_WGRAD, P_PC_AUX, P_NS_BUILD, P_NS_JVP64E, P_NS_NODE, P_NCLS
 };
 struct Profiler {
   bool on = false;

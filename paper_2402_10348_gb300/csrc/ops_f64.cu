@@ -252,13 +252,15 @@ int launch_nse(fsi_mesh* m, const double* dx, double* y, unsigned flags) {
   }
   const Geom& g = m->g;
   const int64_t ne = (int64_t)g.nx * g.ny * g.nz;
-  // algorithmic bytes: the matrices once, the increment read and the product written once
-  // per node, the mask (the element products' round trip through E is not counted)
-  prof_bytes(m, P_NS_JVP64E, (double)ne * NKE * 8.0 + (double)nn * (4.0 * 8.0 + 32.0 + 1.0));
+  // algorithmic bytes: the element kernel reads the matrices once and the increment once per
+  // node and writes the 32 element products; the node kernel reads those back and writes
+  // the product and reads the mask once per node
+  prof_bytes(m, P_NS_JVP64E, (double)ne * (NKE * 8.0 + 32 * 8.0) + (double)nn * 32.0);
+  prof_bytes(m, P_NS_NODE, (double)ne * 32 * 8.0 + (double)nn * (32.0 + 1.0));
   FSI_LAUNCH(m, P_NS_JVP64E,
              nse_elem_kernel<<<dim3((g.nx + 127) / 128, (unsigned)((int64_t)g.ny * g.nz)), 128, 0, m->stream>>>(
                  m->ke64, dx, m->ke_e, g.nx, g.ny, g.nz, nxp, nxyp, nn));
-  FSI_LAUNCH(m, P_NS_JVP64E,
+  FSI_LAUNCH(m, P_NS_NODE,
              nse_node_kernel<<<dim3((g.nx + 1 + 127) / 128, (unsigned)((int64_t)(g.ny + 1) * (g.nz + 1))), 128, 0,
                                m->stream>>>(m->ke_e, g.nx, g.ny, g.nz, nxp, nxyp, nn, g.hx * g.hy * g.hz / 8.0,
                                             m->mask, m->pin_active, dx, y));

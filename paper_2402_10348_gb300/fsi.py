@@ -104,7 +104,7 @@ class fsi_profile_entry(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("ms", C.c_double), ("bytes", C.c_double)]
 
 
-FSI_PROF_CLASSES = 25
+FSI_PROF_CLASSES = 26
 
 EXPORTS = ["fsi_create_mesh", "fsi_destroy_mesh", "fsi_set_stream", "fsi_mesh_info", "fsi_residual",
            "fsi_jvp", "fsi_diag", "fsi_update_ac_coeffs", "fsi_set_ac_coeffs", "fsi_fix_gamma",
