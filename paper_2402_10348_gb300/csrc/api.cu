@@ -387,6 +387,7 @@ int fsi_destroy_mesh(fsi_mesh* m) {
   cudaFree(m->ke64);
   cudaFree(m->ke_e);
   cudaFree(m->ake64);
+  cudaFree(m->bke64);
   tet_free(m->tet);
   if (m->kry_est) cudaFreeHost(m->kry_est);
   for (cudaEvent_t e : m->kry_ev) cudaEventDestroy(e);

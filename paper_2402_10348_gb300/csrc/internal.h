@@ -90,6 +90,11 @@ struct fsi_mesh {
   int64_t ake_gen = -1, ake_count = 0;  // staging the products were counted at / built for
   int ake_phase = -1, ake_built = 0;
   double ake_gamma = 0.0, ake_beta = 0.0;
+  // float64 B split operators (BEOp) of one solid at one staging
+  double* bke64 = nullptr;
+  int64_t bke_len = 0;
+  int64_t bke_gen = -1, bke_count = 0;
+  int bke_solid = -1, bke_built = 0;
   const double* staged_xa = nullptr; // the x^{n+alpha} array in use
   // coefficients
   double gamma[fsi::MAXP] = {0};
@@ -169,6 +174,8 @@ int ns_build(fsi_mesh* m, unsigned flags);  // ops_f64.cu
 int launch_nse(fsi_mesh* m, const double* dx, double* y, unsigned flags);
 // float64 Allen-Cahn product of one phase through element matrices (ops_f64.cu)
 int launch_ace(fsi_mesh* m, int phase, const double* dx, double* y);
+// float64 B product of one solid through the split operator (ops_f64.cu)
+int launch_be(fsi_mesh* m, int solid, const double* dx, double* y);
 constexpr int NSE_AFTER = 8;  // float64 products on one coefficient build before the matrices pay
 template <typename T>
 int launch_nsq(fsi_mesh* m, const double* dx, double* y, unsigned flags);

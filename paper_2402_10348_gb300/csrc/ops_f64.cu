@@ -221,6 +221,47 @@ __global__ void __launch_bounds__(256) nse_node_kernel(const double* __restrict_
   }
 }
 
+int launch_be(fsi_mesh* m, int solid, const double* dx, double* y) {
+  const int nxp = cq_pitch(m);
+  const int64_t nxyp = (int64_t)nxp * m->g.ny;
+  const int64_t nn = m->nn;
+  if (!m->bke_built) {
+    const int64_t len = (int64_t)m->g.nz * NBK * nxyp;
+    if (m->bke_len < len) {
+      cudaFree(m->bke64);
+      m->bke64 = nullptr;
+      m->bke_len = 0;
+      FSI_CUDA(cudaMalloc(&m->bke64, sizeof(double) * (size_t)len));
+      m->bke_len = len;
+    }
+    BEBuildOp b;
+    memset(&b, 0, sizeof(b));
+    const double* xa = m->staged_xa;
+    for (int k = 0; k < 3; ++k) put<double>(b.F, k, xa + k * nn);
+    put<double>(b.F, 3, m->mat + (2 + solid) * nn);
+    b.nf = 4;
+    b.P = m->P;
+    fill_common(m, b.rh, &b.W);
+    b.K = m->bke64;
+    b.nxp = nxp;
+    b.nxyp = nxyp;
+    if (int rc = run_tile(m, b, P_NS_BUILD)) return rc;
+    m->bke_built = 1;
+  }
+  BEOp op;
+  memset(&op, 0, sizeof(op));
+  for (int c = 0; c < 6; ++c) put<double>(op.F, c, dx + c * nn);
+  op.nf = 6;
+  op.K = m->bke64;
+  op.nxp = nxp;
+  op.nxyp = nxyp;
+  op.out.y = y;
+  op.nn_ = nn;
+  const int64_t ne = (int64_t)m->g.nx * m->g.ny * m->g.nz;
+  prof_bytes(m, P_B_JVP64, (double)ne * NBK * 8.0 + (double)nn * 96.0);
+  return run_tile(m, op, P_B_JVP64);
+}
+
 int launch_nse(fsi_mesh* m, const double* dx, double* y, unsigned flags) {
   const int nxp = cq_pitch(m);
   const int64_t nxyp = (int64_t)nxp * m->g.ny;
