@@ -149,10 +149,10 @@ int fsi_fix_gamma(fsi_mesh* mesh, int32_t phase, double gamma);
  * positively oriented (det(x1-x0, x2-x0, x3-x0) > 0), forming a conforming mesh.
  * Geometry (barycentric gradients, volumes, the stabilisation metric G = sum_k
  * grad(xi_k) grad(xi_k)^T) and the node-to-element lists are built here; the caller's
- * arrays are not kept.  Such a mesh carries the float64 NS residual, product, diagonal
- * and GMRES (fsi_residual, fsi_jvp, fsi_diag, fsi_gmres with FSI_BLOCK_NS); the other
- * calls return FSI_EINVAL on it.  Errors: FSI_EINVAL for an index out of range or an
- * element of non-positive volume. */
+ * arrays are not kept.  Such a mesh carries every block's float64 residual, product and
+ * diagonal, gamma and beta, GMRES and fsi_step (float64; FSI_FP32 and FSI_PREC_FP32_IR
+ * return FSI_EINVAL); fsi_init_phases, the diagnostics and batches refuse it.  Errors:
+ * FSI_EINVAL for an index out of range or an element of non-positive volume. */
 int fsi_create_tet_mesh(const fsi_mesh_desc* desc, const double* coords, const int32_t* conn, int64_t ne,
                         fsi_mesh** out);
 

@@ -166,17 +166,17 @@ int block_info(const fsi_mesh* m, int32_t block, BlockInfo* bi) {
   return set_error(FSI_EINVAL, "invalid block id");
 }
 
-static int tet_only_ns(const fsi_mesh* m, const BlockInfo& b) {
-  if (m->tet && b.kind != 0)
-    return set_error(FSI_EINVAL, "tetrahedral meshes carry the momentum/continuity operators only");
-  return FSI_OK;
+// the tetrahedral kernels of a block (tet.cu)
+static int tet_op(fsi_mesh* m, const BlockInfo& b, int mode, const double* dx, double* y, unsigned flags) {
+  if (b.kind == 0) return tet_ns(m, mode, dx, y, flags);
+  if (b.kind == 1) return tet_ac(m, mode, b.index, dx, y, flags);
+  return tet_b(m, mode, b.index, dx, y, flags);
 }
 
 int op_residual(fsi_mesh* m, const BlockInfo& b, double* r) {
-  if (int rc = tet_only_ns(m, b)) return rc;
   m->applies++;
   m->dof_applied += b.n;
-  if (m->tet) return tet_ns(m, 0, nullptr, r, 0);
+  if (m->tet) return tet_op(m, b, 0, nullptr, r, 0);
   if (b.kind == 0) return launch_ns<double>(m, 0, nullptr, r, 0);
   if (b.kind == 1) return launch_ac<double>(m, 0, b.index, nullptr, r);
   return launch_b<double>(m, 0, b.index, nullptr, r);
@@ -193,10 +193,9 @@ int ensure_dx32(fsi_mesh* m) {
 }
 
 int op_jvp(fsi_mesh* m, const BlockInfo& b, const double* dx, double* y, unsigned flags) {
-  if (int rc = tet_only_ns(m, b)) return rc;
   m->applies++;
   m->dof_applied += b.n;
-  if (m->tet) return tet_ns(m, 1, dx, y, flags & ~OP_DX32_READY);
+  if (m->tet) return tet_op(m, b, 1, dx, y, flags & ~OP_DX32_READY);
   const bool f32 = flags & FSI_FP32;
   if (f32) {  // float copy of the increment for the float32 kernels (unless the caller wrote it)
     if (int rc = ensure_dx32(m)) return rc;
@@ -216,8 +215,7 @@ int op_jvp(fsi_mesh* m, const BlockInfo& b, const double* dx, double* y, unsigne
 }
 
 int op_diag(fsi_mesh* m, const BlockInfo& b, double* d, unsigned flags) {
-  if (int rc = tet_only_ns(m, b)) return rc;
-  if (m->tet) return tet_ns(m, 2, nullptr, d, flags);
+  if (m->tet) return tet_op(m, b, 2, nullptr, d, flags);
   const bool f32 = flags & FSI_FP32;
   if (b.kind == 0)
     return f32 ? launch_ns<float>(m, 2, nullptr, d, flags) : launch_ns<double>(m, 2, nullptr, d, flags);
@@ -475,7 +473,6 @@ int fsi_diag(fsi_mesh* m, int32_t block, const fsi_state* st, double* d, uint32_
 }
 
 int fsi_update_ac_coeffs(fsi_mesh* m, int32_t phase, const fsi_state* st, double* out) {
-  if (m && m->tet) return set_error(FSI_EINVAL, "fsi_update_ac_coeffs: not on tetrahedral meshes");
   if (!m || phase < 0 || phase >= (m ? m->N : 0)) return set_error(FSI_EINVAL, "fsi_update_ac_coeffs: bad phase");
   int rc = stage(m, st, false);
   if (rc) return rc;

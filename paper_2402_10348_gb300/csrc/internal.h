@@ -196,8 +196,11 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& b, const double* rhs, double* x, c
 // tile launch geometry
 void tile_grid(const fsi_mesh* m, dim3* grid);
 
-// linear tetrahedra (tet.cu): NS residual (mode 0), product (1), diagonal (2)
+// linear tetrahedra (tet.cu): residual (mode 0), product (1), diagonal (2) of each block
 int tet_ns(fsi_mesh* m, int mode, const double* dx, double* y, unsigned flags);
+int tet_ac(fsi_mesh* m, int mode, int phase, const double* dx, double* y, unsigned flags);
+int tet_b(fsi_mesh* m, int mode, int solid, const double* dx, double* y, unsigned flags);
+int tet_coeffs(fsi_mesh* m, int phase, double* gamma_beta);  // synchronises
 void tet_free(TetData* t);
 
 // time-step pieces (step.cu): predictor and corrector launches, the pressure shift of

@@ -329,6 +329,7 @@ __global__ void coef_finalize(const double* partials, int64_t n, double eta, dou
 
 int op_coeffs(fsi_mesh* m, int i, double* gb) {
   static_assert(CoefOp::MINB == 1, "the partial sums are sized for the mesh's own tile grid");
+  if (m->tet) return tet_coeffs(m, i, gb);
   CoefOp op;
   memset(&op, 0, sizeof(op));
   const int64_t nn = m->nn;

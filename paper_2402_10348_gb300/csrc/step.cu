@@ -89,7 +89,6 @@ int fsi_gmres(fsi_mesh* m, int32_t block, const fsi_state* st, const double* rhs
 int fsi_step(fsi_mesh* m, fsi_state* st, const fsi_step_opts* o, fsi_step_info* info) {
   if (!m || !st || !o) return set_error(FSI_EINVAL, "fsi_step: null argument");
   if (o->k_max < 1) return set_error(FSI_EINVAL, "fsi_step: k_max must be >= 1");
-  if (m->tet) return set_error(FSI_EINVAL, "fsi_step: tetrahedral meshes carry the momentum/continuity operators only");
   const int64_t nn = m->nn;
   const int64_t nmax = 6 * nn;
   if (m->step_ws_n < nmax) {

@@ -27,7 +27,7 @@ struct TetData {
   double* geo = nullptr;    // [TG][ne]: grad lambda_a (12, a-major), quadrature weight |T|/4, G (6 sym)
   int64_t* nptr = nullptr;  // [nn + 1]
   int32_t* nlist = nullptr; // 4 e + a of every (element, corner) at a node, by element
-  double* E = nullptr;      // [16][ne] element contributions, slot (a * 4 + eq)
+  double* E = nullptr;      // [24][ne] element contributions, slot (a * ncomp + eq)
 };
 
 constexpr int TG = 19;
@@ -158,13 +158,13 @@ struct LocalCoef {
   __device__ __forceinline__ double operator()(int i) const { return k[i]; }
 };
 
-__device__ __forceinline__ void tet_load_geo(const TetArgs& A, int64_t e, int (&nd)[4], double (&dN)[4][3],
-                                             double& w, double (&G)[6]) {
-  for (int a = 0; a < 4; ++a) nd[a] = A.conn[a * A.ne + e];
+__device__ __forceinline__ void tet_load_geo(const int32_t* conn, const double* geo, int64_t ne, int64_t e,
+                                             int (&nd)[4], double (&dN)[4][3], double& w, double (&G)[6]) {
+  for (int a = 0; a < 4; ++a) nd[a] = conn[a * ne + e];
   for (int a = 0; a < 4; ++a)
-    for (int d = 0; d < 3; ++d) dN[a][d] = A.geo[(3 * a + d) * A.ne + e];
-  w = A.geo[12 * A.ne + e];
-  for (int c = 0; c < 6; ++c) G[c] = A.geo[(13 + c) * A.ne + e];
+    for (int d = 0; d < 3; ++d) dN[a][d] = geo[(3 * a + d) * ne + e];
+  w = geo[12 * ne + e];
+  for (int c = 0; c < 6; ++c) G[c] = geo[(13 + c) * ne + e];
 }
 
 // MODE 0 residual, 1 product, 2 diagonal of the product: element contributions into E
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(128) tet_ns_elem(const TetArgs A) {
   if (e >= A.ne) return;
   int nd[4];
   double dN[4][3], w, G[6];
-  tet_load_geo(A, e, nd, dN, w, G);
+  tet_load_geo(A.conn, A.geo, A.ne, e, nd, dN, w, G);
   double c[4][4];  // [corner][equation]
   for (int a = 0; a < 4; ++a)
     for (int q = 0; q < 4; ++q) c[a][q] = 0.0;
@@ -303,6 +303,327 @@ int tet_ns(fsi_mesh* m, int mode, const double* dx, double* y, unsigned flags) {
   return tet_ns_run<2>(m, dx, y, flags);
 }
 
+// ------------------------------------------------ Allen-Cahn, B and gamma/beta on tetrahedra
+// The same weak forms as the hexahedral ACOp, BOp and CoefOp (Eq. PPV_AC, Eq. semiCGT,
+// Sections 2.2.1-2.2.2), with the tetrahedral interpolation, the element's metric G and
+// the 4-point rule; element kernels write their corner contributions, tet_node_sum adds
+// them per node in element order.
+
+struct TetACArgs {
+  const int32_t* conn;
+  const double* geo;
+  int64_t ne, nn;
+  const double* xa;
+  const double* xd;
+  const double* dx;
+  double* E;
+  int phase;
+  double gamma, beta;
+  Phys P;
+};
+
+__device__ __forceinline__ double tet_vGv(const double (&v)[3], const double (&G)[6], double* GG) {
+  const double Gm[3][3] = {{G[0], G[3], G[5]}, {G[3], G[1], G[4]}, {G[5], G[4], G[2]}};
+  double s = 0.0, g2 = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      s += v[i] * Gm[i][j] * v[j];
+      g2 += Gm[i][j] * Gm[i][j];
+    }
+  if (GG) *GG = g2;
+  return s;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128) tet_ac_elem(const TetACArgs A) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= A.ne) return;
+  int nd[4];
+  double dN[4][3], w, G[6];
+  tet_load_geo(A.conn, A.geo, A.ne, e, nd, dN, w, G);
+  const Phys& P = A.P;
+  const int64_t nn = A.nn;
+  double uv[3][4], uphi[4], ud[4], gphi[3], gd[3];
+  for (int k = 0; k < 3; ++k) tet_gather(A.xa + k * nn, nd, uv[k]);
+  tet_gather(A.xa + (4 + A.phase) * nn, nd, uphi);
+  tet_grad(uphi, dN, gphi);
+  if (MODE == 0) tet_gather(A.xd + (4 + A.phase) * nn, nd, ud);
+  if (MODE == 1) {
+    tet_gather(A.dx, nd, ud);
+    tet_grad(ud, dN, gd);
+  }
+  const double gam = A.gamma, bet = A.beta, alpha = P.alpha, cm = P.c_mass;
+  const double k_hat = gam * P.eps * P.eps;
+  double c[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int q = 0; q < 4; ++q) {
+    double Nq[4];
+    for (int a = 0; a < 4; ++a) Nq[a] = a == q ? FSI_TA : FSI_TB;
+    double v[3];
+    for (int k = 0; k < 3; ++k) v[k] = tet_val(uv[k], q);
+    const double phi = tet_val(uphi, q);
+    double GG;
+    const double vGv = tet_vGv(v, G, &GG);
+    const double s_hat = gam * (3.0 * phi * phi - 1.0);
+    const double tau = 1.0 / sqrt(4.0 / (P.dt * P.dt) + vGv + 9.0 * k_hat * k_hat * GG + s_hat * s_hat);
+    if (MODE == 0) {
+      const double R = tet_val(ud, q) + v[0] * gphi[0] + v[1] * gphi[1] + v[2] * gphi[2] +
+                       gam * (phi * phi * phi - phi - bet * 0.5 * fabs(phi * phi - 1.0));
+      for (int a = 0; a < 4; ++a) {
+        const double vgN = v[0] * dN[a][0] + v[1] * dN[a][1] + v[2] * dN[a][2];
+        c[a] += w * (Nq[a] * R + k_hat * (dN[a][0] * gphi[0] + dN[a][1] * gphi[1] + dN[a][2] * gphi[2]) +
+                     tau * vgN * R);
+      }
+    } else {
+      const double p2 = phi * phi - 1.0;
+      const double dsF = p2 > 0.0 ? phi : (p2 < 0.0 ? -phi : 0.0);
+      const double rp = gam * (3.0 * phi * phi - 1.0 - bet * dsF);
+      for (int a = 0; a < 4; ++a) {
+        const double vgN = v[0] * dN[a][0] + v[1] * dN[a][1] + v[2] * dN[a][2];
+        if (MODE == 1) {
+          const double d = tet_val(ud, q);
+          const double dR = cm * d + alpha * (v[0] * gd[0] + v[1] * gd[1] + v[2] * gd[2]) + alpha * rp * d;
+          c[a] += w * (Nq[a] * dR + k_hat * alpha * (dN[a][0] * gd[0] + dN[a][1] * gd[1] + dN[a][2] * gd[2]) +
+                       tau * vgN * dR);
+        } else {  // diagonal: trial = test = corner a
+          const double dR = cm * Nq[a] + alpha * vgN + alpha * rp * Nq[a];
+          c[a] += w * (Nq[a] * dR + k_hat * alpha * (dN[a][0] * dN[a][0] + dN[a][1] * dN[a][1] + dN[a][2] * dN[a][2]) +
+                       tau * vgN * dR);
+        }
+      }
+    }
+  }
+  for (int a = 0; a < 4; ++a) A.E[(int64_t)a * A.ne + e] = c[a];
+}
+
+struct TetBArgs {
+  const int32_t* conn;
+  const double* geo;
+  int64_t ne, nn;
+  const double* xa;
+  const double* xd;
+  const double* mat;
+  const double* dx;
+  double* E;
+  int solid;
+  Phys P;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(128) tet_b_elem(const TetBArgs A) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= A.ne) return;
+  int nd[4];
+  double dN[4][3], w, G[6];
+  tet_load_geo(A.conn, A.geo, A.ne, e, nd, dN, w, G);
+  const Phys& P = A.P;
+  const int64_t nn = A.nn;
+  double uv[3][4], L[3][3], ual[4];
+  for (int k = 0; k < 3; ++k) {
+    tet_gather(A.xa + k * nn, nd, uv[k]);
+    tet_grad(uv[k], dN, L[k]);
+  }
+  tet_gather(A.mat + (2 + A.solid) * nn, nd, ual);
+  const int c0 = 4 + P.N + 6 * A.solid;
+  double ub[6][4], gb[6][3], udot[6][4];
+  for (int cc = 0; cc < 6; ++cc) {
+    if (MODE == 1) tet_gather(A.dx + cc * nn, nd, ub[cc]);
+    else tet_gather(A.xa + (int64_t)(c0 + cc) * nn, nd, ub[cc]);
+    tet_grad(ub[cc], dN, gb[cc]);
+    if (MODE == 0) tet_gather(A.xd + (int64_t)(c0 + cc) * nn, nd, udot[cc]);
+  }
+  const double alpha = P.alpha, cm = P.c_mass;
+  double c[4][6];
+  for (int a = 0; a < 4; ++a)
+    for (int cc = 0; cc < 6; ++cc) c[a][cc] = 0.0;
+  for (int q = 0; q < 4; ++q) {
+    double Nq[4];
+    for (int a = 0; a < 4; ++a) Nq[a] = a == q ? FSI_TA : FSI_TB;
+    double v[3];
+    for (int k = 0; k < 3; ++k) v[k] = tet_val(uv[k], q);
+    const double al = tet_val(ual, q);
+    const double tau = 1.0 / sqrt(4.0 / (P.dt * P.dt) + tet_vGv(v, G, nullptr));
+    if (MODE == 2) {
+      for (int a = 0; a < 4; ++a) {
+        const double vgN = v[0] * dN[a][0] + v[1] * dN[a][1] + v[2] * dN[a][2];
+        for (int cc = 0; cc < 6; ++cc) {
+          const int k = sym_k(cc), l = sym_l(cc);
+          const double dR = al * (cm * Nq[a] + alpha * vgN - alpha * Nq[a] * (L[k][k] + L[l][l])) +
+                            (1.0 - al) * alpha * Nq[a];
+          c[a][cc] += w * (Nq[a] + tau * vgN) * dR;
+        }
+      }
+      continue;
+    }
+    double B[6], cv[6];
+    for (int cc = 0; cc < 6; ++cc) {
+      const double sc = MODE == 1 ? alpha : 1.0;
+      B[cc] = sc * tet_val(ub[cc], q);
+      cv[cc] = sc * (v[0] * gb[cc][0] + v[1] * gb[cc][1] + v[2] * gb[cc][2]);
+      if (MODE == 1) cv[cc] += cm * tet_val(ub[cc], q);
+      else cv[cc] += tet_val(udot[cc], q);
+    }
+    for (int cc = 0; cc < 6; ++cc) {
+      const int k = sym_k(cc), l = sym_l(cc);
+      double st = 0.0;
+      for (int m = 0; m < 3; ++m) st += L[k][m] * B[sym_idx(m, l)] + B[sym_idx(k, m)] * L[l][m];
+      const double rec = B[cc] - ((MODE == 0 && cc < 3) ? 1.0 : 0.0);
+      const double R = al * (cv[cc] - st) + (1.0 - al) * rec;
+      for (int a = 0; a < 4; ++a) {
+        const double vgN = v[0] * dN[a][0] + v[1] * dN[a][1] + v[2] * dN[a][2];
+        c[a][cc] += w * (Nq[a] + tau * vgN) * R;
+      }
+    }
+  }
+  for (int a = 0; a < 4; ++a)
+    for (int cc = 0; cc < 6; ++cc) A.E[(int64_t)(a * 6 + cc) * A.ne + e] = c[a][cc];
+}
+
+// node sums of NCOMP components (no Dirichlet rows: the Allen-Cahn and B blocks have none)
+template <int NCOMP>
+__global__ void __launch_bounds__(256) tet_node_sum(const int64_t* __restrict__ nptr, const int32_t* __restrict__ nlist,
+                                                    const double* __restrict__ E, int64_t ne, int64_t nn, double* y) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  double s[NCOMP];
+  for (int k = 0; k < NCOMP; ++k) s[k] = 0.0;
+  for (int64_t i = nptr[n]; i < nptr[n + 1]; ++i) {
+    const int32_t t = nlist[i];
+    const int64_t e = t >> 2;
+    const int a = t & 3;
+    for (int k = 0; k < NCOMP; ++k) s[k] += E[(int64_t)(a * NCOMP + k) * ne + e];
+  }
+  for (int k = 0; k < NCOMP; ++k) y[(int64_t)k * nn + n] = s[k];
+}
+
+int tet_ac(fsi_mesh* m, int mode, int phase, const double* dx, double* y, unsigned flags) {
+  if (flags & FSI_FP32) return set_error(FSI_EINVAL, "tetrahedral meshes: float64 operators only");
+  TetData* t = m->tet;
+  TetACArgs A{t->conn, t->geo, t->ne, m->nn, m->staged_xa, m->xd, dx, t->E, phase, m->gamma[phase], m->beta[phase], m->P};
+  const int cls = mode == 0 ? P_AC_RES : (mode == 1 ? P_AC_JVP64 : P_AC_DIAG);
+  const unsigned ge = (unsigned)((t->ne + 127) / 128);
+  if (mode == 0) FSI_LAUNCH(m, cls, tet_ac_elem<0><<<ge, 128, 0, m->stream>>>(A));
+  else if (mode == 1) FSI_LAUNCH(m, cls, tet_ac_elem<1><<<ge, 128, 0, m->stream>>>(A));
+  else FSI_LAUNCH(m, cls, tet_ac_elem<2><<<ge, 128, 0, m->stream>>>(A));
+  FSI_LAUNCH(m, cls, tet_node_sum<1><<<(unsigned)((m->nn + 255) / 256), 256, 0, m->stream>>>(t->nptr, t->nlist, t->E,
+                                                                                           t->ne, m->nn, y));
+  return FSI_OK;
+}
+
+int tet_b(fsi_mesh* m, int mode, int solid, const double* dx, double* y, unsigned flags) {
+  if (flags & FSI_FP32) return set_error(FSI_EINVAL, "tetrahedral meshes: float64 operators only");
+  TetData* t = m->tet;
+  TetBArgs A{t->conn, t->geo, t->ne, m->nn, m->staged_xa, m->xd, m->mat, dx, t->E, solid, m->P};
+  const int cls = mode == 0 ? P_B_RES : (mode == 1 ? P_B_JVP64 : P_B_DIAG);
+  const unsigned ge = (unsigned)((t->ne + 127) / 128);
+  if (mode == 0) FSI_LAUNCH(m, cls, tet_b_elem<0><<<ge, 128, 0, m->stream>>>(A));
+  else if (mode == 1) FSI_LAUNCH(m, cls, tet_b_elem<1><<<ge, 128, 0, m->stream>>>(A));
+  else FSI_LAUNCH(m, cls, tet_b_elem<2><<<ge, 128, 0, m->stream>>>(A));
+  FSI_LAUNCH(m, cls, tet_node_sum<6><<<(unsigned)((m->nn + 255) / 256), 256, 0, m->stream>>>(t->nptr, t->nlist, t->E,
+                                                                                           t->ne, m->nn, y));
+  return FSI_OK;
+}
+
+// gamma and beta of one phase (Section 2.2.2 mobility by lumped L2 projection, Section
+// 2.2.1 multiplier): element slots 0-3 int N_a q, 4-7 int N_a, 8 int F', 9 int sqrt F
+__global__ void __launch_bounds__(128) tet_coef_elem(const TetArgs A, int phase) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= A.ne) return;
+  int nd[4];
+  double dN[4][3], w, G[6];
+  tet_load_geo(A.conn, A.geo, A.ne, e, nd, dN, w, G);
+  double L[3][3], u[4], uphi[4], g[3];
+  for (int k = 0; k < 3; ++k) {
+    tet_gather(A.xa + k * A.nn, nd, u);
+    tet_grad(u, dN, L[k]);
+  }
+  tet_gather(A.xa + (4 + phase) * A.nn, nd, uphi);
+  tet_grad(uphi, dN, g);
+  const double n2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+  double num = 0.0;
+  for (int j = 0; j < 3; ++j)
+    for (int k = 0; k < 3; ++k) num += g[j] * L[j][k] * g[k];
+  const double qv = n2 < 1e-30 ? 0.0 : num / n2;  // constant on the element
+  double sq[4] = {0.0, 0.0, 0.0, 0.0}, s1[4] = {0.0, 0.0, 0.0, 0.0}, sFp = 0.0, ssF = 0.0;
+  for (int q = 0; q < 4; ++q) {
+    const double phi = tet_val(uphi, q);
+    for (int a = 0; a < 4; ++a) {
+      const double N = a == q ? FSI_TA : FSI_TB;
+      sq[a] += w * N * qv;
+      s1[a] += w * N;
+    }
+    sFp += w * (phi * phi * phi - phi);
+    ssF += w * 0.5 * fabs(phi * phi - 1.0);
+  }
+  for (int a = 0; a < 4; ++a) {
+    A.E[(int64_t)a * A.ne + e] = sq[a];
+    A.E[(int64_t)(4 + a) * A.ne + e] = s1[a];
+  }
+  A.E[(int64_t)8 * A.ne + e] = sFp;
+  A.E[(int64_t)9 * A.ne + e] = ssF;
+}
+
+// per-CTA partial sums {sum val^2 over band nodes, band nodes, int F', int sqrt F} in a
+// fixed partition and order
+__global__ void __launch_bounds__(256) tet_coef_reduce(const int64_t* __restrict__ nptr, const int32_t* __restrict__ nlist,
+                                                       const double* __restrict__ E, int64_t ne, int64_t nn,
+                                                       const double* phi, double* partials) {
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < nn; n += stride) {
+    if (fabs(phi[n]) > 0.9) continue;
+    double num = 0.0, den = 0.0;
+    for (int64_t i = nptr[n]; i < nptr[n + 1]; ++i) {
+      const int64_t e = nlist[i] >> 2;
+      const int c = nlist[i] & 3;
+      num += E[(int64_t)c * ne + e];
+      den += E[(int64_t)(4 + c) * ne + e];
+    }
+    const double val = fabs(num / den);
+    a[0] += val * val;
+    a[1] += 1.0;
+  }
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += stride) {
+    a[2] += E[(int64_t)8 * ne + e];
+    a[3] += E[(int64_t)9 * ne + e];
+  }
+  __shared__ double sm[4][256];
+  for (int k = 0; k < 4; ++k) sm[k][threadIdx.x] = a[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = 0; i < 256; ++i)
+      for (int k = 0; k < 4; ++k) t[k] += sm[k][i];
+    for (int k = 0; k < 4; ++k) partials[4 * blockIdx.x + k] = t[k];
+  }
+}
+
+int tet_coeffs(fsi_mesh* m, int phase, double* gb) {
+  TetData* t = m->tet;
+  constexpr int NB = 152;
+  if (m->n_partials < NB) {
+    cudaFree(m->partials);
+    m->partials = nullptr;
+    FSI_CUDA(cudaMalloc(&m->partials, sizeof(double) * 4 * NB));
+    m->n_partials = NB;
+  }
+  TetArgs A{};
+  A.conn = t->conn;
+  A.geo = t->geo;
+  A.ne = t->ne;
+  A.xa = m->staged_xa;
+  A.E = t->E;
+  A.nn = m->nn;
+  FSI_LAUNCH(m, P_COEF, tet_coef_elem<<<(unsigned)((t->ne + 127) / 128), 128, 0, m->stream>>>(A, phase));
+  FSI_LAUNCH(m, P_COEF, tet_coef_reduce<<<NB, 256, 0, m->stream>>>(t->nptr, t->nlist, t->E, t->ne, m->nn,
+                                                                   m->staged_xa + (4 + phase) * m->nn, m->partials));
+  FSI_LAUNCH(m, P_COEF, coef_finalize<<<1, NTHREADS, 0, m->stream>>>(m->partials, NB, m->P.eta, m->red));
+  FSI_CUDA(cudaMemcpyAsync(m->red_host, m->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  FSI_CUDA(cudaStreamSynchronize(m->stream));
+  gb[0] = m->red_host[0];
+  gb[1] = m->red_host[1];
+  return FSI_OK;
+}
+
 }  // namespace fsi
 
 using namespace fsi;
@@ -387,7 +708,7 @@ extern "C" int fsi_create_tet_mesh(const fsi_mesh_desc* d, const double* coords,
   up((void**)&t->geo, geo.data(), sizeof(double) * geo.size());
   up((void**)&t->nptr, ptr.data(), sizeof(int64_t) * ptr.size());
   up((void**)&t->nlist, list.data(), sizeof(int32_t) * list.size());
-  up((void**)&t->E, nullptr, sizeof(double) * 16 * (size_t)ne);
+  up((void**)&t->E, nullptr, sizeof(double) * 24 * (size_t)ne);
   if (err != cudaSuccess) {
     rc = cuda_check(err, "fsi_create_tet_mesh: device arrays");
     fsi_destroy_mesh(m);
