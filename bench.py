@@ -837,6 +837,17 @@ def run_gpu(args):
                  "s_per_timestep": round(oms / args.steps / 1e3, 5),
                  "step_stats": step_stats(oinfos),
                  ("error_vs_fp64" if f64 else "error_vs_fp32ir"): field_errors(d, xn, final[1])}
+        # one profiled step of this precision: its NS product's roofline
+        restore()
+        fsi.fsi_profile(mesh, True)
+        step(oo)
+        torch.cuda.synchronize()
+        oprof = fsi.fsi_profile_read(mesh)
+        fsi.fsi_profile(mesh, False)
+        oname = "ns_jvp_f32" if f64 else "ns_jvp_f64_em"
+        if oprof.get(oname, (0, 0))[0] > 0:
+            other["roofline_ns_product"] = roofline(oname, *oprof[oname], d, pk, basis_f64=not f64)
+        other["kernel_ms_one_step"] = {k: [v[0], round(v[1], 3)] for k, v in oprof.items() if v[0] > 0}
 
     learned = None
     if pc is not None:

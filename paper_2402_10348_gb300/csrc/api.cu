@@ -39,7 +39,7 @@ int ensure_smem_attr(const void* func, size_t bytes) {
 static const char* kProfNames[P_NCLS] = {
     "stage", "ns_residual", "ns_jvp_f64", "ns_jvp_f32", "ns_diag", "ac_residual", "ac_jvp_f64", "ac_jvp_f32",
     "ac_diag", "b_residual", "b_jvp_f64", "b_jvp_f32", "b_diag", "gamma_beta", "krylov_vector", "init",
-    "krylov_dot", "krylov_update", "krylov_scalar", "to_float", "pc_conv", "pc_wgrad", "pc_aux", "op_builds", "ns_jvp_f64_em", "ns_node_sum"};
+    "krylov_dot", "krylov_update", "krylov_scalar", "to_float", "pc_conv", "pc_wgrad", "pc_aux", "op_builds", "ns_jvp_f64_em", "node_sums"};
 constexpr int PROF_PAIRS = 4096;
 
 int prof_harvest(fsi_mesh* m) {

@@ -19,7 +19,7 @@ namespace fsi {
 enum ProfClass {
   P_STAGE, P_NS_RES, P_NS_JVP64, P_NS_JVP32, P_NS_DIAG, P_AC_RES, P_AC_JVP64, P_AC_JVP32,
   P_AC_DIAG, P_B_RES, P_B_JVP64, P_B_JVP32, P_B_DIAG, P_COEF, P_KRYLOV, P_INIT, P_KRY_DOT, P_KRY_UPD,
-  P_KRY_SMALL, P_KRY_CONV, P_PC_CONV, P_PC_WGRAD, P_PC_AUX, P_NS_BUILD, P_NS_JVP64E, P_NS_NODE, P_NCLS
+  P_KRY_SMALL, P_KRY_CONV, P_PC_CONV, P_PC_WGRAD, P_PC_AUX, P_NS_BUILD, P_NS_JVP64E, P_NODE_SUM, P_NCLS
 };
 struct Profiler {
   bool on = false;
@@ -69,7 +69,7 @@ struct fsi_mesh {
   float* dx32 = nullptr;     // float copy of a product's increment (FSI_FP32)
   const double* staged_x = nullptr;  // x^{n+1} of the last staging (p and Dirichlet rows)
   int64_t stage_gen = 0;             // staging count: coefficients built at another count are stale
-  // quadrature-point coefficients of the NS product (NSBuildOp / NSQOp in ops.cuh)
+  // quadrature-point coefficients of the NS product (NSBuildOp in ops.cuh, nsq_elem_kernel)
   double* cq64 = nullptr;
   float* cq32 = nullptr;
   int64_t cq_len = 0;                // allocated coefficients (each array)
@@ -79,18 +79,18 @@ struct fsi_mesh {
   // a state has taken NSE_AFTER float64 products
   double* ke64 = nullptr;
   int64_t ke_len = 0;
-  double* ke_e = nullptr;            // [32][elements] element products of the matrix form
+  double* ke_e = nullptr;            // [slots][elements] corner contributions of the element-centric products
   int64_t ke_e_len = 0;
   int64_t ke_gen = -1;               // cq_gen they were built from
   int64_t f64_gen = -1, f64_count = 0;  // float64 NS products applied at coefficient build f64_gen
   int64_t cq_builds = 0;             // coefficient builds so far (a new build invalidates ke64)
-  // float64 Allen-Cahn element matrices (ACEOp) of one phase at one staging
+  // float64 Allen-Cahn element matrices (ace_elem_kernel) of one phase at one staging
   double* ake64 = nullptr;
   int64_t ake_len = 0;
   int64_t ake_gen = -1, ake_count = 0;  // staging the products were counted at / built for
   int ake_phase = -1, ake_built = 0;
   double ake_gamma = 0.0, ake_beta = 0.0;
-  // float64 B split operators (BEOp) of one solid at one staging
+  // float64 B split operators (be_elem_kernel) of one solid at one staging
   double* bke64 = nullptr;
   int64_t bke_len = 0;
   int64_t bke_gen = -1, bke_count = 0;
@@ -170,6 +170,8 @@ template <typename T>
 int launch_ns(fsi_mesh* m, int mode, const double* dx, double* y, unsigned flags);
 // NS product from the quadrature-point coefficients (built first when stale)
 int ns_build(fsi_mesh* m, unsigned flags);  // ops_f64.cu
+// [slots][elements] scratch of the element-centric products, grown on demand (ops_f64.cu)
+int ensure_elem_scratch(fsi_mesh* m, int slots, int64_t nxyp);
 // float64 NS product through element matrices (built first when stale), ops_f64.cu
 int launch_nse(fsi_mesh* m, const double* dx, double* y, unsigned flags);
 // float64 Allen-Cahn product of one phase through element matrices (ops_f64.cu)
@@ -177,6 +179,11 @@ int launch_ace(fsi_mesh* m, int phase, const double* dx, double* y);
 // float64 B product of one solid through the split operator (ops_f64.cu)
 int launch_be(fsi_mesh* m, int solid, const double* dx, double* y);
 constexpr int NSE_AFTER = 8;  // float64 products on one coefficient build before the matrices pay
+// Allen-Cahn element matrices: a build costs about three re-interpolating products and
+// each matrix product a fifteenth of one; the B split operator's build costs less than one
+// re-interpolating product, so it is built at the first product of a solve
+constexpr int ACE_AFTER = 2;
+constexpr int BE_AFTER = 0;
 template <typename T>
 int launch_nsq(fsi_mesh* m, const double* dx, double* y, unsigned flags);
 template <typename T>

@@ -335,8 +335,8 @@ struct NSOp {
 // ----------------------------------------------- NS product from frozen coefficients
 // Within one NS block solve every coefficient of the product is fixed: the state the
 // Jacobian is taken at does not move.  NSBuildOp evaluates them once per solve, in
-// float64, at every quadrature point of every element; NSQOp then applies the
-// product by interpolating only the increment (dv, dp).  Per quadrature point:
+// float64, at every quadrature point of every element; the product (nsq_elem_kernel)
+// then interpolates only the increment (dv, dp).  Per quadrature point:
 //   0 rho, 1 mu, 2-4 v, 5-13 L_kj = d_j v_k (k-major), 14-16 R_m,
 //   17 tau_m, 18 tau_c rho, 19 tau_m / rho,
 //   20-25 aB = sum_s a_s B^s, 26-43 aG[c][m] = sum_s a_s d_m B^s_c (c in [11,22,33,12,23,13]),
@@ -543,67 +543,6 @@ struct CoefRef {
   __device__ __forceinline__ T operator()(int i) const { return __ldg(p + i * s); }
 };
 
-// NS product from the coefficients: fields dv(3), dp of the increment.  The element
-// contributions are accumulated without the quadrature weight W, applied per node.
-template <typename TT>
-struct NSQOp {
-  using T = TT;
-  static constexpr int NC = 4;
-  static constexpr int MINB = sizeof(TT) == 4 ? 2 : 1;  // float32: two CTAs per SM (latency)
-  Fields F;
-  int nf;
-  const T* cq;   // coefficients of the compute type
-  int nxp;
-  int64_t nxyp;
-  int elastic;   // 0: aB, aG are zero (no solids or no augmentation) and are not read
-  double alpha, cm;
-  double rh[3], W;
-  OutDesc out;
-  int64_t nn_;
-
-  __device__ __forceinline__ const T* fptr(int f) const { return field_ptr<T>(F, f); }
-  using Red = NoRed;
-  __device__ __forceinline__ void begin_cta(Red&) const {}
-  __device__ __forceinline__ void end_cta(Red&) const {}
-
-  __device__ void element(const Corners<T>& cr, const ElemCtx& ec, T (&c)[NC][8], Red&) const {
-    const T rhx = T(rh[0]), rhy = T(rh[1]), rhz = T(rh[2]);
-    const T al = T(alpha), cmass = T(cm);
-    const T* e0 = cq + (int64_t)ec.ez * 8 * NCQ * nxyp + (int64_t)ec.ey * nxp + ec.ex;
-    T u[8];
-#pragma unroll 1
-    for (int q = 0; q < 8; ++q) {
-      QW<T> w;
-      w.set(q);
-      T dv[3], gd[3][3];
-#pragma unroll
-      for (int kk = 0; kk < 3; ++kk) {
-        cr.get(kk, u);
-        const VG<T> r = interp_vg(u, w, rhx, rhy, rhz);
-        dv[kk] = r.v; gd[kk][0] = r.gx; gd[kk][1] = r.gy; gd[kk][2] = r.gz;
-      }
-      cr.get(3, u);
-      const VG<T> dpr = interp_vg(u, w, rhx, rhy, rhz);
-      const T dgp[3] = {dpr.gx, dpr.gy, dpr.gz};
-      nsq_point<T>(CoefRef<T>{e0 + (int64_t)q * NCQ * nxyp, nxyp}, elastic != 0, dv, gd, dpr.v, dgp, al, cmass, w,
-                   rhx, rhy, rhz, c);
-    }
-  }
-
-  __device__ __forceinline__ void finish(const NodeCtx& nc, const T (&acc)[NC], Red&) const {
-    const int64_t nn = nn_;
-    const uint8_t m = out.mask ? out.mask[nc.n] : 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      double* y = out.y + (int64_t)k * nn + nc.n;
-      if (((m >> k) & 1) && (k < 3 || out.pin)) {
-        *y = out.dx ? out.dx[(int64_t)k * nn + nc.n] : (double)out.dx32[(int64_t)k * nn + nc.n];
-      } else {
-        *y = W * (double)acc[k];
-      }
-    }
-  }
-};
 
 // ------------------------------------------- float64 NS product from element matrices
 // GB300 issues float64 FMAs at 1/64 of the float32 rate, so a float64 solve that
@@ -704,7 +643,7 @@ struct ACOp {
 //   K[b][a] = sum_q W ( N_b dR_a + khat alpha grad N_b . grad N_a + tau (v . grad N_b) dR_a ),
 //   dR_a = c_m N_a + alpha v . grad N_a + alpha gamma (3 phi^2 - 1 - beta dsqrtF) N_a,
 // layout K[((ez * 64 + b * 8 + a) * nxyp + ey * nxp + ex], built once the solve has taken
-// NSE_AFTER float64 products (64 FMAs per element and product against about 2000 flops).
+// ACE_AFTER float64 products (64 FMAs per element and product against about 2000 flops).
 // Build fields: v(3), phi.
 struct ACEBuildOp {
   using T = double;
@@ -778,40 +717,6 @@ struct ACEBuildOp {
   __device__ __forceinline__ void finish(const NodeCtx&, const T (&)[NC], Red&) const {}
 };
 
-// Product: field dphi.
-struct ACEOp {
-  using T = double;
-  static constexpr int NC = 1;
-  static constexpr int MINB = 1;
-  Fields F;
-  int nf;
-  const double* K;
-  int nxp;
-  int64_t nxyp;
-  OutDesc out;
-  int64_t nn_;
-
-  __device__ __forceinline__ const T* fptr(int f) const { return field_ptr<T>(F, f); }
-  using Red = NoRed;
-  __device__ __forceinline__ void begin_cta(Red&) const {}
-  __device__ __forceinline__ void end_cta(Red&) const {}
-
-  __device__ void element(const Corners<T>& cr, const ElemCtx& ec, T (&c)[NC][8], Red&) const {
-    T x[8];
-    cr.get(0, x);
-    const double* k = K + (int64_t)ec.ez * 64 * nxyp + (int64_t)ec.ey * nxp + ec.ex;
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      T acc = 0.0;
-#pragma unroll
-      for (int a = 0; a < 8; ++a) acc += __ldg(k + (int64_t)(b * 8 + a) * nxyp) * x[a];
-      c[0][b] = acc;
-    }
-  }
-  __device__ __forceinline__ void finish(const NodeCtx& nc, const T (&acc)[NC], Red&) const {
-    out.y[nc.n] = acc[0];
-  }
-};
 
 // ----------------------------------------------------------------- B block
 // fields: [dB(6) (JVP)], v(3), alpha^s, B(6), dB/dt(6)
@@ -998,77 +903,6 @@ struct BEBuildOp {
   __device__ __forceinline__ void finish(const NodeCtx&, const T (&)[NC], Red&) const {}
 };
 
-// Product: fields dB(6) of one solid.
-struct BEOp {
-  using T = double;
-  static constexpr int NC = 6;
-  static constexpr int MINB = 1;
-  Fields F;
-  int nf;
-  const double* K;
-  int nxp;
-  int64_t nxyp;
-  OutDesc out;
-  int64_t nn_;
-
-  __device__ __forceinline__ const T* fptr(int f) const { return field_ptr<T>(F, f); }
-  using Red = NoRed;
-  __device__ __forceinline__ void begin_cta(Red&) const {}
-  __device__ __forceinline__ void end_cta(Red&) const {}
-
-  __device__ void element(const Corners<T>& cr, const ElemCtx& ec, T (&c)[NC][8], Red&) const {
-    double x[6][8];
-#pragma unroll
-    for (int cc = 0; cc < 6; ++cc) cr.get(cc, x[cc]);
-    const double* k = K + (int64_t)ec.ez * NBK * nxyp + (int64_t)ec.ey * nxp + ec.ex;
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      double s[8];
-#pragma unroll
-      for (int b = 0; b < 8; ++b) s[b] = __ldg(k + (int64_t)(a * 8 + b) * nxyp);
-#pragma unroll
-      for (int cc = 0; cc < 6; ++cc) {
-        double acc = 0.0;
-#pragma unroll
-        for (int b = 0; b < 8; ++b) acc += s[b] * x[cc][b];
-        c[cc][a] = acc;
-      }
-    }
-#pragma unroll 1
-    for (int q = 0; q < 8; ++q) {
-      QW<double> w;
-      w.set(q);
-      const double* kq = k + (int64_t)(64 + 17 * q) * nxyp;
-      double dB[6];
-#pragma unroll
-      for (int cc = 0; cc < 6; ++cc) dB[cc] = interp_v(x[cc], w);
-      double L[3][3];
-#pragma unroll
-      for (int kk = 0; kk < 3; ++kk)
-#pragma unroll
-        for (int m = 0; m < 3; ++m) L[kk][m] = __ldg(kq + (int64_t)(8 + 3 * kk + m) * nxyp);
-      double st[6];
-#pragma unroll
-      for (int cc = 0; cc < 6; ++cc) {
-        const int kk = sym_k(cc), l = sym_l(cc);
-        double t = 0.0;
-#pragma unroll
-        for (int m = 0; m < 3; ++m) t += L[kk][m] * dB[sym_idx(m, l)] + dB[sym_idx(kk, m)] * L[l][m];
-        st[cc] = t;
-      }
-#pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        const double ta = __ldg(kq + (int64_t)a * nxyp);
-#pragma unroll
-        for (int cc = 0; cc < 6; ++cc) c[cc][a] -= ta * st[cc];
-      }
-    }
-  }
-  __device__ __forceinline__ void finish(const NodeCtx& nc, const T (&acc)[NC], Red&) const {
-#pragma unroll
-    for (int cc = 0; cc < 6; ++cc) out.y[(int64_t)cc * nn_ + nc.n] = acc[cc];
-  }
-};
 
 // ----------------------------------------------------------------- gamma, beta
 // fields: v(3), phi.  Node output: int N_p q and int N_p; band RMS and beta

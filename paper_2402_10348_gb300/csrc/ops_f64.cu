@@ -111,6 +111,137 @@ __global__ void __launch_bounds__(256) nse_build_kernel(const double* __restrict
   for (int i = 0; i < 32; ++i) out[(int64_t)i * 32 * nxyp] = c[i >> 3][i & 7];
 }
 
+// Element-centric products of the Allen-Cahn element matrices and the B split operator:
+// one thread per element (x fastest) gathers its increment values, applies the stored
+// operator and writes its 8 (AC) or 48 (B) corner contributions into E[slot][element];
+// em_node_kernel then sums, per node, the slots of its up to 8 elements in a fixed order
+// (z, y, x).  Each element is evaluated once (no halo recomputation); deterministic.
+// Allen-Cahn: c[b] = sum_a K[b][a] x[a]
+__global__ void __launch_bounds__(128) ace_elem_kernel(const double* __restrict__ K, const double* __restrict__ dx,
+                                                       double* __restrict__ E, int nx, int ny, int nz, int nxp,
+                                                       int64_t nxyp) {
+  ElemIdx I;
+  if (!I.set(nx, ny, nz, nxp, nxyp)) return;
+  double x[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) x[a] = __ldg(dx + I.n0 + I.off[a]);
+  const double* k = K + (int64_t)I.ez * 64 * nxyp + (int64_t)I.ey * nxp + I.ex;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    double acc = 0.0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) acc += __ldg(k + (int64_t)(b * 8 + a) * nxyp) * x[a];
+    E[b * I.es + I.e] = acc;
+  }
+}
+
+// B split operator of one solid: c[cc][a] = sum_b S[a][b] dB_cc[b]
+//   - sum_q Ta_q[a] (L_q dB_q + dB_q L_q^T)_cc   (the stretching coupling at point q)
+__global__ void __launch_bounds__(128) be_elem_kernel(const double* __restrict__ K, const double* __restrict__ dx,
+                                                      double* __restrict__ E, int nx, int ny, int nz, int nxp,
+                                                      int64_t nxyp, int64_t nn) {
+  ElemIdx I;
+  if (!I.set(nx, ny, nz, nxp, nxyp)) return;
+  double x[6][8];
+#pragma unroll
+  for (int cc = 0; cc < 6; ++cc)
+#pragma unroll
+    for (int a = 0; a < 8; ++a) x[cc][a] = __ldg(dx + cc * nn + I.n0 + I.off[a]);
+  const double* k = K + (int64_t)I.ez * NBK * nxyp + (int64_t)I.ey * nxp + I.ex;
+  double c[6][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    double s[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) s[b] = __ldg(k + (int64_t)(a * 8 + b) * nxyp);
+#pragma unroll
+    for (int cc = 0; cc < 6; ++cc) {
+      double acc = 0.0;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc += s[b] * x[cc][b];
+      c[cc][a] = acc;
+    }
+  }
+#pragma unroll 1
+  for (int q = 0; q < 8; ++q) {
+    QW<double> w;
+    w.set(q);
+    const double* kq = k + (int64_t)(64 + 17 * q) * nxyp;
+    double dB[6];
+#pragma unroll
+    for (int cc = 0; cc < 6; ++cc) dB[cc] = interp_v(x[cc], w);
+    double L[3][3];
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk)
+#pragma unroll
+      for (int mm = 0; mm < 3; ++mm) L[kk][mm] = __ldg(kq + (int64_t)(8 + 3 * kk + mm) * nxyp);
+    double st[6];
+#pragma unroll
+    for (int cc = 0; cc < 6; ++cc) {
+      const int kk = sym_k(cc), l = sym_l(cc);
+      double t = 0.0;
+#pragma unroll
+      for (int mm = 0; mm < 3; ++mm) t += L[kk][mm] * dB[sym_idx(mm, l)] + dB[sym_idx(kk, mm)] * L[l][mm];
+      st[cc] = t;
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const double ta = __ldg(kq + (int64_t)a * nxyp);
+#pragma unroll
+      for (int cc = 0; cc < 6; ++cc) c[cc][a] -= ta * st[cc];
+    }
+  }
+#pragma unroll
+  for (int cc = 0; cc < 6; ++cc)
+#pragma unroll
+    for (int a = 0; a < 8; ++a) E[(8 * cc + a) * I.es + I.e] = c[cc][a];
+}
+
+template <int NC>
+__global__ void __launch_bounds__(128) em_node_kernel(const double* __restrict__ E, int nx, int ny, int nz, int nxp,
+                                                      int64_t nxyp, int64_t nn, double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int jk = blockIdx.y;
+  const int j = jk % (ny + 1), k = jk / (ny + 1);
+  if (i > nx || k > nz) return;
+  const int64_t n = i + (int64_t)(nx + 1) * (j + (int64_t)(ny + 1) * k);
+  const int64_t es = (int64_t)nz * nxyp;
+  double s[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) s[c] = 0.0;
+  for (int az = 1; az >= 0; --az) {
+    const int ez = k - az;
+    if (ez < 0 || ez >= nz) continue;
+    for (int ay = 1; ay >= 0; --ay) {
+      const int ey = j - ay;
+      if (ey < 0 || ey >= ny) continue;
+      for (int ax = 1; ax >= 0; --ax) {
+        const int ex = i - ax;
+        if (ex < 0 || ex >= nx) continue;
+        const int64_t e = (int64_t)ez * nxyp + (int64_t)ey * nxp + ex;
+        const int a = ax + 2 * ay + 4 * az;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) s[c] += E[(8 * c + a) * es + e];
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) y[c * nn + n] = s[c];
+}
+
+// E[slots][nz * nxyp] scratch of the element-centric products (NS, AC and B in turn)
+int ensure_elem_scratch(fsi_mesh* m, int slots, int64_t nxyp) {
+  const int64_t elen = (int64_t)slots * m->g.nz * nxyp;
+  if (m->ke_e_len < elen) {
+    cudaFree(m->ke_e);
+    m->ke_e = nullptr;
+    m->ke_e_len = 0;
+    FSI_CUDA(cudaMalloc(&m->ke_e, sizeof(double) * (size_t)elen));
+    m->ke_e_len = elen;
+  }
+  return FSI_OK;
+}
+
 int launch_ace(fsi_mesh* m, int phase, const double* dx, double* y) {
   const int nxp = cq_pitch(m);
   const int64_t nxyp = (int64_t)nxp * m->g.ny;
@@ -140,25 +271,23 @@ int launch_ace(fsi_mesh* m, int phase, const double* dx, double* y) {
     if (int rc = run_tile(m, b, P_NS_BUILD)) return rc;
     m->ake_built = 1;
   }
-  ACEOp op;
-  memset(&op, 0, sizeof(op));
-  put<double>(op.F, 0, dx);
-  op.nf = 1;
-  op.K = m->ake64;
-  op.nxp = nxp;
-  op.nxyp = nxyp;
-  op.out.y = y;
-  op.nn_ = nn;
-  const int64_t ne = (int64_t)m->g.nx * m->g.ny * m->g.nz;
-  prof_bytes(m, P_AC_JVP64, (double)ne * 64 * 8.0 + (double)nn * 16.0);
-  return run_tile(m, op, P_AC_JVP64);
+  if (int rc = ensure_elem_scratch(m, 8, nxyp)) return rc;
+  const Geom& g = m->g;
+  const int64_t ne = (int64_t)g.nx * g.ny * g.nz;
+  prof_bytes(m, P_AC_JVP64, (double)ne * (64 * 8.0 + 8 * 8.0) + (double)nn * 8.0);
+  prof_bytes(m, P_NODE_SUM, (double)ne * 8 * 8.0 + (double)nn * 8.0);
+  FSI_LAUNCH(m, P_AC_JVP64,
+             ace_elem_kernel<<<elem_grid(g), 128, 0, m->stream>>>(m->ake64, dx, m->ke_e, g.nx, g.ny, g.nz, nxp, nxyp));
+  FSI_LAUNCH(m, P_NODE_SUM,
+             em_node_kernel<1><<<node_grid(g), 128, 0, m->stream>>>(m->ke_e, g.nx, g.ny, g.nz, nxp, nxyp, nn, y));
+  return FSI_OK;
 }
 
 // Product with element matrices, element-centric: one thread per element (x fastest)
 // gathers its 32 increment values, applies its matrix and writes the 32 products into
-// E[i][element] (each element evaluated once: no halo recomputation); one thread per node
-// then sums the slots of its up to 8 elements in a fixed order (z, y, x) and applies the
-// Dirichlet rows (deterministic, no atomics).
+// E[i][element] (each element evaluated once: no halo recomputation); ns_node_kernel then
+// sums, per node, the slots of its up to 8 elements in a fixed order (z, y, x) and applies
+// the Dirichlet rows (deterministic, no atomics).
 __global__ void __launch_bounds__(256) nse_elem_kernel(const double* __restrict__ K, const double* __restrict__ dx,
                                                        double* __restrict__ E, int nx, int ny, int nz, int nxp,
                                                        int64_t nxyp, int64_t nn) {
@@ -184,40 +313,6 @@ __global__ void __launch_bounds__(256) nse_elem_kernel(const double* __restrict_
 #pragma unroll
     for (int j = 0; j < 32; ++j) acc += __ldg(row + j * nxyp) * x[j];
     E[i * es + e] = acc;
-  }
-}
-
-__global__ void __launch_bounds__(256) nse_node_kernel(const double* __restrict__ E, int nx, int ny, int nz, int nxp,
-                                                       int64_t nxyp, int64_t nn, double W, const uint8_t* mask,
-                                                       int pin, const double* __restrict__ dx, double* __restrict__ y) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int jk = blockIdx.y;
-  const int j = jk % (ny + 1), k = jk / (ny + 1);
-  if (i > nx || k > nz) return;
-  const int64_t n = i + (int64_t)(nx + 1) * (j + (int64_t)(ny + 1) * k);
-  const int64_t es = (int64_t)nz * nxyp;
-  double s[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int az = 1; az >= 0; --az) {
-    const int ez = k - az;
-    if (ez < 0 || ez >= nz) continue;
-    for (int ay = 1; ay >= 0; --ay) {
-      const int ey = j - ay;
-      if (ey < 0 || ey >= ny) continue;
-      for (int ax = 1; ax >= 0; --ax) {
-        const int ex = i - ax;
-        if (ex < 0 || ex >= nx) continue;
-        const int64_t e = (int64_t)ez * nxyp + (int64_t)ey * nxp + ex;
-        const int a = ax + 2 * ay + 4 * az;  // this node's corner in element (ex, ey, ez)
-#pragma unroll
-        for (int f = 0; f < 4; ++f) s[f] += E[(8 * f + a) * es + e];
-      }
-    }
-  }
-  const uint8_t mk = mask[n];
-#pragma unroll
-  for (int f = 0; f < 4; ++f) {
-    const bool dir = ((mk >> f) & 1) && (f < 3 || pin);
-    y[f * nn + n] = dir ? dx[f * nn + n] : W * s[f];
   }
 }
 
@@ -248,18 +343,17 @@ int launch_be(fsi_mesh* m, int solid, const double* dx, double* y) {
     if (int rc = run_tile(m, b, P_NS_BUILD)) return rc;
     m->bke_built = 1;
   }
-  BEOp op;
-  memset(&op, 0, sizeof(op));
-  for (int c = 0; c < 6; ++c) put<double>(op.F, c, dx + c * nn);
-  op.nf = 6;
-  op.K = m->bke64;
-  op.nxp = nxp;
-  op.nxyp = nxyp;
-  op.out.y = y;
-  op.nn_ = nn;
-  const int64_t ne = (int64_t)m->g.nx * m->g.ny * m->g.nz;
-  prof_bytes(m, P_B_JVP64, (double)ne * NBK * 8.0 + (double)nn * 96.0);
-  return run_tile(m, op, P_B_JVP64);
+  if (int rc = ensure_elem_scratch(m, 48, nxyp)) return rc;
+  const Geom& g = m->g;
+  const int64_t ne = (int64_t)g.nx * g.ny * g.nz;
+  prof_bytes(m, P_B_JVP64, (double)ne * (NBK * 8.0 + 48 * 8.0) + (double)nn * 48.0);
+  prof_bytes(m, P_NODE_SUM, (double)ne * 48 * 8.0 + (double)nn * 48.0);
+  FSI_LAUNCH(m, P_B_JVP64,
+             be_elem_kernel<<<elem_grid(g), 128, 0, m->stream>>>(m->bke64, dx, m->ke_e, g.nx, g.ny, g.nz, nxp, nxyp,
+                                                                nn));
+  FSI_LAUNCH(m, P_NODE_SUM,
+             em_node_kernel<6><<<node_grid(g), 128, 0, m->stream>>>(m->ke_e, g.nx, g.ny, g.nz, nxp, nxyp, nn, y));
+  return FSI_OK;
 }
 
 int launch_nse(fsi_mesh* m, const double* dx, double* y, unsigned flags) {
@@ -283,28 +377,21 @@ int launch_nse(fsi_mesh* m, const double* dx, double* y, unsigned flags) {
     m->ke_gen = m->cq_builds;
   }
   const int64_t nn = m->nn;
-  const int64_t elen = 32 * (int64_t)m->g.nz * nxyp;
-  if (m->ke_e_len < elen) {
-    cudaFree(m->ke_e);
-    m->ke_e = nullptr;
-    m->ke_e_len = 0;
-    FSI_CUDA(cudaMalloc(&m->ke_e, sizeof(double) * (size_t)elen));
-    m->ke_e_len = elen;
-  }
+  if (int rc = ensure_elem_scratch(m, 32, nxyp)) return rc;
   const Geom& g = m->g;
   const int64_t ne = (int64_t)g.nx * g.ny * g.nz;
   // algorithmic bytes: the element kernel reads the matrices once and the increment once per
   // node and writes the 32 element products; the node kernel reads those back and writes
   // the product and reads the mask once per node
   prof_bytes(m, P_NS_JVP64E, (double)ne * (NKE * 8.0 + 32 * 8.0) + (double)nn * 32.0);
-  prof_bytes(m, P_NS_NODE, (double)ne * 32 * 8.0 + (double)nn * (32.0 + 1.0));
+  prof_bytes(m, P_NODE_SUM, (double)ne * 32 * 8.0 + (double)nn * (32.0 + 1.0));
   FSI_LAUNCH(m, P_NS_JVP64E,
-             nse_elem_kernel<<<dim3((g.nx + 127) / 128, (unsigned)((int64_t)g.ny * g.nz)), 128, 0, m->stream>>>(
+             nse_elem_kernel<<<elem_grid(g), 128, 0, m->stream>>>(
                  m->ke64, dx, m->ke_e, g.nx, g.ny, g.nz, nxp, nxyp, nn));
-  FSI_LAUNCH(m, P_NS_NODE,
-             nse_node_kernel<<<dim3((g.nx + 1 + 127) / 128, (unsigned)((int64_t)(g.ny + 1) * (g.nz + 1))), 128, 0,
-                               m->stream>>>(m->ke_e, g.nx, g.ny, g.nz, nxp, nxyp, nn, g.hx * g.hy * g.hz / 8.0,
-                                            m->mask, m->pin_active, dx, y));
+  FSI_LAUNCH(m, P_NODE_SUM,
+             ns_node_kernel<double><<<node_grid(g), 128, 0, m->stream>>>(m->ke_e, g.nx, g.ny, g.nz, nxp, nxyp, nn,
+                                                                         g.hx * g.hy * g.hz / 8.0, m->mask,
+                                                                         m->pin_active, dx, nullptr, y));
   return FSI_OK;
 }
 template int launch_ac<double>(fsi_mesh*, int, int, const double*, double*);

@@ -197,6 +197,110 @@ int launch_ns(fsi_mesh* m, int mode, const double* dx, double* y, unsigned flags
 // x pitch of the coefficient planes: a multiple of 16 bytes for either compute type
 inline int cq_pitch(const fsi_mesh* m) { return (m->g.nx + 3) & ~3; }
 
+// ------------------------------------------------ element-centric products
+// One thread per element (x fastest, one CTA row per (ey, ez)) gathers its corner values
+// from the nodal vectors and writes its corner contributions into E[slot][element]
+// (slot = 8 * component + corner, element index ez * nxyp + ey * nxp + ex); a node
+// kernel then sums, per node, the slots of its up to 8 elements in a fixed order
+// (z, y, x).  Each element is evaluated once (no halo recomputation); deterministic.
+struct ElemIdx {
+  int ex, ey, ez;
+  int64_t n0, e, es;
+  int64_t off[8];
+  __device__ __forceinline__ bool set(int nx, int ny, int nz, int nxp, int64_t nxyp) {
+    ex = blockIdx.x * blockDim.x + threadIdx.x;
+    const int eyz = blockIdx.y;
+    ey = eyz % ny;
+    ez = eyz / ny;
+    if (ex >= nx || ez >= nz) return false;
+    const int64_t sy = nx + 1, sz = (int64_t)(nx + 1) * (ny + 1);
+    n0 = ex + sy * ey + sz * ez;
+    off[0] = 0; off[1] = 1; off[2] = sy; off[3] = sy + 1;
+    off[4] = sz; off[5] = sz + 1; off[6] = sz + sy; off[7] = sz + sy + 1;
+    e = (int64_t)ez * nxyp + (int64_t)ey * nxp + ex;
+    es = (int64_t)nz * nxyp;
+    return true;
+  }
+};
+
+inline dim3 elem_grid(const Geom& g) { return dim3((g.nx + 127) / 128, (unsigned)((int64_t)g.ny * g.nz)); }
+inline dim3 node_grid(const Geom& g) { return dim3((g.nx + 1 + 127) / 128, (unsigned)((int64_t)(g.ny + 1) * (g.nz + 1))); }
+
+// NS node sums: y = W * sum of the element slots, the Dirichlet rows (velocity; pressure
+// at the pin node when pinned) take the increment itself (dx, or its float32 copy dx32)
+template <typename T>
+__global__ void __launch_bounds__(128) ns_node_kernel(const T* __restrict__ E, int nx, int ny, int nz, int nxp,
+                                                      int64_t nxyp, int64_t nn, double W, const uint8_t* __restrict__ mask,
+                                                      int pin, const double* __restrict__ dx,
+                                                      const float* __restrict__ dx32, double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int jk = blockIdx.y;
+  const int j = jk % (ny + 1), k = jk / (ny + 1);
+  if (i > nx || k > nz) return;
+  const int64_t n = i + (int64_t)(nx + 1) * (j + (int64_t)(ny + 1) * k);
+  const int64_t es = (int64_t)nz * nxyp;
+  T s[4] = {T(0), T(0), T(0), T(0)};
+  for (int az = 1; az >= 0; --az) {
+    const int ez = k - az;
+    if (ez < 0 || ez >= nz) continue;
+    for (int ay = 1; ay >= 0; --ay) {
+      const int ey = j - ay;
+      if (ey < 0 || ey >= ny) continue;
+      for (int ax = 1; ax >= 0; --ax) {
+        const int ex = i - ax;
+        if (ex < 0 || ex >= nx) continue;
+        const int64_t e = (int64_t)ez * nxyp + (int64_t)ey * nxp + ex;
+        const int a = ax + 2 * ay + 4 * az;  // this node's corner in element (ex, ey, ez)
+#pragma unroll
+        for (int f = 0; f < 4; ++f) s[f] += E[(8 * f + a) * es + e];
+      }
+    }
+  }
+  const uint8_t mk = mask[n];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const bool dir = ((mk >> f) & 1) && (f < 3 || pin);
+    y[f * nn + n] = dir ? (dx ? dx[f * nn + n] : (double)dx32[f * nn + n]) : W * (double)s[f];
+  }
+}
+
+// NS product from the quadrature-point coefficients (see nsq_point), element-centric
+template <typename T>
+__global__ void __launch_bounds__(128) nsq_elem_kernel(const T* __restrict__ cq, const T* __restrict__ dx,
+                                                       T* __restrict__ E, int nx, int ny, int nz, int nxp, int64_t nxyp,
+                                                       int64_t nn, int elastic, T al, T cmass, T rhx, T rhy, T rhz) {
+  ElemIdx I;
+  if (!I.set(nx, ny, nz, nxp, nxyp)) return;
+  T x[4][8], c[4][8];
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      x[f][a] = __ldg(dx + f * nn + I.n0 + I.off[a]);
+      c[f][a] = T(0);
+    }
+  const T* e0 = cq + (int64_t)I.ez * 8 * NCQ * nxyp + (int64_t)I.ey * nxp + I.ex;
+#pragma unroll 1
+  for (int q = 0; q < 8; ++q) {
+    QW<T> w;
+    w.set(q);
+    T dv[3], gd[3][3];
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) {
+      const VG<T> r = interp_vg(x[kk], w, rhx, rhy, rhz);
+      dv[kk] = r.v; gd[kk][0] = r.gx; gd[kk][1] = r.gy; gd[kk][2] = r.gz;
+    }
+    const VG<T> dpr = interp_vg(x[3], w, rhx, rhy, rhz);
+    const T dgp[3] = {dpr.gx, dpr.gy, dpr.gz};
+    nsq_point<T>(CoefRef<T>{e0 + (int64_t)q * NCQ * nxyp, nxyp}, elastic != 0, dv, gd, dpr.v, dgp, al, cmass, w, rhx,
+                 rhy, rhz, c);
+  }
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+#pragma unroll
+    for (int a = 0; a < 8; ++a) E[(8 * f + a) * I.es + I.e] = c[f][a];
+}
+
 template <typename T>
 int launch_nsq(fsi_mesh* m, const double* dx, double* y, unsigned flags) {
   const unsigned eflags = flags & FSI_ELASTIC_AUG;
@@ -211,32 +315,38 @@ int launch_nsq(fsi_mesh* m, const double* dx, double* y, unsigned flags) {
     }
     if (++m->f64_count > NSE_AFTER) return launch_nse(m, dx, y, flags);
   }
-  NSQOp<T> op;
-  memset(&op, 0, sizeof(op));
+  const Geom& g = m->g;
   const int64_t nn = m->nn;
-  for (int k = 0; k < 4; ++k) put_dx<T>(op.F, k, m, dx, k * nn);
-  op.nf = 4;
-  if constexpr (sizeof(T) == 8) op.cq = reinterpret_cast<const T*>(m->cq64);
-  else op.cq = reinterpret_cast<const T*>(m->cq32);
-  op.nxp = cq_pitch(m);
-  op.nxyp = (int64_t)op.nxp * m->g.ny;
-  op.elastic = (eflags && m->ns > 0) ? 1 : 0;
-  op.alpha = m->P.alpha;
-  op.cm = m->P.c_mass;
-  fill_common(m, op.rh, &op.W);
-  op.out.y = y;
-  op.out.dx = dx;
-  op.out.dx32 = sizeof(T) == 4 ? m->dx32 : nullptr;
-  op.out.mask = m->mask;
-  op.out.dirichlet = 1;
-  op.out.pin = m->pin_active;
-  op.nn_ = nn;
-  // algorithmic bytes: the coefficient planes once per element, the increment read and
-  // the product written once per node, the Dirichlet mask
-  const int64_t ne = (int64_t)m->g.nx * m->g.ny * m->g.nz;
+  const int nxp = cq_pitch(m);
+  const int64_t nxyp = (int64_t)nxp * g.ny;
+  const int elastic = (eflags && m->ns > 0) ? 1 : 0;
+  if (int rc = ensure_elem_scratch(m, 32, nxyp)) return rc;
+  const T* cq;
+  const T* xin;
+  if constexpr (sizeof(T) == 8) {
+    cq = reinterpret_cast<const T*>(m->cq64);
+    xin = reinterpret_cast<const T*>(dx);
+  } else {
+    cq = reinterpret_cast<const T*>(m->cq32);
+    xin = reinterpret_cast<const T*>(m->dx32);
+  }
+  T* E = reinterpret_cast<T*>(m->ke_e);
+  // algorithmic bytes: the coefficient planes once per element, the increment once per
+  // node, the 32 element contributions written; the node sums read them back and write
+  // the product (the mask once per node)
+  const int64_t ne = (int64_t)g.nx * g.ny * g.nz;
   prof_bytes(m, jvp_class<T>(0),
-             (double)ne * 8.0 * (op.elastic ? NCQ : NCQ_FLUID) * sizeof(T) + (double)nn * (4.0 * sizeof(T) + 32.0 + 1.0));
-  return run_tile(m, op, jvp_class<T>(0));
+             (double)ne * (8.0 * (elastic ? NCQ : NCQ_FLUID) + 32.0) * sizeof(T) + (double)nn * 4.0 * sizeof(T));
+  prof_bytes(m, P_NODE_SUM, (double)ne * 32.0 * sizeof(T) + (double)nn * (32.0 + 1.0));
+  FSI_LAUNCH(m, jvp_class<T>(0),
+             nsq_elem_kernel<T><<<elem_grid(g), 128, 0, m->stream>>>(
+                 cq, xin, E, g.nx, g.ny, g.nz, nxp, nxyp, nn, elastic, T(m->P.alpha), T(m->P.c_mass), T(1.0 / g.hx),
+                 T(1.0 / g.hy), T(1.0 / g.hz)));
+  FSI_LAUNCH(m, P_NODE_SUM,
+             ns_node_kernel<T><<<node_grid(g), 128, 0, m->stream>>>(
+                 E, g.nx, g.ny, g.nz, nxp, nxyp, nn, g.hx * g.hy * g.hz / 8.0, m->mask, m->pin_active,
+                 dx, sizeof(T) == 4 ? m->dx32 : nullptr, y));
+  return FSI_OK;
 }
 
 template <typename T, int MODE>
@@ -264,7 +374,7 @@ int ac_run(fsi_mesh* m, int i, const double* dx, double* y) {
 template <typename T>
 int launch_ac(fsi_mesh* m, int mode, int i, const double* dx, double* y) {
   if constexpr (sizeof(T) == 8) {
-    // a float64 solve of this phase at this staging: after NSE_AFTER products switch to the
+    // a float64 solve of this phase at this staging: after ACE_AFTER products switch to the
     // element matrices (not for recorded batched launches)
     if (mode == 1 && !m->rec) {
       if (m->ake_gen != m->stage_gen || m->ake_phase != i || m->ake_gamma != m->gamma[i] ||
@@ -276,7 +386,7 @@ int launch_ac(fsi_mesh* m, int mode, int i, const double* dx, double* y) {
         m->ake_count = 0;
         m->ake_built = 0;
       }
-      if (++m->ake_count > NSE_AFTER) return launch_ace(m, i, dx, y);
+      if (++m->ake_count > ACE_AFTER) return launch_ace(m, i, dx, y);
     }
   }
   if (mode == 0) return ac_run<T, 0>(m, i, dx, y);
@@ -313,7 +423,7 @@ int b_run(fsi_mesh* m, int s, const double* dx, double* y) {
 template <typename T>
 int launch_b(fsi_mesh* m, int mode, int s, const double* dx, double* y) {
   if constexpr (sizeof(T) == 8) {
-    // a float64 solve of this solid at this staging: after NSE_AFTER products switch to the
+    // a float64 solve of this solid at this staging: after BE_AFTER products switch to the
     // split operator (not for recorded batched launches)
     if (mode == 1 && !m->rec) {
       if (m->bke_gen != m->stage_gen || m->bke_solid != s) {
@@ -322,7 +432,7 @@ int launch_b(fsi_mesh* m, int mode, int s, const double* dx, double* y) {
         m->bke_count = 0;
         m->bke_built = 0;
       }
-      if (++m->bke_count > NSE_AFTER) return launch_be(m, s, dx, y);
+      if (++m->bke_count > BE_AFTER) return launch_be(m, s, dx, y);
     }
   }
   if (mode == 0) return b_run<T, 0>(m, s, dx, y);
