@@ -200,10 +200,10 @@ __global__ void __launch_bounds__(128) be_elem_kernel(const double* __restrict__
 template <int NC>
 __global__ void __launch_bounds__(128) em_node_kernel(const double* __restrict__ E, int nx, int ny, int nz, int nxp,
                                                       int64_t nxyp, int64_t nn, double* __restrict__ y) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int jk = blockIdx.y;
-  const int j = jk % (ny + 1), k = jk / (ny + 1);
-  if (i > nx || k > nz) return;
+  int i;
+  const int64_t jk = row_index(nx + 1, &i);
+  if (i > nx || jk >= (int64_t)(ny + 1) * (nz + 1)) return;
+  const int j = (int)(jk % (ny + 1)), k = (int)(jk / (ny + 1));
   const int64_t n = i + (int64_t)(nx + 1) * (j + (int64_t)(ny + 1) * k);
   const int64_t es = (int64_t)nz * nxyp;
   double s[NC];
@@ -276,10 +276,11 @@ int launch_ace(fsi_mesh* m, int phase, const double* dx, double* y) {
   const int64_t ne = (int64_t)g.nx * g.ny * g.nz;
   prof_bytes(m, P_AC_JVP64, (double)ne * (64 * 8.0 + 8 * 8.0) + (double)nn * 8.0);
   prof_bytes(m, P_NODE_SUM, (double)ne * 8 * 8.0 + (double)nn * 8.0);
+  const RowLaunch el = elem_launch(g), nl = node_launch(g);
   FSI_LAUNCH(m, P_AC_JVP64,
-             ace_elem_kernel<<<elem_grid(g), 128, 0, m->stream>>>(m->ake64, dx, m->ke_e, g.nx, g.ny, g.nz, nxp, nxyp));
+             ace_elem_kernel<<<el.grid, el.block, 0, m->stream>>>(m->ake64, dx, m->ke_e, g.nx, g.ny, g.nz, nxp, nxyp));
   FSI_LAUNCH(m, P_NODE_SUM,
-             em_node_kernel<1><<<node_grid(g), 128, 0, m->stream>>>(m->ke_e, g.nx, g.ny, g.nz, nxp, nxyp, nn, y));
+             em_node_kernel<1><<<nl.grid, nl.block, 0, m->stream>>>(m->ke_e, g.nx, g.ny, g.nz, nxp, nxyp, nn, y));
   return FSI_OK;
 }
 
@@ -288,13 +289,13 @@ int launch_ace(fsi_mesh* m, int phase, const double* dx, double* y) {
 // E[i][element] (each element evaluated once: no halo recomputation); ns_node_kernel then
 // sums, per node, the slots of its up to 8 elements in a fixed order (z, y, x) and applies
 // the Dirichlet rows (deterministic, no atomics).
-__global__ void __launch_bounds__(256) nse_elem_kernel(const double* __restrict__ K, const double* __restrict__ dx,
+__global__ void __launch_bounds__(128) nse_elem_kernel(const double* __restrict__ K, const double* __restrict__ dx,
                                                        double* __restrict__ E, int nx, int ny, int nz, int nxp,
                                                        int64_t nxyp, int64_t nn) {
-  const int ex = blockIdx.x * blockDim.x + threadIdx.x;
-  const int eyz = blockIdx.y;
-  const int ey = eyz % ny, ez = eyz / ny;
-  if (ex >= nx || ez >= nz) return;
+  int ex;
+  const int64_t eyz = row_index(nx, &ex);
+  if (ex >= nx || eyz >= (int64_t)ny * nz) return;
+  const int ey = (int)(eyz % ny), ez = (int)(eyz / ny);
   const int64_t sx = 1, sy = nx + 1, sz = (int64_t)(nx + 1) * (ny + 1);
   const int64_t n0 = ex + sy * ey + sz * ez;
   const int64_t off[8] = {0, sx, sy, sx + sy, sz, sz + sx, sz + sy, sz + sx + sy};
@@ -348,11 +349,12 @@ int launch_be(fsi_mesh* m, int solid, const double* dx, double* y) {
   const int64_t ne = (int64_t)g.nx * g.ny * g.nz;
   prof_bytes(m, P_B_JVP64, (double)ne * (NBK * 8.0 + 48 * 8.0) + (double)nn * 48.0);
   prof_bytes(m, P_NODE_SUM, (double)ne * 48 * 8.0 + (double)nn * 48.0);
+  const RowLaunch el = elem_launch(g), nl = node_launch(g);
   FSI_LAUNCH(m, P_B_JVP64,
-             be_elem_kernel<<<elem_grid(g), 128, 0, m->stream>>>(m->bke64, dx, m->ke_e, g.nx, g.ny, g.nz, nxp, nxyp,
+             be_elem_kernel<<<el.grid, el.block, 0, m->stream>>>(m->bke64, dx, m->ke_e, g.nx, g.ny, g.nz, nxp, nxyp,
                                                                 nn));
   FSI_LAUNCH(m, P_NODE_SUM,
-             em_node_kernel<6><<<node_grid(g), 128, 0, m->stream>>>(m->ke_e, g.nx, g.ny, g.nz, nxp, nxyp, nn, y));
+             em_node_kernel<6><<<nl.grid, nl.block, 0, m->stream>>>(m->ke_e, g.nx, g.ny, g.nz, nxp, nxyp, nn, y));
   return FSI_OK;
 }
 
@@ -385,11 +387,12 @@ int launch_nse(fsi_mesh* m, const double* dx, double* y, unsigned flags) {
   // the product and reads the mask once per node
   prof_bytes(m, P_NS_JVP64E, (double)ne * (NKE * 8.0 + 32 * 8.0) + (double)nn * 32.0);
   prof_bytes(m, P_NODE_SUM, (double)ne * 32 * 8.0 + (double)nn * (32.0 + 1.0));
+  const RowLaunch el = elem_launch(g), nl = node_launch(g);
   FSI_LAUNCH(m, P_NS_JVP64E,
-             nse_elem_kernel<<<elem_grid(g), 128, 0, m->stream>>>(
+             nse_elem_kernel<<<el.grid, el.block, 0, m->stream>>>(
                  m->ke64, dx, m->ke_e, g.nx, g.ny, g.nz, nxp, nxyp, nn));
   FSI_LAUNCH(m, P_NODE_SUM,
-             ns_node_kernel<double><<<node_grid(g), 128, 0, m->stream>>>(m->ke_e, g.nx, g.ny, g.nz, nxp, nxyp, nn,
+             ns_node_kernel<double><<<nl.grid, nl.block, 0, m->stream>>>(m->ke_e, g.nx, g.ny, g.nz, nxp, nxyp, nn,
                                                                          g.hx * g.hy * g.hz / 8.0, m->mask,
                                                                          m->pin_active, dx, nullptr, y));
   return FSI_OK;

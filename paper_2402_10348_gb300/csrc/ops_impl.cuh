@@ -203,16 +203,23 @@ inline int cq_pitch(const fsi_mesh* m) { return (m->g.nx + 3) & ~3; }
 // (slot = 8 * component + corner, element index ez * nxyp + ey * nxp + ex); a node
 // kernel then sums, per node, the slots of its up to 8 elements in a fixed order
 // (z, y, x).  Each element is evaluated once (no halo recomputation); deterministic.
+// the thread's position in a row_launch grid: x within the row (*x), row index returned
+__device__ __forceinline__ int64_t row_index(int len, int* x) {
+  const int nbx = (len + blockDim.x - 1) / blockDim.x;
+  const int64_t bxi = blockIdx.x % nbx, byi = blockIdx.x / nbx;
+  *x = (int)(bxi * blockDim.x + threadIdx.x);
+  return byi * blockDim.y + threadIdx.y;
+}
+
 struct ElemIdx {
   int ex, ey, ez;
   int64_t n0, e, es;
   int64_t off[8];
   __device__ __forceinline__ bool set(int nx, int ny, int nz, int nxp, int64_t nxyp) {
-    ex = blockIdx.x * blockDim.x + threadIdx.x;
-    const int eyz = blockIdx.y;
-    ey = eyz % ny;
-    ez = eyz / ny;
-    if (ex >= nx || ez >= nz) return false;
+    const int64_t eyz = row_index(nx, &ex);
+    ey = (int)(eyz % ny);
+    if (ex >= nx || eyz >= (int64_t)ny * nz) return false;
+    ez = (int)(eyz / ny);
     const int64_t sy = nx + 1, sz = (int64_t)(nx + 1) * (ny + 1);
     n0 = ex + sy * ey + sz * ez;
     off[0] = 0; off[1] = 1; off[2] = sy; off[3] = sy + 1;
@@ -223,8 +230,19 @@ struct ElemIdx {
   }
 };
 
-inline dim3 elem_grid(const Geom& g) { return dim3((g.nx + 127) / 128, (unsigned)((int64_t)g.ny * g.nz)); }
-inline dim3 node_grid(const Geom& g) { return dim3((g.nx + 1 + 127) / 128, (unsigned)((int64_t)(g.ny + 1) * (g.nz + 1))); }
+// Launch shape over rows of `len` items (elements or nodes along x), `rows` rows: CTAs of
+// bx x by threads (bx the row length rounded up to a warp, at most 128; by = 128 / bx
+// rows), numbered x-block fastest in a one-dimensional grid (no 65,535 limit on rows).
+struct RowLaunch {
+  dim3 grid, block;
+};
+inline RowLaunch row_launch(int len, int64_t rows) {
+  const int bx = std::min(128, (len + 31) / 32 * 32), by = 128 / bx;
+  const int64_t nbx = (len + bx - 1) / bx, nby = (rows + by - 1) / by;
+  return RowLaunch{dim3((unsigned)(nbx * nby)), dim3(bx, by)};
+}
+inline RowLaunch elem_launch(const Geom& g) { return row_launch(g.nx, (int64_t)g.ny * g.nz); }
+inline RowLaunch node_launch(const Geom& g) { return row_launch(g.nx + 1, (int64_t)(g.ny + 1) * (g.nz + 1)); }
 
 // NS node sums: y = W * sum of the element slots, the Dirichlet rows (velocity; pressure
 // at the pin node when pinned) take the increment itself (dx, or its float32 copy dx32)
@@ -233,10 +251,10 @@ __global__ void __launch_bounds__(128) ns_node_kernel(const T* __restrict__ E, i
                                                       int64_t nxyp, int64_t nn, double W, const uint8_t* __restrict__ mask,
                                                       int pin, const double* __restrict__ dx,
                                                       const float* __restrict__ dx32, double* __restrict__ y) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int jk = blockIdx.y;
-  const int j = jk % (ny + 1), k = jk / (ny + 1);
-  if (i > nx || k > nz) return;
+  int i;
+  const int64_t jk = row_index(nx + 1, &i);
+  if (i > nx || jk >= (int64_t)(ny + 1) * (nz + 1)) return;
+  const int j = (int)(jk % (ny + 1)), k = (int)(jk / (ny + 1));
   const int64_t n = i + (int64_t)(nx + 1) * (j + (int64_t)(ny + 1) * k);
   const int64_t es = (int64_t)nz * nxyp;
   T s[4] = {T(0), T(0), T(0), T(0)};
@@ -338,12 +356,13 @@ int launch_nsq(fsi_mesh* m, const double* dx, double* y, unsigned flags) {
   prof_bytes(m, jvp_class<T>(0),
              (double)ne * (8.0 * (elastic ? NCQ : NCQ_FLUID) + 32.0) * sizeof(T) + (double)nn * 4.0 * sizeof(T));
   prof_bytes(m, P_NODE_SUM, (double)ne * 32.0 * sizeof(T) + (double)nn * (32.0 + 1.0));
+  const RowLaunch el = elem_launch(g), nl = node_launch(g);
   FSI_LAUNCH(m, jvp_class<T>(0),
-             nsq_elem_kernel<T><<<elem_grid(g), 128, 0, m->stream>>>(
+             nsq_elem_kernel<T><<<el.grid, el.block, 0, m->stream>>>(
                  cq, xin, E, g.nx, g.ny, g.nz, nxp, nxyp, nn, elastic, T(m->P.alpha), T(m->P.c_mass), T(1.0 / g.hx),
                  T(1.0 / g.hy), T(1.0 / g.hz)));
   FSI_LAUNCH(m, P_NODE_SUM,
-             ns_node_kernel<T><<<node_grid(g), 128, 0, m->stream>>>(
+             ns_node_kernel<T><<<nl.grid, nl.block, 0, m->stream>>>(
                  E, g.nx, g.ny, g.nz, nxp, nxyp, nn, g.hx * g.hy * g.hz / 8.0, m->mask, m->pin_active,
                  dx, sizeof(T) == 4 ? m->dx32 : nullptr, y));
   return FSI_OK;
