@@ -48,7 +48,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner arm")
-    p.add_argument("--train-steps", type=int, default=3000)
+    p.add_argument("--train-steps", type=int, default=4000)
+    p.add_argument("--smooth-pairs", type=int, default=360,
+                   help="synthetic multi-scale training pairs added to the harvested ones")
     p.add_argument("--restart", type=int, default=30, help="GMRES restart length m (<= 64)")
     p.add_argument("--ir-inner-rtol", type=float, default=1e-3,
                    help="relative tolerance of each inner float32 solve of the refinement")
@@ -913,22 +915,28 @@ def run_gpu(args):
 
 
 def run_learned_arm(fsi, torch, mesh, pc, solve, step, state, snapshot, args, stream):
-    """Trains the network on the harvested pairs (timed apart), then replays the timed
-    steps from the same initial state with flexible GMRES + the network on the NS block
-    (Jacobi on the other blocks, and as the fallback); s/timestep to rel-res 1e-8."""
+    """Trains the network on the harvested pairs plus synthetic multi-scale pairs at the
+    warm-up's final state (timed apart), then replays the timed steps from the same
+    initial state with flexible GMRES on the NS block whose directions alternate between
+    the network and Jacobi (Jacobi on the other blocks, and as the fallback);
+    s/timestep to rel-res 1e-8."""
     import numpy as np
     x, xn, xdn = state
+    harvested = fsi.fsi_pc_pairs(pc)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if args.smooth_pairs > 0:
+        fsi.fsi_pc_add_smooth_pairs(pc, x, xn, xdn, args.smooth_pairs, seed=1)
     npairs = fsi.fsi_pc_pairs(pc)
     fsi.fsi_pc_fit_norm(pc)
     rng = np.random.default_rng(0)
     order = rng.integers(0, npairs, size=args.train_steps)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
     losses = fsi.fsi_pc_train(pc, order, 2e-4)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     opts = fsi.fsi_solve_opts.from_buffer_copy(solve)
     opts.precond = fsi.FSI_PC_LEARNED
+    opts.flags |= fsi.FSI_PC_ALTERNATE
 
     def restore():
         for dst, src in zip((x, xn, xdn), snapshot):
@@ -947,7 +955,9 @@ def run_learned_arm(fsi, torch, mesh, pc, solve, step, state, snapshot, args, st
     return {
         "network": "U-Net, 4 levels, 16 channels, 3x3x3 convolutions (tcgen05, bf16 x bf16 -> f32), "
                    "linear (no activation), inputs modulated by the solid indicator",
-        "pairs": npairs, "train_steps": args.train_steps, "train_s": round(train_s, 3),
+        "directions": "flexible GMRES, network and Jacobi directions alternately",
+        "pairs": npairs, "pairs_harvested": harvested, "pairs_smooth": npairs - harvested,
+        "train_steps": args.train_steps, "train_s": round(train_s, 3),
         "train_ms_per_step": round(1e3 * train_s / max(1, args.train_steps), 3),
         "relative_loss_first_last": [round(float(losses[:50].mean()), 4), round(float(losses[-200:].mean()), 4)],
         "s_per_timestep": round(ms / args.steps / 1e3, 5),

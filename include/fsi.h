@@ -390,6 +390,17 @@ int fsi_pc_apply(fsi_pc* pc, const fsi_state* st, const double* r, double* z);
  * an apply, target t_c = (e - D^{-1} r)_c sqrt(n) / (|r| dbar_c); the first pair
  * fixes dbar_c = mean of D^{-1}_c over non-Dirichlet rows */
 int fsi_pc_add_pair(fsi_pc* pc, const fsi_state* st, const double* r, const double* e);
+/* adds `count` synthetic training pairs (A z, z) of the NS block at the state st.  z: every
+ * component (v, p) a trilinear interpolation of standard normals on a coarse grid of 2, 4,
+ * 8, 16 or 32 intervals along the longest axis, or one normal per node (the six scales in
+ * turn), 0 on velocity Dirichlet rows, the pressure's mean removed; A: the NS block's
+ * Jacobian with the solid-stress linearization (Section 2.4), unpinned where fsi_step
+ * shifts the pressure.  The normals come from a counter-based generator keyed by seed
+ * (splitmix64 of the counter, Box-Muller).  The pairs enter the store as fsi_pc_add_pair's
+ * do (the oldest are overwritten beyond the capacity).  Synchronises the mesh's stream.
+ * Errors: FSI_EINVAL (null, count < 0, no pair storage, not the NS block's network, a
+ * tetrahedral mesh). */
+int fsi_pc_add_smooth_pairs(fsi_pc* pc, const fsi_state* st, int32_t count, uint64_t seed);
 int fsi_pc_pairs(const fsi_pc* pc, int32_t* n_pairs);
 /* kc_c = RMS of the stored targets' component c (non-Dirichlet rows) */
 int fsi_pc_fit_norm(fsi_pc* pc);

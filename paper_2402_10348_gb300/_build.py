@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libfsi.so")
 BUILD = os.path.join(HERE, "_build")
-UNITS = ["api.cu", "ops_f64.cu", "ops_f32.cu", "krylov.cu", "step.cu", "gridcell.cu", "noalloc.cu", "pcnet.cu", "batch.cu", "diag.cu", "probe.cu", "tet.cu"]
+UNITS = ["api.cu", "ops_f64.cu", "ops_f32.cu", "krylov.cu", "step.cu", "gridcell.cu", "noalloc.cu", "pcnet.cu", "batch.cu", "diag.cu", "probe.cu", "tet.cu", "nsq_tma.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 # the initialisation's integer results must not depend on FMA contraction

@@ -384,6 +384,7 @@ int fsi_destroy_mesh(fsi_mesh* m) {
   cudaFree(m->cq32);
   cudaFree(m->ke64);
   cudaFree(m->ke_e);
+  cudaFree(m->tma_err);
   cudaFree(m->ake64);
   cudaFree(m->bke64);
   tet_free(m->tet);

@@ -75,6 +75,11 @@ struct fsi_mesh {
   int64_t cq_len = 0;                // allocated coefficients (each array)
   int64_t cq_gen = -1;               // stage_gen of the last build
   unsigned cq_flags = 0;             // FSI_ELASTIC_AUG of the last build
+  // TMA descriptors of the float32 coefficients (boxes of 44 and of 20 values; nsq_tma.cu),
+  // encoded for the allocation at cq_tmap_base; tma_err: a bounded wait gave up
+  alignas(64) unsigned char cq_tmap[256] = {};
+  const void* cq_tmap_base = nullptr;
+  int* tma_err = nullptr;
   // float64 element matrices of the NS product (NSEOp), built from the coefficients once
   // a state has taken NSE_AFTER float64 products
   double* ke64 = nullptr;
@@ -170,6 +175,11 @@ template <typename T>
 int launch_ns(fsi_mesh* m, int mode, const double* dx, double* y, unsigned flags);
 // NS product from the quadrature-point coefficients (built first when stale)
 int ns_build(fsi_mesh* m, unsigned flags);  // ops_f64.cu
+// float32 NS product from the coefficients with TMA-staged coefficient boxes: the element
+// contributions into E (nsq_tma.cu)
+int launch_nsq_tma(fsi_mesh* m, int elastic, float* E, const double* dx, double* y);
+// FSI_ECUDA if a bounded wait of that kernel gave up since the flag was allocated (syncs)
+int check_tma(fsi_mesh* m);
 // [slots][elements] scratch of the element-centric products, grown on demand (ops_f64.cu)
 int ensure_elem_scratch(fsi_mesh* m, int slots, int64_t nxyp);
 // float64 NS product through element matrices (built first when stale), ops_f64.cu

@@ -1007,6 +1007,7 @@ int gmres_solve(fsi_mesh* m, const BlockInfo& blk, const double* rhs, double* x,
       }
     }
     rfin = r;
+    if ((rc = check_tma(m))) return rc;
   }
   if (harvest) {
     // pairs (r_k - r*, x* - x_k): A (x* - x_k) = r_k - r* holds exactly for the

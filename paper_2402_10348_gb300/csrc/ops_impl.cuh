@@ -357,10 +357,16 @@ int launch_nsq(fsi_mesh* m, const double* dx, double* y, unsigned flags) {
              (double)ne * (8.0 * (elastic ? NCQ : NCQ_FLUID) + 32.0) * sizeof(T) + (double)nn * 4.0 * sizeof(T));
   prof_bytes(m, P_NODE_SUM, (double)ne * 32.0 * sizeof(T) + (double)nn * (32.0 + 1.0));
   const RowLaunch el = elem_launch(g), nl = node_launch(g);
-  FSI_LAUNCH(m, jvp_class<T>(0),
-             nsq_elem_kernel<T><<<el.grid, el.block, 0, m->stream>>>(
-                 cq, xin, E, g.nx, g.ny, g.nz, nxp, nxyp, nn, elastic, T(m->P.alpha), T(m->P.c_mass), T(1.0 / g.hx),
-                 T(1.0 / g.hy), T(1.0 / g.hz)));
+  if constexpr (sizeof(T) == 4) {
+    (void)cq;
+    (void)xin;
+    if (int rc = launch_nsq_tma(m, elastic, E, dx, y)) return rc;
+  } else {
+    FSI_LAUNCH(m, jvp_class<T>(0),
+               nsq_elem_kernel<T><<<el.grid, el.block, 0, m->stream>>>(
+                   cq, xin, E, g.nx, g.ny, g.nz, nxp, nxyp, nn, elastic, T(m->P.alpha), T(m->P.c_mass),
+                   T(1.0 / g.hx), T(1.0 / g.hy), T(1.0 / g.hz)));
+  }
   FSI_LAUNCH(m, P_NODE_SUM,
              ns_node_kernel<T><<<nl.grid, nl.block, 0, m->stream>>>(
                  E, g.nx, g.ny, g.nz, nxp, nxyp, nn, g.hx * g.hy * g.hz / 8.0, m->mask, m->pin_active,

@@ -1385,6 +1385,120 @@ int fsi_pc_apply(fsi_pc* pc, const fsi_state* st, const double* r, double* z) {
   return check_err(pc);
 }
 
+namespace fsi {
+namespace pcn {
+// --------------------------------------------------- synthetic smooth training pairs
+// A counter-based standard normal per (key, field, coarse node): the splitmix64 finaliser
+// of the counter gives two uniforms, Box-Muller gives the normal.
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+__device__ __forceinline__ double normal_at(uint64_t key) {
+  const uint64_t a = mix64(key), b = mix64(key ^ 0xD1B54A32D192ED03ull);
+  const double u1 = ((double)(a >> 11) + 0.5) * 0x1.0p-53, u2 = ((double)(b >> 11) + 0.5) * 0x1.0p-53;
+  return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
+// z_f(node) = trilinear interpolation of normals on a coarse grid of L[axis] intervals
+// spanning the box (L = the mesh's own intervals: a normal per node); velocity rows with a
+// Dirichlet condition are 0.  Per CTA partial sums of the pressure into part[cta].
+__global__ void smooth_field_kernel(double* __restrict__ z, int nx, int ny, int nz, int lx, int ly, int lz,
+                                    uint64_t key, const uint8_t* __restrict__ mask, int64_t nn,
+                                    double* __restrict__ part) {
+  double psum = 0.0;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < nn; n += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(n % (nx + 1));
+    const int j = (int)((n / (nx + 1)) % (ny + 1));
+    const int k = (int)(n / ((int64_t)(nx + 1) * (ny + 1)));
+    const double ux = (double)i * lx / nx, uy = (double)j * ly / ny, uz = (double)k * lz / nz;
+    const int cx = min((int)ux, lx - 1), cy = min((int)uy, ly - 1), cz = min((int)uz, lz - 1);
+    const double tx = ux - cx, ty = uy - cy, tz = uz - cz;
+    const uint8_t mk = mask[n];
+    for (int f = 0; f < 4; ++f) {
+      double v = 0.0;
+      for (int c = 0; c < 8; ++c) {
+        const int ax = c & 1, ay = (c >> 1) & 1, az = (c >> 2) & 1;
+        const double w = (ax ? tx : 1.0 - tx) * (ay ? ty : 1.0 - ty) * (az ? tz : 1.0 - tz);
+        const uint64_t id = (((uint64_t)(cz + az) * (ly + 1) + (cy + ay)) * (lx + 1) + (cx + ax)) * 4 + f;
+        v += w * normal_at(key ^ mix64(id));
+      }
+      if (f < 3 && ((mk >> f) & 1)) v = 0.0;
+      z[f * nn + n] = v;
+      if (f == 3) psum += v;
+    }
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = psum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) t += red[i];
+    part[blockIdx.x] = t;
+  }
+}
+
+// p -= mean(p), the mean summed from the CTA partials in a fixed order
+__global__ void sub_mean_kernel(double* __restrict__ p, const double* __restrict__ part, int nparts, int64_t nn) {
+  double t = 0.0;
+  for (int i = 0; i < nparts; ++i) t += part[i];
+  const double mean = t / (double)nn;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < nn; n += (int64_t)gridDim.x * blockDim.x)
+    p[n] -= mean;
+}
+}  // namespace pcn
+}  // namespace fsi
+
+int fsi_pc_add_smooth_pairs(fsi_pc* pc, const fsi_state* st, int32_t count, uint64_t seed) {
+  if (!pc || !st || count < 0) return set_error(FSI_EINVAL, "fsi_pc_add_smooth_pairs: bad argument");
+  if (pc->cap <= 0) return set_error(FSI_EINVAL, "fsi_pc_add_smooth_pairs: the preconditioner holds no pair storage");
+  if (pc->ncomp != 4) return set_error(FSI_EINVAL, "fsi_pc_add_smooth_pairs: the preconditioner is not the NS block's");
+  fsi_mesh* m = pc->m;
+  if (m->tet) return set_error(FSI_EINVAL, "fsi_pc_add_smooth_pairs: structured meshes only");
+  int rc;
+  if ((rc = stage(m, st, false))) return rc;
+  BlockInfo b;
+  if ((rc = block_info(m, FSI_BLOCK_NS, &b))) return rc;
+  // the system of the step's NS solves: unpinned where the step shifts the pressure
+  PinGuard guard(m, shifts_pressure(m, FSI_ELASTIC_AUG) ? 0 : m->pin_active);
+  if (sizeof(double) * b.n > sizeof(uint16_t) * 4 * pc->lv[0].nv() * 8)
+    return set_error(FSI_EINVAL, "fsi_pc_add_smooth_pairs: scratch too small");
+  double* dinv = reinterpret_cast<double*>(pc->gcat[0]);
+  if ((rc = op_diag(m, b, dinv, FSI_ELASTIC_AUG))) return rc;
+  if ((rc = vec_recip(m, dinv, dinv, b.n))) return rc;
+  double *z = nullptr, *y = nullptr, *part = nullptr;
+  constexpr int NB = 152;
+  FSI_CUDA(cudaMalloc(&z, sizeof(double) * 2 * b.n + sizeof(double) * NB));
+  y = z + b.n;
+  part = y + b.n;
+  const Geom& g = m->g;
+  const int nmax = std::max(g.nx, std::max(g.ny, g.nz));
+  for (int32_t k = 0; k < count && rc == FSI_OK; ++k) {
+    // coarse spacing 2, 4, 8, 16, 32 intervals along the longest axis, then every node
+    const int level = k % 6;
+    auto coarse = [&](int n) {
+      if (level == 5) return n;
+      const int l = (int)std::lround((double)(2 << level) * n / nmax);
+      return std::max(1, std::min(n, l));
+    };
+    const uint64_t key = seed * 0x2545F4914F6CDD1Dull + (uint64_t)k;
+    FSI_LAUNCH(m, P_PC_AUX, (fsi::pcn::smooth_field_kernel<<<NB, 256, 0, m->stream>>>(
+                                z, g.nx, g.ny, g.nz, coarse(g.nx), coarse(g.ny), coarse(g.nz), key, m->mask, m->nn,
+                                part)));
+    FSI_LAUNCH(m, P_PC_AUX, (fsi::pcn::sub_mean_kernel<<<vgrid1(m->nn), 256, 0, m->stream>>>(z + 3 * m->nn, part,
+                                                                                             NB, m->nn)));
+    if ((rc = op_jvp(m, b, z, y, FSI_ELASTIC_AUG))) break;
+    rc = fsi::pcn::add_pair(pc, y, nullptr, z, nullptr, dinv);
+  }
+  const cudaError_t se = cudaStreamSynchronize(m->stream);
+  cudaFree(z);
+  if (rc) return rc;
+  if (se != cudaSuccess) return set_error(FSI_ECUDA, cudaGetErrorString(se));
+  return FSI_OK;
+}
+
 int fsi_pc_add_pair(fsi_pc* pc, const fsi_state* st, const double* r, const double* e) {
   if (!pc || !st || !r || !e) return set_error(FSI_EINVAL, "fsi_pc_add_pair: null argument");
   if (pc->cap <= 0) return set_error(FSI_EINVAL, "fsi_pc_add_pair: the preconditioner holds no pair storage");

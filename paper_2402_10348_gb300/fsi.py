@@ -112,7 +112,7 @@ EXPORTS = ["fsi_create_mesh", "fsi_destroy_mesh", "fsi_set_stream", "fsi_mesh_in
            "fsi_gmres", "fsi_step", "fsi_init_phases", "fsi_gamma_beta_noalloc", "fsi_profile",
            "fsi_profile_read", "fsi_pc_create", "fsi_pc_destroy", "fsi_pc_layout", "fsi_pc_set_weights",
            "fsi_pc_get_weights", "fsi_pc_set_norm", "fsi_pc_get_norm", "fsi_pc_forward", "fsi_pc_grad",
-           "fsi_pc_apply", "fsi_pc_add_pair", "fsi_pc_pairs", "fsi_pc_fit_norm", "fsi_pc_train", "fsi_set_pc",
+           "fsi_pc_apply", "fsi_pc_add_pair", "fsi_pc_add_smooth_pairs", "fsi_pc_pairs", "fsi_pc_fit_norm", "fsi_pc_train", "fsi_set_pc",
            "fsi_batch_create", "fsi_batch_destroy", "fsi_batch_layout", "fsi_batch_jvp", "fsi_batch_gmres",
            "fsi_batch_autotune", "fsi_batch_set_graph", "fsi_center_of_mass", "fsi_track_points",
            "fsi_probe_peaks", "fsi_batch_create_blocks", "fsi_batch_stepper_create", "fsi_batch_stepper_destroy",
@@ -460,6 +460,11 @@ def fsi_pc_apply(pc: PC, x, xn, xdn, r, z):
 def fsi_pc_add_pair(pc: PC, x, xn, xdn, r, e):
     st = _state(x, xn, xdn)
     _check(lib().fsi_pc_add_pair(pc.handle, C.byref(st), _dptr(r), _dptr(e)))
+
+
+def fsi_pc_add_smooth_pairs(pc: PC, x, xn, xdn, count: int, seed: int = 0):
+    st = _state(x, xn, xdn)
+    _check(lib().fsi_pc_add_smooth_pairs(pc.handle, C.byref(st), C.c_int32(count), C.c_uint64(seed)))
 
 
 def fsi_pc_pairs(pc: PC) -> int:
