@@ -49,6 +49,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner arm")
     p.add_argument("--train-steps", type=int, default=4000)
+    p.add_argument("--solve-block", default="ns", choices=["ns", "ac", "b"], help="block of --case solve")
     p.add_argument("--smooth-pairs", type=int, default=360,
                    help="synthetic multi-scale training pairs added to the harvested ones")
     p.add_argument("--restart", type=int, default=30, help="GMRES restart length m (<= 64)")
@@ -67,11 +68,12 @@ def parse():
     return p.parse_args()
 
 
-def run_solve_case(precision: str = "fp32ir"):
-    """Forty Arnoldi steps of the NS block of the 64^3 cavity, float32 operator inside
-    float64 refinement (fp32ir: the coefficient product in float32) or float64 (the first
-    8 products from the coefficients, the rest through element matrices): the launch
-    sequences the profiles under profiles/ were captured on."""
+def run_solve_case(precision: str = "fp32ir", block: str = "ns"):
+    """Forty Arnoldi steps of one block of the 64^3 cavity (ns, ac: phase 0, b: the solid),
+    float32 operator inside float64 refinement (fp32ir: the NS coefficient product in
+    float32) or float64 (NS: the first 8 products from the coefficients, the rest through
+    element matrices; AC: element matrices from the third product; B: the split operator):
+    the launch sequences the profiles under profiles/ were captured on."""
     import torch
     from paper_2402_10348_gb300 import fsi
     from workloads import cavity64
@@ -82,14 +84,17 @@ def run_solve_case(precision: str = "fp32ir"):
     fsi.fsi_set_stream(mesh)
     x, xn, xdn = initial_state(fsi, mesh, wl, torch, dev)
     g = torch.Generator(device=dev).manual_seed(0)
-    rhs = torch.randn(4 * d.nn, dtype=torch.float64, device=dev, generator=g)
+    blk, ncomp = {"ns": (fsi.FSI_BLOCK_NS, 4), "ac": (fsi.FSI_BLOCK_AC(0), 1), "b": (fsi.FSI_BLOCK_B(0), 6)}[block]
+    if block == "ac":
+        fsi.fsi_set_ac_coeffs(mesh, 0, 0.5, 0.0)
+    rhs = torch.randn(ncomp * d.nn, dtype=torch.float64, device=dev, generator=g)
     sol = torch.zeros_like(rhs)
     prec = fsi.FSI_PREC_FP32_IR if precision == "fp32ir" else fsi.FSI_PREC_FP64
     o = fsi.solve_opts(m=64, rtol=1e-30, max_iter=40, precision=prec, ir_max=1, ir_inner_rtol=1e-30)
     o.flags |= fsi.FSI_NO_STALL_STOP
-    info = fsi.fsi_gmres(mesh, fsi.FSI_BLOCK_NS, x, xn, xdn, rhs, sol, o, allow_noconv=True)
+    info = fsi.fsi_gmres(mesh, blk, x, xn, xdn, rhs, sol, o, allow_noconv=True)
     torch.cuda.synchronize()
-    print(f"solve case ({precision}): {info.iterations} iterations")
+    print(f"solve case ({block}, {precision}): {info.iterations} iterations")
 
 
 def pc_flops_per_forward(grids, fan):
@@ -1121,7 +1126,7 @@ def main():
     elif args.case == "diagnostics":
         run_diagnostics_case()
     elif args.case == "solve":
-        run_solve_case(args.precision if "--precision" in sys.argv else "fp32ir")
+        run_solve_case(args.precision if "--precision" in sys.argv else "fp32ir", args.solve_block)
     else:
         run_gpu(args)
 

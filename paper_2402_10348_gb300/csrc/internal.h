@@ -80,7 +80,7 @@ struct fsi_mesh {
   alignas(64) unsigned char cq_tmap[256] = {};
   const void* cq_tmap_base = nullptr;
   int* tma_err = nullptr;
-  // float64 element matrices of the NS product (NSEOp), built from the coefficients once
+  // float64 element matrices of the NS product (nse_elem_kernel), built from the coefficients once
   // a state has taken NSE_AFTER float64 products
   double* ke64 = nullptr;
   int64_t ke_len = 0;
