@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--restart", type=int, default=30, help="GMRES restart length m (<= 64)")
     p.add_argument("--ir-inner-rtol", type=float, default=1e-3,
                    help="relative tolerance of each inner float32 solve of the refinement")
-    p.add_argument("--case", default="step", choices=["step", "solve", "pcnet", "batch", "mixed", "operators", "diagnostics"],
+    p.add_argument("--case", default="step", choices=["step", "solve", "pcnet", "batch", "mixed", "operators", "diagnostics", "tet"],
                    help="solve: only a fixed 40-iteration float32-IR NS GMRES solve at 64^3 (a short, "
                         "repeatable launch sequence for ncu captures); pcnet: learned-preconditioner "
                         "applies and training steps at 64^3 with per-kernel timing (JSON on stdout); "
@@ -392,6 +392,59 @@ def run_operators_case(reps: int = 3):
     dev = torch.device("cuda", 0)
     out = {wl.name: operator_rates_of(wl, fsi, torch, dev, reps) for wl in (cavity64(), falling(), shipice())}
     print(json.dumps({"case": "operators", "reps": reps, "unit": "GDoF/s per apply", "configs": out}), flush=True)
+
+
+def run_tet_case(reps: int = 5):
+    """Per-apply device times of the float64 operators on linear tetrahedra (six per box
+    cell, interior nodes jittered by 0.2 h): the 64^3 cavity's box (1.57 M elements) and
+    the falling sphere's 96x96x192 box (10.6 M elements), on seeded random states.  Each
+    apply is an element kernel plus a node-sum kernel; time per apply = class time / calls."""
+    import torch
+    from paper_2402_10348_gb300 import fsi
+    from workloads import cavity64, falling, random_state, tet_box_mesh
+    dev = torch.device("cuda", 0)
+    out = {}
+    for wl in (cavity64(), falling()):
+        d = wl.desc
+        X, conn = tet_box_mesh(d, 0.2, seed=1)
+        mesh = fsi.fsi_create_tet_mesh(d, X, conn)
+        fsi.fsi_set_stream(mesh)
+        st = [torch.from_numpy(a.ravel()).to(dev) for a in random_state(d, 0)]
+        nn = d.nn
+        for i in range(d.n_phase):
+            fsi.fsi_set_ac_coeffs(mesh, i, 0.5, 0.1)
+        calls = {
+            "ns_residual": (lambda y: fsi.fsi_residual(mesh, fsi.FSI_BLOCK_NS, *st, y), 4),
+            "ns_jvp_f64": (lambda y: fsi.fsi_jvp(mesh, fsi.FSI_BLOCK_NS, *st, dxs[4], y, fsi.FSI_ELASTIC_AUG), 4),
+            "ns_diag": (lambda y: fsi.fsi_diag(mesh, fsi.FSI_BLOCK_NS, *st, y, fsi.FSI_ELASTIC_AUG), 4),
+            "ac_jvp_f64": (lambda y: fsi.fsi_jvp(mesh, fsi.FSI_BLOCK_AC(0), *st, dxs[1], y), 1),
+            "b_jvp_f64": (lambda y: fsi.fsi_jvp(mesh, fsi.FSI_BLOCK_B(0), *st, dxs[6], y), 6),
+        }
+        g = torch.Generator(device=dev).manual_seed(0)
+        dxs = {c: torch.randn(c * nn, dtype=torch.float64, device=dev, generator=g) for c in (1, 4, 6)}
+        res = {}
+        for name, (fn, c) in calls.items():
+            y = torch.zeros(c * nn, dtype=torch.float64, device=dev)
+            fn(y)  # warm
+            torch.cuda.synchronize()
+            fsi.fsi_profile(mesh, True)
+            for _ in range(reps):
+                fn(y)
+            torch.cuda.synchronize()
+            prof = fsi.fsi_profile_read(mesh)
+            fsi.fsi_profile(mesh, False)
+            ms = prof.get(name, (0, 0.0))[1] / reps
+            res[name] = {"ms_per_apply": round(ms, 3), "gdofs": round(c * nn / (ms / 1e3) / 1e9, 3) if ms > 0 else None}
+        fsi.fsi_profile(mesh, True)
+        for _ in range(reps):
+            fsi.fsi_update_ac_coeffs(mesh, 0, *st)
+        prof = fsi.fsi_profile_read(mesh)
+        fsi.fsi_profile(mesh, False)
+        res["gamma_beta"] = {"ms_per_call": round(prof.get("gamma_beta", (0, 0.0))[1] / reps, 3)}
+        out[wl.name] = {"elements": int(conn.shape[0]), "nodes": nn, "operators": res}
+        del mesh
+        torch.cuda.empty_cache()
+    print(json.dumps({"case": "tet", "reps": reps, "precision": "float64", "configs": out}), flush=True)
 
 
 def run_diagnostics_case(reps: int = 20):
@@ -1125,6 +1178,8 @@ def main():
         run_operators_case()
     elif args.case == "diagnostics":
         run_diagnostics_case()
+    elif args.case == "tet":
+        run_tet_case()
     elif args.case == "solve":
         run_solve_case(args.precision if "--precision" in sys.argv else "fp32ir", args.solve_block)
     else:

@@ -24,27 +24,16 @@ it through TetProblem.
 """
 from __future__ import annotations
 
-import itertools
 
 import numpy as np
 
-from workloads import MeshDesc
+from workloads import MeshDesc, tet_box_mesh  # the seeded input mesh
 
 from .fields import Problem
 
 _A = (5.0 + 3.0 * np.sqrt(5.0)) / 20.0
 _B = (5.0 - np.sqrt(5.0)) / 20.0
 QBARY = np.array([[_A, _B, _B, _B], [_B, _A, _B, _B], [_B, _B, _A, _B], [_B, _B, _B, _A]])  # (4q, 4a)
-
-
-def kuhn_corners():
-    """(6, 4) cell corners of the six tetrahedra: 0 -> e_p1 -> e_p1 + e_p2 -> 7."""
-    out = []
-    for p in itertools.permutations(range(3)):
-        c1 = 1 << p[0]
-        c2 = c1 | (1 << p[1])
-        out.append([0, c1, c2, 7])
-    return np.array(out)
 
 
 class TetMesh:
@@ -56,24 +45,8 @@ class TetMesh:
         self.nn = (nx + 1) * (ny + 1) * (nz + 1)
         h = desc.h
         self.h = h
-        i, j, k = self.ijk()
-        X = np.stack([i * h[0], j * h[1], k * h[2]]).astype(np.float64)
-        if jitter > 0.0:
-            rng = np.random.default_rng(seed)
-            inner = (i > 0) & (i < nx) & (j > 0) & (j < ny) & (k > 0) & (k < nz)
-            d = rng.uniform(-jitter, jitter, size=(3, self.nn)) * np.array(h)[:, None]
-            X[:, inner] += d[:, inner]
+        X, conn = tet_box_mesh(desc, jitter, seed)  # element e = 6 * cell + t, positive orientation
         self.X = X
-        ex, ey, ez = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
-        ex, ey, ez = (a.transpose(2, 1, 0).ravel() for a in (ex, ey, ez))
-        cells = np.empty((ex.size, 8), dtype=np.int64)
-        for a in range(8):
-            cells[:, a] = (ex + (a & 1)) + (nx + 1) * ((ey + ((a >> 1) & 1)) + (ny + 1) * (ez + ((a >> 2) & 1)))
-        conn = cells[:, kuhn_corners()].reshape(-1, 4)  # element e = 6 * cell + t
-        # positive orientation: det(x1 - x0, x2 - x0, x3 - x0) > 0
-        J = np.stack([X[:, conn[:, a]].T - X[:, conn[:, 0]].T for a in (1, 2, 3)], axis=2)  # (ne, 3, 3) columns
-        neg = np.linalg.det(J) < 0
-        conn[neg] = conn[neg][:, [0, 2, 1, 3]]
         self.conn = conn
         self.ne = conn.shape[0]
         J = np.stack([X[:, conn[:, a]].T - X[:, conn[:, 0]].T for a in (1, 2, 3)], axis=2)

@@ -381,6 +381,47 @@ def random_state(desc: MeshDesc, seed: int, amp_v: float = 1.0, amp_B: float = 0
     return x1, xn, xdn
 
 
+def kuhn_corners() -> np.ndarray:
+    """(6, 4) cell corners (bit 0 x, bit 1 y, bit 2 z) of the six tetrahedra around the
+    cell diagonal 0 -> 7: 0 -> e_p1 -> e_p1 + e_p2 -> 7 for each permutation p of the axes."""
+    import itertools
+    out = []
+    for p in itertools.permutations(range(3)):
+        c1 = 1 << p[0]
+        c2 = c1 | (1 << p[1])
+        out.append([0, c1, c2, 7])
+    return np.array(out)
+
+
+def tet_box_mesh(desc: MeshDesc, jitter: float = 0.0, seed: int = 0):
+    """Linear tetrahedra on a box grid's nodes: (X (3, nn) coordinates, conn (ne, 4) int64),
+    six tetrahedra per cell (element e = 6 x cell + t, cells x fastest), interior nodes
+    moved by uniform offsets in [-jitter, jitter] x h per axis (numpy.random.default_rng(seed)),
+    each element's corners ordered for a positive volume."""
+    nx, ny, nz = desc.nx, desc.ny, desc.nz
+    nn = (nx + 1) * (ny + 1) * (nz + 1)
+    h = desc.h
+    n = np.arange(nn)
+    i, j, k = n % (nx + 1), (n // (nx + 1)) % (ny + 1), n // ((nx + 1) * (ny + 1))
+    X = np.stack([i * h[0], j * h[1], k * h[2]]).astype(np.float64)
+    if jitter > 0.0:
+        rng = np.random.default_rng(seed)
+        inner = (i > 0) & (i < nx) & (j > 0) & (j < ny) & (k > 0) & (k < nz)
+        d = rng.uniform(-jitter, jitter, size=(3, nn)) * np.array(h)[:, None]
+        X[:, inner] += d[:, inner]
+    ex, ey, ez = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    ex, ey, ez = (a.transpose(2, 1, 0).ravel() for a in (ex, ey, ez))
+    cells = np.empty((ex.size, 8), dtype=np.int64)
+    for a in range(8):
+        cells[:, a] = (ex + (a & 1)) + (nx + 1) * ((ey + ((a >> 1) & 1)) + (ny + 1) * (ez + ((a >> 2) & 1)))
+    conn = cells[:, kuhn_corners()].reshape(-1, 4)
+    e1, e2, e3 = (X[:, conn[:, a]] - X[:, conn[:, 0]] for a in (1, 2, 3))
+    det = np.einsum("ie,ie->e", e1, np.cross(e2.T, e3.T).T)
+    neg = det < 0
+    conn[neg] = conn[neg][:, [0, 2, 1, 3]]
+    return X, conn
+
+
 def random_vector(n: int, seed: int) -> np.ndarray:
     return np.random.default_rng(seed).normal(size=n)
 
