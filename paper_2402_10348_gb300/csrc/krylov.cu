@@ -250,6 +250,61 @@ __global__ void __launch_bounds__(VB) upd_kernel(double* __restrict__ w, const V
   block_reduce_store<1>(nd, 1, part + blockIdx.x, 1);
 }
 
+// The second-pass update for the float32 basis, laid out as mdot4_kernel: a CTA works on
+// four chunks at a time, a thread on four adjacent elements (one float4 per basis vector,
+// two double2 of w).  part[cta] = partial of |w|^2 (float32 up to the CTA's sum).
+__global__ void __launch_bounds__(VB) upd4_kernel(double* __restrict__ w, const float* __restrict__ V, int M1, int k,
+                                                  const double* __restrict__ h, int64_t n, double* part,
+                                                  const int* skip) {
+  if (skip && !*skip) return;
+  __shared__ float hs[MMAX + 2];
+  for (int i = threadIdx.x; i < k; i += VB) hs[i] = (float)h[i];
+  __syncthreads();
+  const int G = gridDim.x;
+  const int64_t nch = (n + CH - 1) / CH;
+  const int64_t per = (nch + G - 1) / G;
+  const int64_t c0 = blockIdx.x * per, c1 = min(nch, c0 + per);
+  const int sub = threadIdx.x >> 6;
+  const int e0 = (threadIdx.x & 63) * 4;
+  float nrm = 0.f;
+  for (int64_t c = c0 + sub; c < c1; c += 4) {
+    const int64_t j = c * CH + e0;
+    if (j >= n) break;
+    const float* blk = V + c * (int64_t)M1 * CH + e0;
+    if (j + 4 <= n) {
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+      int i = 0;
+      for (; i + 2 <= k; i += 2) {
+        const float4 v0 = *reinterpret_cast<const float4*>(blk + i * CH);
+        const float4 v1 = *reinterpret_cast<const float4*>(blk + (i + 1) * CH);
+        a.x += hs[i] * v0.x; a.y += hs[i] * v0.y; a.z += hs[i] * v0.z; a.w += hs[i] * v0.w;
+        b.x += hs[i + 1] * v1.x; b.y += hs[i + 1] * v1.y; b.z += hs[i + 1] * v1.z; b.w += hs[i + 1] * v1.w;
+      }
+      if (i < k) {
+        const float4 v0 = *reinterpret_cast<const float4*>(blk + i * CH);
+        a.x += hs[i] * v0.x; a.y += hs[i] * v0.y; a.z += hs[i] * v0.z; a.w += hs[i] * v0.w;
+      }
+      const double2 w01 = *reinterpret_cast<const double2*>(w + j);
+      const double2 w23 = *reinterpret_cast<const double2*>(w + j + 2);
+      const float s0 = (float)w01.x - (a.x + b.x), s1 = (float)w01.y - (a.y + b.y);
+      const float s2 = (float)w23.x - (a.z + b.z), s3 = (float)w23.y - (a.w + b.w);
+      *reinterpret_cast<double2*>(w + j) = make_double2((double)s0, (double)s1);
+      *reinterpret_cast<double2*>(w + j + 2) = make_double2((double)s2, (double)s3);
+      nrm += (s0 * s0 + s1 * s1) + (s2 * s2 + s3 * s3);
+    } else {
+      for (int e = 0; e < 4 && j + e < n; ++e) {
+        float acc = 0.f;
+        for (int i = 0; i < k; ++i) acc += hs[i] * blk[i * CH + e];
+        const float se = (float)w[j + e] - acc;
+        w[j + e] = (double)se;
+        nrm += se * se;
+      }
+    }
+  }
+  float acc[1] = {nrm};
+  block_reduce_store_f<1>(acc, 1, part + blockIdx.x, 1);
+}
+
 // Pass-1 update fused with the pass-2 projections: w' = w - sum_{i<k} h_i V_i, the
 // partial |w'|^2 and the partial V_i . w' (i < k) of the updated vector, from one read
 // of the basis: a thread keeps the k basis values of its element in registers, uses
@@ -416,9 +471,13 @@ __global__ void store_slot(VT* __restrict__ V, int M1, int slot, const double* _
     const double nf = K->nrm_fin;
     s = nf > 0.0 ? 1.0 / nf : 0.0;
   }
-  for (int64_t j = blockIdx.x * (int64_t)VB + threadIdx.x; j < n; j += (int64_t)gridDim.x * VB) {
+  // one chunk of CH = VB elements per CTA pass
+  const int64_t nch = (n + CH - 1) / CH;
+  for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
+    const int64_t j = c * CH + threadIdx.x;
+    if (j >= n) continue;
     const VT v = (VT)(src[j] * s);
-    V[(j / CH) * (int64_t)M1 * CH + (int64_t)slot * CH + (j % CH)] = v;
+    V[c * (int64_t)M1 * CH + (int64_t)slot * CH + threadIdx.x] = v;
     if (z) z[j] = (VT)(dinv[j] * (double)v);
   }
 }
@@ -427,8 +486,11 @@ __global__ void store_slot(VT* __restrict__ V, int M1, int slot, const double* _
 template <typename VT, typename ZT>
 __global__ void precond_kernel(const VT* __restrict__ V, int M1, int slot, const double* __restrict__ dinv,
                                ZT* __restrict__ z, int64_t n) {
-  for (int64_t j = blockIdx.x * (int64_t)VB + threadIdx.x; j < n; j += (int64_t)gridDim.x * VB)
-    z[j] = (ZT)(dinv[j] * (double)V[(j / CH) * (int64_t)M1 * CH + (int64_t)slot * CH + (j % CH)]);
+  const int64_t nch = (n + CH - 1) / CH;
+  for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
+    const int64_t j = c * CH + threadIdx.x;
+    if (j < n) z[j] = (ZT)(dinv[j] * (double)V[c * (int64_t)M1 * CH + (int64_t)slot * CH + threadIdx.x]);
+  }
 }
 
 // x += dinv * sum_i y_i V_i
@@ -450,8 +512,11 @@ __global__ void __launch_bounds__(VB) combine_kernel(double* __restrict__ x, con
 // z = V_slot (contiguous float64 copy of one basis vector)
 template <typename VT>
 __global__ void extract_kernel(const VT* __restrict__ V, int M1, int slot, double* __restrict__ z, int64_t n) {
-  for (int64_t j = blockIdx.x * (int64_t)VB + threadIdx.x; j < n; j += (int64_t)gridDim.x * VB)
-    z[j] = (double)V[(j / CH) * (int64_t)M1 * CH + (int64_t)slot * CH + (j % CH)];
+  const int64_t nch = (n + CH - 1) / CH;
+  for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
+    const int64_t j = c * CH + threadIdx.x;
+    if (j < n) z[j] = (double)V[c * (int64_t)M1 * CH + (int64_t)slot * CH + threadIdx.x];
+  }
 }
 
 // x += sum_i y_i Z_i (flexible GMRES: the stored preconditioned directions)
@@ -480,32 +545,6 @@ __device__ void orth_decide_body(KryDev* K, int j) {
   K->nrm_fin = nn;
 }
 
-// After the (possible) second pass: fold h2 into h, rotate, update the estimate.
-__device__ void givens_body(KryDev* K, int j, int mm) {
-  if (K->reorth) {
-    for (int i = 0; i <= j; ++i) K->h[i] += K->h2[i];
-    K->nrm_fin = sqrt(K->nrm_new);
-  }
-  double* col = K->H;  // column j stored at H[i*mm + j]
-  for (int i = 0; i <= j; ++i) col[i * mm + j] = K->h[i];
-  const double hn = K->nrm_fin;
-  col[(j + 1) * mm + j] = hn;
-  for (int i = 0; i < j; ++i) {
-    const double a = K->cs[i] * col[i * mm + j] + K->sn[i] * col[(i + 1) * mm + j];
-    col[(i + 1) * mm + j] = -K->sn[i] * col[i * mm + j] + K->cs[i] * col[(i + 1) * mm + j];
-    col[i * mm + j] = a;
-  }
-  const double den = hypot(col[j * mm + j], col[(j + 1) * mm + j]);
-  K->cs[j] = den > 0.0 ? col[j * mm + j] / den : 1.0;
-  K->sn[j] = den > 0.0 ? col[(j + 1) * mm + j] / den : 0.0;
-  col[j * mm + j] = den;
-  col[(j + 1) * mm + j] = 0.0;
-  K->g[j + 1] = -K->sn[j] * K->g[j];
-  K->g[j] = K->cs[j] * K->g[j];
-  K->est = fabs(K->g[j + 1]) / K->bnorm;
-  K->breakdown = (hn == 0.0 || den == 0.0 || !isfinite(hn)) ? 1 : 0;
-}
-
 // Rows of the fused update's partials into K->h2 (one CTA per row, fixed order); the last
 // CTA to finish takes the DGKS decision, so no single-thread launch follows.
 __global__ void sum_partials_decide(const double* __restrict__ part, int G, KryDev* K, int j) {
@@ -530,18 +569,63 @@ __global__ void sum_partials_decide(const double* __restrict__ part, int G, KryD
   }
 }
 
-// The second pass's |w|^2 (only when it ran) and the Givens step, in one CTA.
+// The second pass's |w|^2 (only when it ran) and the Givens step, in one CTA: the column,
+// the rotations and the right-hand side are read into shared memory by all threads, one
+// thread applies the rotations there (a chain of shared-memory operations, not of global
+// loads), and the column goes back in parallel.  Column j of the Hessenberg matrix (h,
+// plus h2 when the second pass ran, and the new norm below it) is rotated by the previous
+// rotations, the new rotation zeroes its subdiagonal entry, and g and the residual
+// estimate |g_{j+1}| / |b| follow.
 __global__ void sum_partials_givens(const double* __restrict__ part, int G, KryDev* K, int j, int mm) {
-  if (K->reorth) {
+  __shared__ double col[MMAX + 2], cs[MMAX], sn[MMAX];
+  __shared__ double res;
+  const int reorth = K->reorth;
+  if (reorth) {
     double s = 0.0;
     for (int c = threadIdx.x; c < G; c += VB) s += part[c];
     double acc[1] = {s};
-    __shared__ double res;
     block_reduce_store<1>(acc, 1, &res, 1);
-    __syncthreads();
-    if (threadIdx.x == 0) K->nrm_new = res;
   }
-  if (threadIdx.x == 0) givens_body(K, j, mm);
+  for (int i = threadIdx.x; i <= j; i += VB) {
+    double h = K->h[i];
+    if (reorth) {
+      h += K->h2[i];
+      K->h[i] = h;
+    }
+    col[i] = h;
+    if (i < j) {
+      cs[i] = K->cs[i];
+      sn[i] = K->sn[i];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (reorth) {
+      K->nrm_new = res;
+      K->nrm_fin = sqrt(res);
+    }
+    const double hn = K->nrm_fin;
+    col[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+      const double a = cs[i] * col[i] + sn[i] * col[i + 1];
+      col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+      col[i] = a;
+    }
+    const double den = hypot(col[j], col[j + 1]);
+    const double c = den > 0.0 ? col[j] / den : 1.0;
+    const double sj = den > 0.0 ? col[j + 1] / den : 0.0;
+    K->cs[j] = c;
+    K->sn[j] = sj;
+    col[j] = den;
+    col[j + 1] = 0.0;
+    const double gj = K->g[j];
+    K->g[j + 1] = -sj * gj;
+    K->g[j] = c * gj;
+    K->est = fabs(K->g[j + 1]) / K->bnorm;
+    K->breakdown = (hn == 0.0 || den == 0.0 || !isfinite(hn)) ? 1 : 0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= j + 1; i += VB) K->H[i * mm + j] = col[i];
 }
 
 // y = R^{-1} g for the first jend columns (back substitution).
@@ -807,8 +891,13 @@ static int gmres_core_t(fsi_mesh* m, const BlockInfo& blk, const double* b, doub
         prof_bytes(m, P_KRY_UPD, (j + 1) * vb + 2 * wb);  // j+1 basis vectors and w read, w written
         // the pass-2 update only when the DGKS test asked for it (exits at once otherwise),
         // then its norm and the Givens step
-        FSI_LAUNCH(m, P_KRY_UPD, upd_kernel<VT><<<Gc, VB, 0, m->stream>>>(w, V, M1, j + 1, K->h2, n, m->partials_dot,
-                                                                           &K->reorth));
+        if constexpr (F32) {
+          FSI_LAUNCH(m, P_KRY_UPD, upd4_kernel<<<Gc, VB, 0, m->stream>>>(w, reinterpret_cast<const float*>(V), M1,
+                                                                        j + 1, K->h2, n, m->partials_dot, &K->reorth));
+        } else {
+          FSI_LAUNCH(m, P_KRY_UPD, upd_kernel<VT><<<Gc, VB, 0, m->stream>>>(w, V, M1, j + 1, K->h2, n,
+                                                                             m->partials_dot, &K->reorth));
+        }
         FSI_LAUNCH(m, P_KRY_SMALL, sum_partials_givens<<<1, VB, 0, m->stream>>>(m->partials_dot, Gc, K, j, mm));
       }
       FSI_LAUNCH(m, P_KRYLOV, store_slot<VT><<<G, VB, 0, m->stream>>>(V, M1, j + 1, w, nullptr, K, n, m->dinv, zn));
