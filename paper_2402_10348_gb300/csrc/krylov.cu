@@ -48,6 +48,14 @@ static int vgrid(int64_t n) {
 // two CTAs per SM: each streams enough chunks to amortise its end-of-kernel
 // reduction of up to 16 sums (the reduction dominated at four CTAs per SM)
 static int cgrid(int64_t nch) { return (int)std::max<int64_t>(1, std::min<int64_t>(nch, 152 * 2)); }
+// the float32-basis kernels reduce in float32 up to the CTA (cheap): four CTAs per SM
+// keep more loads in flight
+template <typename VT>
+static int cgrid_t(int64_t nch) {
+  return sizeof(VT) == 4 ? (int)std::max<int64_t>(1, std::min<int64_t>(nch, 152 * 4)) : cgrid(nch);
+}
+// one CTA per 256-element chunk (every load of the basis store in flight at once)
+static int chunk_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + CH - 1) / CH, 1 << 30)); }
 
 // device-resident Arnoldi/Givens state (inside fsi_mesh::kry_dev)
 struct KryDev {
@@ -710,7 +718,7 @@ static void launch_mdot_rem(fsi_mesh* m, int rem, dim3 g1, const VT* V, int M1, 
 template <typename VT>
 static int basis_dots(fsi_mesh* m, const VT* V, int M1, int k, const double* w, int64_t n, double* out, bool self,
                       const int* skip = nullptr) {
-  const int G = cgrid((n + CH - 1) / CH);
+  const int G = cgrid_t<VT>((n + CH - 1) / CH);
   const int nfull = k / DCH, rem = k % DCH;
   if (nfull)
     FSI_LAUNCH(m, P_KRY_DOT, (launch_mdot<DCH, false>(m, dim3(G, nfull), V, M1, 0, w, n, skip)));
@@ -846,7 +854,7 @@ static int gmres_core_t(fsi_mesh* m, const BlockInfo& blk, const double* b, doub
     FSI_LAUNCH(m, P_KRY_SMALL, cycle_start<<<1, 1, 0, m->stream>>>(K, m->red, mm));
     // the operator input of the plain (Jacobi) steps: z = dinv V_j, written with V_j
     VT* zn = pc ? nullptr : (F32 ? reinterpret_cast<VT*>(m->dx32) : reinterpret_cast<VT*>(z));
-    FSI_LAUNCH(m, P_KRYLOV, store_slot<VT><<<G, VB, 0, m->stream>>>(V, M1, 0, r, m->red, K, n, m->dinv, zn));
+    FSI_LAUNCH(m, P_KRYLOV, store_slot<VT><<<chunk_grid(n), VB, 0, m->stream>>>(V, M1, 0, r, m->red, K, n, m->dinv, zn));
     int jend = 0, enq = 0;
     bool done = false;
     const int jmax = std::min(mm, max_iter - *iters);
@@ -883,7 +891,7 @@ static int gmres_core_t(fsi_mesh* m, const BlockInfo& blk, const double* b, doub
       if ((rc = basis_dots(m, V, M1, j + 1, w, n, K->h, true))) return rc;
       // pass-1 update fused with the pass-2 projections of the updated vector
       {
-        const int Gc = cgrid((n + CH - 1) / CH);
+        const int Gc = cgrid_t<VT>((n + CH - 1) / CH);
         FSI_LAUNCH(m, P_KRY_UPD, rc = upd_dot<VT>(m, Gc, w, V, M1, j + 1, K->h, n));
         if (rc) return rc;
         FSI_LAUNCH(m, P_KRY_UPD, sum_partials_decide<<<j + 2, VB, 0, m->stream>>>(m->partials_dot, Gc, K, j));
@@ -900,7 +908,7 @@ static int gmres_core_t(fsi_mesh* m, const BlockInfo& blk, const double* b, doub
         }
         FSI_LAUNCH(m, P_KRY_SMALL, sum_partials_givens<<<1, VB, 0, m->stream>>>(m->partials_dot, Gc, K, j, mm));
       }
-      FSI_LAUNCH(m, P_KRYLOV, store_slot<VT><<<G, VB, 0, m->stream>>>(V, M1, j + 1, w, nullptr, K, n, m->dinv, zn));
+      FSI_LAUNCH(m, P_KRYLOV, store_slot<VT><<<chunk_grid(n), VB, 0, m->stream>>>(V, M1, j + 1, w, nullptr, K, n, m->dinv, zn));
       // estimate, reorth and breakdown flags: one copy (the fields are adjacent)
       FSI_CUDA(cudaMemcpyAsync(est + 3 * j, &K->est, sizeof(double) + 2 * sizeof(int), cudaMemcpyDeviceToHost,
                                m->stream));
