@@ -54,8 +54,8 @@ template <typename VT>
 static int cgrid_t(int64_t nch) {
   return sizeof(VT) == 4 ? (int)std::max<int64_t>(1, std::min<int64_t>(nch, 152 * 4)) : cgrid(nch);
 }
-// one CTA per 256-element chunk (every load of the basis store in flight at once)
-static int chunk_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + CH - 1) / CH, 1 << 30)); }
+// the basis store: a few chunks of 256 elements per CTA, eight CTAs per SM
+static int chunk_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + CH - 1) / CH, 152 * 8)); }
 
 // device-resident Arnoldi/Givens state (inside fsi_mesh::kry_dev)
 struct KryDev {
@@ -472,13 +472,18 @@ static int upd_dot(fsi_mesh* m, int G, double* w, const VT* V, int M1, int k, co
 template <typename VT>
 __global__ void store_slot(VT* __restrict__ V, int M1, int slot, const double* __restrict__ src, const double* n2,
                            const KryDev* K, int64_t n, const double* __restrict__ dinv, VT* __restrict__ z) {
-  double s;
-  if (n2) {
-    s = 1.0 / sqrt(*n2);
-  } else {
-    const double nf = K->nrm_fin;
-    s = nf > 0.0 ? 1.0 / nf : 0.0;
+  // the scale once per CTA: float64 division and square root are slow on this GPU
+  __shared__ double s_sh;
+  if (threadIdx.x == 0) {
+    if (n2) {
+      s_sh = 1.0 / sqrt(*n2);
+    } else {
+      const double nf = K->nrm_fin;
+      s_sh = nf > 0.0 ? 1.0 / nf : 0.0;
+    }
   }
+  __syncthreads();
+  const double s = s_sh;
   // one chunk of CH = VB elements per CTA pass
   const int64_t nch = (n + CH - 1) / CH;
   for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
@@ -486,7 +491,10 @@ __global__ void store_slot(VT* __restrict__ V, int M1, int slot, const double* _
     if (j >= n) continue;
     const VT v = (VT)(src[j] * s);
     V[c * (int64_t)M1 * CH + (int64_t)slot * CH + threadIdx.x] = v;
-    if (z) z[j] = (VT)(dinv[j] * (double)v);
+    if (z) {
+      if constexpr (sizeof(VT) == 4) z[j] = (float)dinv[j] * v;  // the float32 operator's increment
+      else z[j] = dinv[j] * v;
+    }
   }
 }
 
