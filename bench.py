@@ -398,7 +398,9 @@ def run_tet_case(reps: int = 5):
     """Per-apply device times of the float64 operators on linear tetrahedra (six per box
     cell, interior nodes jittered by 0.2 h): the 64^3 cavity's box (1.57 M elements) and
     the falling sphere's 96x96x192 box (10.6 M elements), on seeded random states.  Each
-    apply is an element kernel plus a node-sum kernel; time per apply = class time / calls."""
+    apply is an element kernel plus a node-sum kernel; time per apply = class time / calls.
+    Inside a 40-iteration NS GMRES the products after the eighth run through the element
+    matrices (`ns_jvp_f64_element_matrix`, with the one build's time)."""
     import torch
     from paper_2402_10348_gb300 import fsi
     from workloads import cavity64, falling, random_state, tet_box_mesh
@@ -441,6 +443,21 @@ def run_tet_case(reps: int = 5):
         prof = fsi.fsi_profile_read(mesh)
         fsi.fsi_profile(mesh, False)
         res["gamma_beta"] = {"ms_per_call": round(prof.get("gamma_beta", (0, 0.0))[1] / reps, 3)}
+        # inside a solve: after 8 products the NS product runs through element matrices
+        rhs = torch.randn(4 * nn, dtype=torch.float64, device=dev, generator=g)
+        sol = torch.zeros_like(rhs)
+        o = fsi.solve_opts(m=30, rtol=1e-30, max_iter=40)
+        o.flags |= fsi.FSI_NO_STALL_STOP
+        fsi.fsi_profile(mesh, True)
+        fsi.fsi_gmres(mesh, fsi.FSI_BLOCK_NS, *st, rhs, sol, o, allow_noconv=True)
+        torch.cuda.synchronize()
+        prof = fsi.fsi_profile_read(mesh)
+        fsi.fsi_profile(mesh, False)
+        em, nd, bld = (prof.get(k, (0, 0.0)) for k in ("ns_jvp_f64_em", "node_sums", "op_builds"))
+        if em[0] > 0:
+            per = (em[1] + nd[1]) / em[0]
+            res["ns_jvp_f64_element_matrix"] = {"ms_per_apply": round(per, 3), "gdofs": round(4 * nn / (per / 1e3) / 1e9, 3),
+                                                "applies": em[0], "build_ms": round(bld[1], 3)}
         out[wl.name] = {"elements": int(conn.shape[0]), "nodes": nn, "operators": res}
         del mesh
         torch.cuda.empty_cache()

@@ -28,6 +28,11 @@ struct TetData {
   int64_t* nptr = nullptr;  // [nn + 1]
   int32_t* nlist = nullptr; // 4 e + a of every (element, corner) at a node, by element
   double* E = nullptr;      // [24][ne] element contributions, slot (a * ncomp + eq)
+  // float64 NS element matrices [256][ne], row a * 4 + eq, column b * 4 + f, built once a
+  // solve has taken NSE_AFTER products on one staging (k_stage) with one elastic flag
+  double* K = nullptr;
+  int64_t k_stage = -1;
+  int k_elastic = -1, k_count = 0, k_built = 0;
 };
 
 constexpr int TG = 19;
@@ -41,6 +46,7 @@ void tet_free(TetData* t) {
   cudaFree(t->nptr);
   cudaFree(t->nlist);
   cudaFree(t->E);
+  cudaFree(t->K);
   delete t;
 }
 
@@ -296,8 +302,102 @@ int tet_ns_run(fsi_mesh* m, const double* dx, double* y, unsigned flags) {
   return FSI_OK;
 }
 
+// NS element matrices: one thread per element; per quadrature point the coefficients once,
+// then the product's point arithmetic for each of the 16 unit increments (field f at corner
+// b), added into column b * 4 + f of the element's matrix (the first point writes).  Same
+// operator as tet_ns_elem<1> up to the order of the sums.
+__global__ void __launch_bounds__(128) tet_nsk_build(const TetArgs A, double* __restrict__ K) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= A.ne) return;
+  int nd[4];
+  double dN[4][3], w, G[6];
+  tet_load_geo(A.conn, A.geo, A.ne, e, nd, dN, w, G);
+  for (int q = 0; q < 4; ++q) {
+    TetPoint pt;
+    tet_point(A, nd, dN, G, q, A.elastic, pt);
+    double Nq[4];
+    for (int a = 0; a < 4; ++a) Nq[a] = a == q ? FSI_TA : FSI_TB;
+    for (int col = 0; col < 16; ++col) {
+      const int b = col >> 2, f = col & 3;
+      double dv[3], gd[3][3], dgp[3];
+      for (int kk = 0; kk < 3; ++kk) {
+        dv[kk] = kk == f ? Nq[b] : 0.0;
+        for (int d = 0; d < 3; ++d) gd[kk][d] = kk == f ? dN[b][d] : 0.0;
+        dgp[kk] = f == 3 ? dN[b][kk] : 0.0;
+      }
+      const double dp = f == 3 ? Nq[b] : 0.0;
+      double fo[4], go[4][3];
+      nsq_point_fg<double>(LocalCoef{pt.k}, A.elastic != 0, dv, gd, dp, dgp, A.P.alpha, A.P.c_mass, fo, go);
+      for (int a = 0; a < 4; ++a)
+        for (int eq = 0; eq < 4; ++eq) {
+          const double v = w * (Nq[a] * fo[eq] + dN[a][0] * go[eq][0] + dN[a][1] * go[eq][1] + dN[a][2] * go[eq][2]);
+          double* kp = K + (int64_t)((a * 4 + eq) * 16 + col) * A.ne + e;
+          *kp = q == 0 ? v : *kp + v;
+        }
+    }
+  }
+}
+
+// product through the element matrices: E slot a * 4 + eq = row of K times the element's
+// increment values (column b * 4 + f = field f at corner b)
+__global__ void __launch_bounds__(128) tet_nsk_apply(const int32_t* __restrict__ conn, const double* __restrict__ K,
+                                                     const double* __restrict__ dx, double* __restrict__ E, int64_t ne,
+                                                     int64_t nn) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  double u[16];
+  for (int b = 0; b < 4; ++b) {
+    const int64_t node = conn[(int64_t)b * ne + e];
+    for (int f = 0; f < 4; ++f) u[b * 4 + f] = __ldg(dx + (int64_t)f * nn + node);
+  }
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    double acc = 0.0;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc += __ldg(K + (int64_t)(r * 16 + c) * ne + e) * u[c];
+    E[(int64_t)r * ne + e] = acc;
+  }
+}
+
 int tet_ns(fsi_mesh* m, int mode, const double* dx, double* y, unsigned flags) {
   if (flags & FSI_FP32) return set_error(FSI_EINVAL, "tetrahedral meshes: float64 operators only");
+  if (mode == 1 && !m->rec) {
+    // a float64 solve on one staging: after NSE_AFTER products switch to element matrices
+    TetData* t = m->tet;
+    const int elastic = ((flags & FSI_ELASTIC_AUG) && m->ns > 0) ? 1 : 0;
+    if (t->k_stage != m->stage_gen || t->k_elastic != elastic) {
+      t->k_stage = m->stage_gen;
+      t->k_elastic = elastic;
+      t->k_count = 0;
+      t->k_built = 0;
+    }
+    if (++t->k_count > NSE_AFTER) {
+      const unsigned grid = (unsigned)((t->ne + 127) / 128);
+      if (!t->k_built) {
+        if (!t->K) FSI_CUDA(cudaMalloc(&t->K, sizeof(double) * 256 * (size_t)t->ne));
+        TetArgs A;
+        A.conn = t->conn;
+        A.geo = t->geo;
+        A.ne = t->ne;
+        A.xa = m->staged_xa;
+        A.xd = m->xd;
+        A.mat = m->mat;
+        A.dx = nullptr;
+        A.E = t->E;
+        A.nn = m->nn;
+        A.elastic = elastic;
+        A.P = m->P;
+        FSI_LAUNCH(m, P_NS_BUILD, tet_nsk_build<<<grid, 128, 0, m->stream>>>(A, t->K));
+        t->k_built = 1;
+      }
+      prof_bytes(m, P_NS_JVP64E, (double)t->ne * (256 * 8.0 + 16 * 4.0 + 16 * 8.0) + (double)m->nn * 32.0);
+      FSI_LAUNCH(m, P_NS_JVP64E, tet_nsk_apply<<<grid, 128, 0, m->stream>>>(t->conn, t->K, dx, t->E, t->ne, m->nn));
+      FSI_LAUNCH(m, P_NODE_SUM, tet_ns_node<1><<<(unsigned)((m->nn + 255) / 256), 256, 0, m->stream>>>(
+                                    t->nptr, t->nlist, t->E, t->ne, m->nn, m->mask, m->pin_active, m->staged_x, m->vD,
+                                    dx, y));
+      return FSI_OK;
+    }
+  }
   if (mode == 0) return tet_ns_run<0>(m, dx, y, flags);
   if (mode == 1) return tet_ns_run<1>(m, dx, y, flags);
   return tet_ns_run<2>(m, dx, y, flags);
