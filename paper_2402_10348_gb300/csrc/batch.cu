@@ -117,6 +117,11 @@ struct fsi_batch {
   int use_graph = 1;
   int64_t launches = 0;          // launches of this batch (graph replays count their nodes)
   int64_t launches_per_cycle = 0;
+  // work lists of the batched float32 NS coefficient product (built on first use)
+  int4* nsq_eitems = nullptr;     // (instance, x block, y block, layer)
+  int nsq_ne = 0;
+  int4* nsq_nitems = nullptr;     // (instance, 128-node block, 0, 0)
+  int nsq_nn = 0;
 };
 
 namespace fsi {
@@ -521,10 +526,77 @@ int build_tiles(fsi_batch* b, int target_mult, int grid_mult) {
   return FSI_OK;
 }
 
+// the batched float32 NS product from per-instance coefficients (nsq_tma.cu): element
+// launch over every instance's 64 x 2-element tiles, node launch over its 128-node blocks
+int launch_nsq_batch(fsi_batch* b, const void* ops_dev, size_t, int cls, int use_active) {
+  if (!b->nsq_eitems) {
+    std::vector<int4> ei, ni;
+    for (int i = 0; i < b->n; ++i) {
+      const Geom& g = b->meshes[i]->g;
+      const int nbx = (g.nx + NSQ_TBX - 1) / NSQ_TBX, nby = (g.ny + NSQ_TBY - 1) / NSQ_TBY;
+      for (int ez = 0; ez < g.nz; ++ez)
+        for (int by = 0; by < nby; ++by)
+          for (int bx = 0; bx < nbx; ++bx) ei.push_back(make_int4(i, bx, by, ez));
+      const int64_t nblk = (b->meshes[i]->nn + 127) / 128;
+      for (int64_t k = 0; k < nblk; ++k) ni.push_back(make_int4(i, (int)k, 0, 0));
+    }
+    if (ei.size() > (size_t)INT32_MAX || ni.size() > (size_t)INT32_MAX)
+      return set_error(FSI_EINVAL, "batch: too many tiles for one launch");
+    FSI_CUDA(cudaMalloc(&b->nsq_eitems, sizeof(int4) * ei.size()));
+    FSI_CUDA(cudaMalloc(&b->nsq_nitems, sizeof(int4) * ni.size()));
+    FSI_CUDA(cudaMemcpy(b->nsq_eitems, ei.data(), sizeof(int4) * ei.size(), cudaMemcpyHostToDevice));
+    FSI_CUDA(cudaMemcpy(b->nsq_nitems, ni.data(), sizeof(int4) * ni.size(), cudaMemcpyHostToDevice));
+    b->nsq_ne = (int)ei.size();
+    b->nsq_nn = (int)ni.size();
+  }
+  fsi_mesh* m = b->meshes[0];
+  const int* active = use_active == 1 ? b->act : (use_active == 2 ? b->live : nullptr);
+  int rc = prof_begin(m, cls);
+  if (rc) return rc;
+  if ((rc = nsq_batch_launch(static_cast<const NSQBatchRec*>(ops_dev), b->nsq_eitems, b->nsq_ne, b->nsq_nitems,
+                             b->nsq_nn, active, b->stream)))
+    return rc;
+  b->launches += 2;
+  return prof_end(m, cls);
+}
+
+// (re)allocates a set's device records for `bytes` (a captured cycle holding the old
+// records is dropped)
+int set_storage(fsi_batch* b, OpSet* set, size_t bytes) {
+  if (set->ops && set->bytes == bytes) return FSI_OK;
+  cudaFree(set->ops);
+  set->ops = nullptr;
+  FSI_CUDA(cudaMalloc(&set->ops, bytes));
+  set->bytes = bytes;
+  if (b->cycle) cudaGraphExecDestroy(b->cycle);
+  b->cycle = nullptr;
+  return FSI_OK;
+}
+
 // records the operator of every instance (dx = dx_base + off, y = y_base + off)
 int record_set(fsi_batch* b, OpSet* set, unsigned flags, const double* dx_base, double* y_base) {
   BatchRec rec;
   const bool f32 = flags & FSI_FP32;
+  bool all_ns = true;
+  for (int i = 0; i < b->n; ++i) all_ns = all_ns && b->blocks[i] == FSI_BLOCK_NS;
+  if (f32 && all_ns) {
+    // float32 NS products from each instance's frozen coefficients (built here, on the
+    // staged states), TMA-staged, in one element and one node launch
+    std::vector<NSQBatchRec> recs(b->n);
+    for (int i = 0; i < b->n; ++i) {
+      int rc = nsq_batch_record(b->meshes[i], flags, dx_base + b->off[i], y_base + b->off[i],
+                                b->dx32_own + b->off[i], &recs[i]);
+      if (rc) return rc;
+    }
+    const size_t bytes = sizeof(NSQBatchRec) * recs.size();
+    if (int rc = set_storage(b, set, bytes)) return rc;
+    FSI_CUDA(cudaMemcpyAsync(set->ops, recs.data(), bytes, cudaMemcpyHostToDevice, b->stream));
+    FSI_CUDA(cudaStreamSynchronize(b->stream));
+    set->smem = 0;
+    set->cls = P_NS_JVP32;
+    set->launch = &launch_nsq_batch;
+    return FSI_OK;
+  }
   for (int i = 0; i < b->n; ++i) {
     fsi_mesh* m = b->meshes[i];
     BlockInfo bi;
@@ -545,11 +617,7 @@ int record_set(fsi_batch* b, OpSet* set, unsigned flags, const double* dx_base, 
   }
   if (rec.count != b->n)
     return set_error(FSI_EINVAL, "batch: an operator needs more than one pass (too many solids) for batching");
-  if (!set->ops) {
-    FSI_CUDA(cudaMalloc(&set->ops, rec.bytes.size()));
-    set->bytes = rec.bytes.size();
-  }
-  if (set->bytes != rec.bytes.size()) return set_error(FSI_EINVAL, "batch: operator record size changed");
+  if (int rc = set_storage(b, set, rec.bytes.size())) return rc;
   FSI_CUDA(cudaMemcpyAsync(set->ops, rec.bytes.data(), rec.bytes.size(), cudaMemcpyHostToDevice, b->stream));
   FSI_CUDA(cudaStreamSynchronize(b->stream));  // the host record is freed on return
   set->smem = rec.smem;
@@ -795,6 +863,8 @@ int fsi_batch_destroy(fsi_batch* b) {
   if (!b) return FSI_OK;
   if (b->cycle) cudaGraphExecDestroy(b->cycle);
   for (OpSet* s : {&b->jvp_inner, &b->jvp_d, &b->jvp_outer, &b->jvp_user}) cudaFree(s->ops);
+  cudaFree(b->nsq_eitems);
+  cudaFree(b->nsq_nitems);
   cudaFree(b->geoms_dev), cudaFree(b->tiles_dev), cudaFree(b->items_dev), cudaFree(b->item_first_dev);
   cudaFree(b->V), cudaFree(b->vbase_dev), cudaFree(b->off_dev), cudaFree(b->nloc_dev), cudaFree(b->dx32_dev);
   cudaFree(b->w), cudaFree(b->z), cudaFree(b->r), cudaFree(b->t), cudaFree(b->dinv), cudaFree(b->d);

@@ -180,6 +180,29 @@ int ns_build(fsi_mesh* m, unsigned flags);  // ops_f64.cu
 int launch_nsq_tma(fsi_mesh* m, int elastic, float* E, const double* dx, double* y);
 // FSI_ECUDA if a bounded wait of that kernel gave up since the flag was allocated (syncs)
 int check_tma(fsi_mesh* m);
+// One instance's float32 NS product in a batched launch (nsq_tma.cu): the TMA descriptor of
+// its coefficients, its increment (float copy and float64 for the Dirichlet rows), its
+// contribution scratch and output, its geometry.  64-byte aligned (the descriptor's rule).
+struct alignas(64) NSQBatchRec {
+  unsigned char map[128];
+  const float* dx32;
+  const double* dx;
+  float* E;
+  double* y;
+  const uint8_t* mask;
+  int* err;
+  int64_t nxyp, nn;
+  double W;
+  int nx, ny, nz, nxp, pin, elastic;
+  float al, cm, rhx, rhy, rhz;
+};
+// builds the instance's coefficients (if stale), scratch and descriptor and fills rec
+int nsq_batch_record(fsi_mesh* m, unsigned flags, const double* dx, double* y, float* dx32, NSQBatchRec* rec);
+// element and node launches of a batch (recs in device memory; items: (instance, x block,
+// y block, layer) and (instance, 128-node block)); active gates instances (nullable)
+int nsq_batch_launch(const NSQBatchRec* recs, const int4* eitems, int neitems, const int4* nitems, int nnitems,
+                     const int* active, cudaStream_t s);
+constexpr int NSQ_TBX = 64, NSQ_TBY = 2;  // element tile of the TMA product
 // [slots][elements] scratch of the element-centric products, grown on demand (ops_f64.cu)
 int ensure_elem_scratch(fsi_mesh* m, int slots, int64_t nxyp);
 // float64 NS product through element matrices (built first when stale), ops_f64.cu

@@ -22,7 +22,7 @@
 namespace fsi {
 namespace {
 
-constexpr int TBX = 64, TBY = 2;  // CTA tile of elements (x, y), one thread each
+constexpr int TBX = NSQ_TBX, TBY = NSQ_TBY;  // CTA tile of elements (x, y), one thread each
 constexpr int TSTAGES = 2;
 constexpr long long TWAIT = 1LL << 22;
 
@@ -60,24 +60,18 @@ struct SmemCoef {
   __device__ __forceinline__ float operator()(int i) const { return p[i * (TBX * TBY)]; }
 };
 
-template <int NCOEF>
-__global__ void __launch_bounds__(TBX * TBY) nsq_tma_kernel(const __grid_constant__ CUtensorMap map,
-                                                            const float* __restrict__ dx, float* __restrict__ E, int nx,
-                                                            int ny, int nz, int nxp, int64_t nxyp, int64_t nn, float al,
-                                                            float cmass, float rhx, float rhy, float rhz, int* err) {
-  extern __shared__ __align__(128) float stage[];  // [TSTAGES][NCOEF][TBY][TBX]
+// One CTA's tile: elements (x0 .. x0 + 63, y0 .. y0 + 1) of layer ez, ncoef coefficients per
+// point staged from the tensor map `map` (in kernel parameter or global memory) into
+// `stage` ([TSTAGES][ncoef][TBY][TBX]); contributions into E (element plane pitch nxyp).
+__device__ __forceinline__ void nsq_tma_tile(float* stage, const CUtensorMap* map, int ncoef,
+                                             const float* __restrict__ dx, float* __restrict__ E, int nx, int ny,
+                                             int nz, int nxp, int64_t nxyp, int64_t nn, float al, float cmass,
+                                             float rhx, float rhy, float rhz, int x0, int y0, int ez, int* err) {
   __shared__ __align__(8) uint64_t bar[TSTAGES];
   __shared__ int failed;
-  constexpr int SF = NCOEF * TBX * TBY;  // floats per stage
-  constexpr uint32_t SBYTES = SF * sizeof(float);
+  const int SF = ncoef * TBX * TBY;  // floats per stage
+  const uint32_t SBYTES = (uint32_t)SF * sizeof(float);
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TBX + tx;
-  const int nbx = (nx + TBX - 1) / TBX, nby = (ny + TBY - 1) / TBY;
-  int64_t b = blockIdx.x;
-  const int bx = (int)(b % nbx);
-  b /= nbx;
-  const int by = (int)(b % nby);
-  const int ez = (int)(b / nby);
-  const int x0 = bx * TBX, y0 = by * TBY;
   if (tid == 0) {
     failed = 0;
     for (int s = 0; s < TSTAGES; ++s)
@@ -86,7 +80,7 @@ __global__ void __launch_bounds__(TBX * TBY) nsq_tma_kernel(const __grid_constan
   }
   __syncthreads();
   if (tid == 0)
-    for (int s = 0; s < TSTAGES; ++s) load_box(sptr(stage + s * SF), &map, sptr(&bar[s]), SBYTES, x0, y0, ez * 8 + s);
+    for (int s = 0; s < TSTAGES; ++s) load_box(sptr(stage + s * SF), map, sptr(&bar[s]), SBYTES, x0, y0, ez * 8 + s);
   // the increment at the element's corners (while the first boxes arrive)
   const int ex = x0 + tx, ey = y0 + ty;
   const bool valid = ex < nx && ey < ny;
@@ -118,17 +112,17 @@ __global__ void __launch_bounds__(TBX * TBY) nsq_tma_kernel(const __grid_constan
       }
       const VG<float> dpr = interp_vg(x[3], w, rhx, rhy, rhz);
       const float dgp[3] = {dpr.gx, dpr.gy, dpr.gz};
-      nsq_point<float>(SmemCoef{stage + s * SF + tid}, NCOEF == NCQ, dv, gd, dpr.v, dgp, al, cmass, w, rhx, rhy, rhz,
+      nsq_point<float>(SmemCoef{stage + s * SF + tid}, ncoef == NCQ, dv, gd, dpr.v, dgp, al, cmass, w, rhx, rhy, rhz,
                        c);
     }
     __syncthreads();  // every thread is done with stage s
-    if (tid == 0 && q + TSTAGES < 8) load_box(sptr(stage + s * SF), &map, sptr(&bar[s]), SBYTES, x0, y0, ez * 8 + q + TSTAGES);
+    if (tid == 0 && q + TSTAGES < 8) load_box(sptr(stage + s * SF), map, sptr(&bar[s]), SBYTES, x0, y0, ez * 8 + q + TSTAGES);
   }
   if (failed) {
     // copies issued for points q .. min(q + TSTAGES, 8) - 1 may still be in flight; the
     // product of this tile is NaN, so the solve that uses it stops on a non-finite vector
     if (tid == 0) {
-      *err = 1;
+      if (err) *err = 1;
       for (int p = q; p < 8 && p < q + TSTAGES; ++p) bar_wait(sptr(&bar[p % TSTAGES]), (uint32_t)((p / TSTAGES) & 1));
     }
 #pragma unroll
@@ -143,6 +137,71 @@ __global__ void __launch_bounds__(TBX * TBY) nsq_tma_kernel(const __grid_constan
   for (int f = 0; f < 4; ++f)
 #pragma unroll
     for (int a = 0; a < 8; ++a) E[(8 * f + a) * es + e] = c[f][a];
+}
+
+__global__ void __launch_bounds__(TBX * TBY) nsq_tma_kernel(const __grid_constant__ CUtensorMap map, int ncoef,
+                                                            const float* __restrict__ dx, float* __restrict__ E, int nx,
+                                                            int ny, int nz, int nxp, int64_t nxyp, int64_t nn, float al,
+                                                            float cmass, float rhx, float rhy, float rhz, int* err) {
+  extern __shared__ __align__(128) float stage[];
+  const int nbx = (nx + TBX - 1) / TBX, nby = (ny + TBY - 1) / TBY;
+  int64_t b = blockIdx.x;
+  const int bx = (int)(b % nbx);
+  b /= nbx;
+  const int by = (int)(b % nby);
+  const int ez = (int)(b / nby);
+  nsq_tma_tile(stage, &map, ncoef, dx, E, nx, ny, nz, nxp, nxyp, nn, al, cmass, rhx, rhy, rhz, bx * TBX, by * TBY, ez,
+               err);
+}
+
+// Batched: one CTA per work item (instance, x block, y block, layer); the instance's
+// parameters and tensor map come from its record in global memory.
+__global__ void __launch_bounds__(TBX * TBY) nsq_tma_batch_kernel(const NSQBatchRec* __restrict__ recs,
+                                                                  const int4* __restrict__ items, const int* active) {
+  extern __shared__ __align__(128) float stage[];
+  const int4 it = items[blockIdx.x];
+  if (active && !active[it.x]) return;
+  const NSQBatchRec& R = recs[it.x];
+  nsq_tma_tile(stage, reinterpret_cast<const CUtensorMap*>(R.map), R.elastic ? NCQ : NCQ_FLUID, R.dx32, R.E, R.nx,
+               R.ny, R.nz, R.nxp, R.nxyp, R.nn, R.al, R.cm, R.rhx, R.rhy, R.rhz, it.y * TBX, it.z * TBY, it.w, R.err);
+}
+
+// Batched node sums: one CTA per (instance, 128 consecutive nodes)
+__global__ void __launch_bounds__(128) ns_node_batch_kernel(const NSQBatchRec* __restrict__ recs,
+                                                            const int4* __restrict__ items, const int* active) {
+  const int4 it = items[blockIdx.x];
+  if (active && !active[it.x]) return;
+  const NSQBatchRec& R = recs[it.x];
+  const int64_t n = (int64_t)it.y * 128 + threadIdx.x;
+  if (n >= R.nn) return;
+  const int nx = R.nx, ny = R.ny, nz = R.nz;
+  const int i = (int)(n % (nx + 1));
+  const int64_t jk = n / (nx + 1);
+  const int j = (int)(jk % (ny + 1)), k = (int)(jk / (ny + 1));
+  const int64_t es = (int64_t)nz * R.nxyp;
+  float s[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int az = 1; az >= 0; --az) {
+    const int ez = k - az;
+    if (ez < 0 || ez >= nz) continue;
+    for (int ay = 1; ay >= 0; --ay) {
+      const int ey = j - ay;
+      if (ey < 0 || ey >= ny) continue;
+      for (int ax = 1; ax >= 0; --ax) {
+        const int ex = i - ax;
+        if (ex < 0 || ex >= nx) continue;
+        const int64_t e = (int64_t)ez * R.nxyp + (int64_t)ey * R.nxp + ex;
+        const int a = ax + 2 * ay + 4 * az;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) s[f] += R.E[(8 * f + a) * es + e];
+      }
+    }
+  }
+  const uint8_t mk = R.mask[n];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const bool dir = ((mk >> f) & 1) && (f < 3 || R.pin);
+    R.y[f * R.nn + n] = dir ? (R.dx ? R.dx[f * R.nn + n] : (double)R.dx32[f * R.nn + n]) : R.W * (double)s[f];
+  }
 }
 
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -190,6 +249,55 @@ int check_tma(fsi_mesh* m) {
   return FSI_OK;
 }
 
+int nsq_batch_record(fsi_mesh* m, unsigned flags, const double* dx, double* y, float* dx32, NSQBatchRec* rec) {
+  const unsigned eflags = flags & FSI_ELASTIC_AUG;
+  if (m->cq_gen != m->stage_gen || m->cq_flags != eflags || !m->cq64)
+    if (int rc = ns_build(m, flags)) return rc;
+  const Geom& g = m->g;
+  const int nxp = cq_pitch(m);
+  const int64_t nxyp = (int64_t)nxp * g.ny;
+  if (int rc = ensure_elem_scratch(m, 32, nxyp)) return rc;
+  if (m->cq_tmap_base != m->cq32)
+    if (int rc = encode_maps(m, nxp, nxyp)) return rc;
+  if (!m->tma_err) {
+    FSI_CUDA(cudaMalloc(&m->tma_err, sizeof(int)));
+    FSI_CUDA(cudaMemsetAsync(m->tma_err, 0, sizeof(int), m->stream));
+  }
+  const int elastic = (eflags && m->ns > 0) ? 1 : 0;
+  memset(rec, 0, sizeof(*rec));
+  memcpy(rec->map, m->cq_tmap + (elastic ? 0 : 128), 128);
+  rec->dx32 = dx32;
+  rec->dx = dx;
+  rec->E = reinterpret_cast<float*>(m->ke_e);
+  rec->y = y;
+  rec->mask = m->mask;
+  rec->err = m->tma_err;
+  rec->nxyp = nxyp;
+  rec->nn = m->nn;
+  rec->W = g.hx * g.hy * g.hz / 8.0;
+  rec->nx = g.nx;
+  rec->ny = g.ny;
+  rec->nz = g.nz;
+  rec->nxp = nxp;
+  rec->pin = m->pin_active;
+  rec->elastic = elastic;
+  rec->al = (float)m->P.alpha;
+  rec->cm = (float)m->P.c_mass;
+  rec->rhx = (float)(1.0 / g.hx);
+  rec->rhy = (float)(1.0 / g.hy);
+  rec->rhz = (float)(1.0 / g.hz);
+  return FSI_OK;
+}
+
+int nsq_batch_launch(const NSQBatchRec* recs, const int4* eitems, int neitems, const int4* nitems, int nnitems,
+                     const int* active, cudaStream_t s) {
+  const size_t smem = sizeof(float) * (size_t)TSTAGES * NCQ * TBX * TBY;
+  if (neitems > 0) nsq_tma_batch_kernel<<<neitems, dim3(TBX, TBY), smem, s>>>(recs, eitems, active);
+  if (nnitems > 0) ns_node_batch_kernel<<<nnitems, 128, 0, s>>>(recs, nitems, active);
+  FSI_CUDA(cudaGetLastError());
+  return FSI_OK;
+}
+
 int launch_nsq_tma(fsi_mesh* m, int elastic, float* E, const double* dx, double* y) {
   const Geom& g = m->g;
   const int nxp = cq_pitch(m);
@@ -208,15 +316,9 @@ int launch_nsq_tma(fsi_mesh* m, int elastic, float* E, const double* dx, double*
   const dim3 blk(TBX, TBY);
   const float al = (float)m->P.alpha, cm = (float)m->P.c_mass;
   const float rx = (float)(1.0 / g.hx), ry = (float)(1.0 / g.hy), rz = (float)(1.0 / g.hz);
-  if (elastic) {
-    FSI_LAUNCH(m, P_NS_JVP32,
-               (nsq_tma_kernel<NCQ><<<(unsigned)nblk, blk, smem, m->stream>>>(
-                   *map, m->dx32, E, g.nx, g.ny, g.nz, nxp, nxyp, m->nn, al, cm, rx, ry, rz, m->tma_err)));
-  } else {
-    FSI_LAUNCH(m, P_NS_JVP32,
-               (nsq_tma_kernel<NCQ_FLUID><<<(unsigned)nblk, blk, smem, m->stream>>>(
-                   *map, m->dx32, E, g.nx, g.ny, g.nz, nxp, nxyp, m->nn, al, cm, rx, ry, rz, m->tma_err)));
-  }
+  FSI_LAUNCH(m, P_NS_JVP32,
+             (nsq_tma_kernel<<<(unsigned)nblk, blk, smem, m->stream>>>(*map, ncoef, m->dx32, E, g.nx, g.ny, g.nz, nxp,
+                                                                      nxyp, m->nn, al, cm, rx, ry, rz, m->tma_err)));
   (void)dx;
   (void)y;
   return FSI_OK;
