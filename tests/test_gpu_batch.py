@@ -65,7 +65,9 @@ def test_batched_jvp_matches_per_instance(flags, block):
     err = float((yb - ref).abs().max() / ref.abs().max())
     print(f"block {block} flags {flags}: max relative difference {err:.2e}")
     assert err <= (1e-6 if flags & fsi.FSI_FP32 else 1e-13)
-    assert launches1 - launches0 <= 2  # one operator launch (+ the float copy)
+    # one operator launch (+ the float copy); the float32 NS product from per-instance
+    # coefficients is an element launch and a node launch
+    assert launches1 - launches0 <= (3 if block == fsi.FSI_BLOCK_NS and flags & fsi.FSI_FP32 else 2)
 
 
 @pytest.mark.parametrize("precision", [fsi.FSI_PREC_FP64, fsi.FSI_PREC_FP32_IR])
