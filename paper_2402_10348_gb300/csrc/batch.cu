@@ -528,7 +528,9 @@ int build_tiles(fsi_batch* b, int target_mult, int grid_mult) {
 
 // the batched float32 NS product from per-instance coefficients (nsq_tma.cu): element
 // launch over every instance's 64 x 2-element tiles, node launch over its 128-node blocks
-int launch_nsq_batch(fsi_batch* b, const void* ops_dev, size_t, int cls, int use_active) {
+// work lists of the batched float32 NS product (built when the operator set is recorded,
+// never inside a captured cycle)
+int ensure_nsq_items(fsi_batch* b) {
   if (!b->nsq_eitems) {
     std::vector<int4> ei, ni;
     for (int i = 0; i < b->n; ++i) {
@@ -549,6 +551,11 @@ int launch_nsq_batch(fsi_batch* b, const void* ops_dev, size_t, int cls, int use
     b->nsq_ne = (int)ei.size();
     b->nsq_nn = (int)ni.size();
   }
+  return FSI_OK;
+}
+
+int launch_nsq_batch(fsi_batch* b, const void* ops_dev, size_t, int cls, int use_active) {
+  if (!b->nsq_eitems) return set_error(FSI_EINVAL, "batch: NS product work lists missing");
   fsi_mesh* m = b->meshes[0];
   const int* active = use_active == 1 ? b->act : (use_active == 2 ? b->live : nullptr);
   int rc = prof_begin(m, cls);
@@ -589,6 +596,7 @@ int record_set(fsi_batch* b, OpSet* set, unsigned flags, const double* dx_base, 
       if (rc) return rc;
     }
     const size_t bytes = sizeof(NSQBatchRec) * recs.size();
+    if (int rc = ensure_nsq_items(b)) return rc;
     if (int rc = set_storage(b, set, bytes)) return rc;
     FSI_CUDA(cudaMemcpyAsync(set->ops, recs.data(), bytes, cudaMemcpyHostToDevice, b->stream));
     FSI_CUDA(cudaStreamSynchronize(b->stream));
