@@ -554,17 +554,23 @@ int ensure_nsq_items(fsi_batch* b) {
   return FSI_OK;
 }
 
-int launch_nsq_batch(fsi_batch* b, const void* ops_dev, size_t, int cls, int use_active) {
+int launch_nsq_batch_prec(fsi_batch* b, const void* ops_dev, int cls, int use_active, bool f64) {
   if (!b->nsq_eitems) return set_error(FSI_EINVAL, "batch: NS product work lists missing");
   fsi_mesh* m = b->meshes[0];
   const int* active = use_active == 1 ? b->act : (use_active == 2 ? b->live : nullptr);
   int rc = prof_begin(m, cls);
   if (rc) return rc;
-  if ((rc = nsq_batch_launch(static_cast<const NSQBatchRec*>(ops_dev), b->nsq_eitems, b->nsq_ne, b->nsq_nitems,
-                             b->nsq_nn, active, b->stream)))
+  if ((rc = nsq_batch_launch(f64, static_cast<const NSQBatchRec*>(ops_dev), b->nsq_eitems, b->nsq_ne,
+                             b->nsq_nitems, b->nsq_nn, active, b->stream)))
     return rc;
   b->launches += 2;
   return prof_end(m, cls);
+}
+int launch_nsq_batch32(fsi_batch* b, const void* ops_dev, size_t, int cls, int use_active) {
+  return launch_nsq_batch_prec(b, ops_dev, cls, use_active, false);
+}
+int launch_nsq_batch64(fsi_batch* b, const void* ops_dev, size_t, int cls, int use_active) {
+  return launch_nsq_batch_prec(b, ops_dev, cls, use_active, true);
 }
 
 // (re)allocates a set's device records for `bytes` (a captured cycle holding the old
@@ -586,12 +592,12 @@ int record_set(fsi_batch* b, OpSet* set, unsigned flags, const double* dx_base, 
   const bool f32 = flags & FSI_FP32;
   bool all_ns = true;
   for (int i = 0; i < b->n; ++i) all_ns = all_ns && b->blocks[i] == FSI_BLOCK_NS;
-  if (f32 && all_ns) {
-    // float32 NS products from each instance's frozen coefficients (built here, on the
-    // staged states), TMA-staged, in one element and one node launch
+  if (all_ns) {
+    // NS products from each instance's frozen coefficients (built here, on the staged
+    // states) in one element and one node launch: float32 TMA-staged, float64 read directly
     std::vector<NSQBatchRec> recs(b->n);
     for (int i = 0; i < b->n; ++i) {
-      int rc = nsq_batch_record(b->meshes[i], flags, dx_base + b->off[i], y_base + b->off[i],
+      int rc = nsq_batch_record(b->meshes[i], flags, !f32, dx_base + b->off[i], y_base + b->off[i],
                                 b->dx32_own + b->off[i], &recs[i]);
       if (rc) return rc;
     }
@@ -601,8 +607,8 @@ int record_set(fsi_batch* b, OpSet* set, unsigned flags, const double* dx_base, 
     FSI_CUDA(cudaMemcpyAsync(set->ops, recs.data(), bytes, cudaMemcpyHostToDevice, b->stream));
     FSI_CUDA(cudaStreamSynchronize(b->stream));
     set->smem = 0;
-    set->cls = P_NS_JVP32;
-    set->launch = &launch_nsq_batch;
+    set->cls = f32 ? P_NS_JVP32 : P_NS_JVP64;
+    set->launch = f32 ? &launch_nsq_batch32 : &launch_nsq_batch64;
     return FSI_OK;
   }
   for (int i = 0; i < b->n; ++i) {

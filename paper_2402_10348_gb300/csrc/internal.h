@@ -185,6 +185,8 @@ int check_tma(fsi_mesh* m);
 // contribution scratch and output, its geometry.  64-byte aligned (the descriptor's rule).
 struct alignas(64) NSQBatchRec {
   unsigned char map[128];
+  const double* cq64;  // float64 products: the coefficients, read directly
+  double* E64;         // float64 products: the contribution scratch
   const float* dx32;
   const double* dx;
   float* E;
@@ -193,15 +195,18 @@ struct alignas(64) NSQBatchRec {
   int* err;
   int64_t nxyp, nn;
   double W;
+  double al64, cm64, rh64[3];  // the float64 product's constants
   int nx, ny, nz, nxp, pin, elastic;
   float al, cm, rhx, rhy, rhz;
 };
-// builds the instance's coefficients (if stale), scratch and descriptor and fills rec
-int nsq_batch_record(fsi_mesh* m, unsigned flags, const double* dx, double* y, float* dx32, NSQBatchRec* rec);
+// builds the instance's coefficients (if stale), scratch and descriptor and fills rec;
+// f64: a float64 product (coefficients read directly, no descriptor)
+int nsq_batch_record(fsi_mesh* m, unsigned flags, bool f64, const double* dx, double* y, float* dx32,
+                     NSQBatchRec* rec);
 // element and node launches of a batch (recs in device memory; items: (instance, x block,
 // y block, layer) and (instance, 128-node block)); active gates instances (nullable)
-int nsq_batch_launch(const NSQBatchRec* recs, const int4* eitems, int neitems, const int4* nitems, int nnitems,
-                     const int* active, cudaStream_t s);
+int nsq_batch_launch(bool f64, const NSQBatchRec* recs, const int4* eitems, int neitems, const int4* nitems,
+                     int nnitems, const int* active, cudaStream_t s);
 constexpr int NSQ_TBX = 64, NSQ_TBY = 2;  // element tile of the TMA product
 // [slots][elements] scratch of the element-centric products, grown on demand (ops_f64.cu)
 int ensure_elem_scratch(fsi_mesh* m, int slots, int64_t nxyp);

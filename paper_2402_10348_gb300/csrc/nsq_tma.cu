@@ -166,7 +166,21 @@ __global__ void __launch_bounds__(TBX * TBY) nsq_tma_batch_kernel(const NSQBatch
                R.ny, R.nz, R.nxp, R.nxyp, R.nn, R.al, R.cm, R.rhx, R.rhy, R.rhz, it.y * TBX, it.z * TBY, it.w, R.err);
 }
 
+// Batched float64 product from the coefficients (nsq_elem_body): one CTA of 64 x 2
+// threads per (instance, x block, y block, layer) work item
+__global__ void __launch_bounds__(TBX * TBY) nsq_elem_batch_kernel(const NSQBatchRec* __restrict__ recs,
+                                                                   const int4* __restrict__ items, const int* active) {
+  const int4 it = items[blockIdx.x];
+  if (active && !active[it.x]) return;
+  const NSQBatchRec& R = recs[it.x];
+  const int ex = it.y * TBX + threadIdx.x, ey = it.z * TBY + threadIdx.y;
+  if (ex >= R.nx || ey >= R.ny) return;
+  nsq_elem_body<double>(R.cq64, R.dx, R.E64, R.nx, R.ny, R.nz, R.nxp, R.nxyp, R.nn, R.elastic, R.al64, R.cm64,
+                        R.rh64[0], R.rh64[1], R.rh64[2], ex, ey, it.w);
+}
+
 // Batched node sums: one CTA per (instance, 128 consecutive nodes)
+template <typename T>
 __global__ void __launch_bounds__(128) ns_node_batch_kernel(const NSQBatchRec* __restrict__ recs,
                                                             const int4* __restrict__ items, const int* active) {
   const int4 it = items[blockIdx.x];
@@ -179,7 +193,8 @@ __global__ void __launch_bounds__(128) ns_node_batch_kernel(const NSQBatchRec* _
   const int64_t jk = n / (nx + 1);
   const int j = (int)(jk % (ny + 1)), k = (int)(jk / (ny + 1));
   const int64_t es = (int64_t)nz * R.nxyp;
-  float s[4] = {0.f, 0.f, 0.f, 0.f};
+  const T* E = sizeof(T) == 8 ? reinterpret_cast<const T*>(R.E64) : reinterpret_cast<const T*>(R.E);
+  T s[4] = {T(0), T(0), T(0), T(0)};
   for (int az = 1; az >= 0; --az) {
     const int ez = k - az;
     if (ez < 0 || ez >= nz) continue;
@@ -192,7 +207,7 @@ __global__ void __launch_bounds__(128) ns_node_batch_kernel(const NSQBatchRec* _
         const int64_t e = (int64_t)ez * R.nxyp + (int64_t)ey * R.nxp + ex;
         const int a = ax + 2 * ay + 4 * az;
 #pragma unroll
-        for (int f = 0; f < 4; ++f) s[f] += R.E[(8 * f + a) * es + e];
+        for (int f = 0; f < 4; ++f) s[f] += E[(8 * f + a) * es + e];
       }
     }
   }
@@ -249,7 +264,8 @@ int check_tma(fsi_mesh* m) {
   return FSI_OK;
 }
 
-int nsq_batch_record(fsi_mesh* m, unsigned flags, const double* dx, double* y, float* dx32, NSQBatchRec* rec) {
+int nsq_batch_record(fsi_mesh* m, unsigned flags, bool f64, const double* dx, double* y, float* dx32,
+                     NSQBatchRec* rec) {
   const unsigned eflags = flags & FSI_ELASTIC_AUG;
   if (m->cq_gen != m->stage_gen || m->cq_flags != eflags || !m->cq64)
     if (int rc = ns_build(m, flags)) return rc;
@@ -257,7 +273,7 @@ int nsq_batch_record(fsi_mesh* m, unsigned flags, const double* dx, double* y, f
   const int nxp = cq_pitch(m);
   const int64_t nxyp = (int64_t)nxp * g.ny;
   if (int rc = ensure_elem_scratch(m, 32, nxyp)) return rc;
-  if (m->cq_tmap_base != m->cq32)
+  if (!f64 && m->cq_tmap_base != m->cq32)
     if (int rc = encode_maps(m, nxp, nxyp)) return rc;
   if (!m->tma_err) {
     FSI_CUDA(cudaMalloc(&m->tma_err, sizeof(int)));
@@ -265,7 +281,17 @@ int nsq_batch_record(fsi_mesh* m, unsigned flags, const double* dx, double* y, f
   }
   const int elastic = (eflags && m->ns > 0) ? 1 : 0;
   memset(rec, 0, sizeof(*rec));
-  memcpy(rec->map, m->cq_tmap + (elastic ? 0 : 128), 128);
+  if (f64) {
+    rec->cq64 = m->cq64;
+    rec->E64 = m->ke_e;
+  } else {
+    memcpy(rec->map, m->cq_tmap + (elastic ? 0 : 128), 128);
+  }
+  rec->al64 = m->P.alpha;
+  rec->cm64 = m->P.c_mass;
+  rec->rh64[0] = 1.0 / g.hx;
+  rec->rh64[1] = 1.0 / g.hy;
+  rec->rh64[2] = 1.0 / g.hz;
   rec->dx32 = dx32;
   rec->dx = dx;
   rec->E = reinterpret_cast<float*>(m->ke_e);
@@ -289,11 +315,17 @@ int nsq_batch_record(fsi_mesh* m, unsigned flags, const double* dx, double* y, f
   return FSI_OK;
 }
 
-int nsq_batch_launch(const NSQBatchRec* recs, const int4* eitems, int neitems, const int4* nitems, int nnitems,
-                     const int* active, cudaStream_t s) {
+int nsq_batch_launch(bool f64, const NSQBatchRec* recs, const int4* eitems, int neitems, const int4* nitems,
+                     int nnitems, const int* active, cudaStream_t s) {
+  if (f64) {
+    if (neitems > 0) nsq_elem_batch_kernel<<<neitems, dim3(TBX, TBY), 0, s>>>(recs, eitems, active);
+    if (nnitems > 0) ns_node_batch_kernel<double><<<nnitems, 128, 0, s>>>(recs, nitems, active);
+    FSI_CUDA(cudaGetLastError());
+    return FSI_OK;
+  }
   const size_t smem = sizeof(float) * (size_t)TSTAGES * NCQ * TBX * TBY;
   if (neitems > 0) nsq_tma_batch_kernel<<<neitems, dim3(TBX, TBY), smem, s>>>(recs, eitems, active);
-  if (nnitems > 0) ns_node_batch_kernel<<<nnitems, 128, 0, s>>>(recs, nitems, active);
+  if (nnitems > 0) ns_node_batch_kernel<float><<<nnitems, 128, 0, s>>>(recs, nitems, active);
   FSI_CUDA(cudaGetLastError());
   return FSI_OK;
 }

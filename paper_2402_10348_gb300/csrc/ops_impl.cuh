@@ -282,22 +282,24 @@ __global__ void __launch_bounds__(128) ns_node_kernel(const T* __restrict__ E, i
   }
 }
 
-// NS product from the quadrature-point coefficients (see nsq_point), element-centric
+// NS product from the quadrature-point coefficients (see nsq_point) of element (ex, ey, ez)
+// into its 32 contribution slots (element-centric)
 template <typename T>
-__global__ void __launch_bounds__(128) nsq_elem_kernel(const T* __restrict__ cq, const T* __restrict__ dx,
-                                                       T* __restrict__ E, int nx, int ny, int nz, int nxp, int64_t nxyp,
-                                                       int64_t nn, int elastic, T al, T cmass, T rhx, T rhy, T rhz) {
-  ElemIdx I;
-  if (!I.set(nx, ny, nz, nxp, nxyp)) return;
+__device__ __forceinline__ void nsq_elem_body(const T* __restrict__ cq, const T* __restrict__ dx, T* __restrict__ E,
+                                              int nx, int ny, int nz, int nxp, int64_t nxyp, int64_t nn, int elastic,
+                                              T al, T cmass, T rhx, T rhy, T rhz, int ex, int ey, int ez) {
+  const int64_t sy = nx + 1, sz = (int64_t)(nx + 1) * (ny + 1);
+  const int64_t n0 = ex + sy * ey + sz * ez;
+  const int64_t off[8] = {0, 1, sy, sy + 1, sz, sz + 1, sz + sy, sz + sy + 1};
   T x[4][8], c[4][8];
 #pragma unroll
   for (int f = 0; f < 4; ++f)
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
-      x[f][a] = __ldg(dx + f * nn + I.n0 + I.off[a]);
+      x[f][a] = __ldg(dx + f * nn + n0 + off[a]);
       c[f][a] = T(0);
     }
-  const T* e0 = cq + (int64_t)I.ez * 8 * NCQ * nxyp + (int64_t)I.ey * nxp + I.ex;
+  const T* e0 = cq + (int64_t)ez * 8 * NCQ * nxyp + (int64_t)ey * nxp + ex;
 #pragma unroll 1
   for (int q = 0; q < 8; ++q) {
     QW<T> w;
@@ -313,10 +315,21 @@ __global__ void __launch_bounds__(128) nsq_elem_kernel(const T* __restrict__ cq,
     nsq_point<T>(CoefRef<T>{e0 + (int64_t)q * NCQ * nxyp, nxyp}, elastic != 0, dv, gd, dpr.v, dgp, al, cmass, w, rhx,
                  rhy, rhz, c);
   }
+  const int64_t e = (int64_t)ez * nxyp + (int64_t)ey * nxp + ex;
+  const int64_t es = (int64_t)nz * nxyp;
 #pragma unroll
   for (int f = 0; f < 4; ++f)
 #pragma unroll
-    for (int a = 0; a < 8; ++a) E[(8 * f + a) * I.es + I.e] = c[f][a];
+    for (int a = 0; a < 8; ++a) E[(8 * f + a) * es + e] = c[f][a];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) nsq_elem_kernel(const T* __restrict__ cq, const T* __restrict__ dx,
+                                                       T* __restrict__ E, int nx, int ny, int nz, int nxp, int64_t nxyp,
+                                                       int64_t nn, int elastic, T al, T cmass, T rhx, T rhy, T rhz) {
+  ElemIdx I;
+  if (!I.set(nx, ny, nz, nxp, nxyp)) return;
+  nsq_elem_body<T>(cq, dx, E, nx, ny, nz, nxp, nxyp, nn, elastic, al, cmass, rhx, rhy, rhz, I.ex, I.ey, I.ez);
 }
 
 template <typename T>
