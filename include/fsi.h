@@ -434,7 +434,11 @@ int fsi_batch_destroy(fsi_batch* batch);
  * (a replayed graph counts its nodes).  Outputs are nullable. */
 int fsi_batch_layout(const fsi_batch* batch, int64_t* offsets, int32_t* target_mult, int32_t* grid_mult,
                      int64_t* launches);
-/* y = J_i(states[i]) dx for every instance, one launch (flags as in fsi_jvp) */
+/* y = J_i(states[i]) dx for every instance (flags as in fsi_jvp).  NS batches: each
+ * instance's quadrature-point coefficients are built at its state (Section 2.4's
+ * linearization frozen), then one element launch over all instances' tiles (float32: the
+ * coefficients TMA-staged) and one node launch; AC and B batches: one persistent launch of
+ * the re-interpolating element operators. */
 int fsi_batch_jvp(fsi_batch* batch, const fsi_state* states, const double* dx, double* y, uint32_t flags);
 /* fsi_gmres for every instance (Jacobi or no preconditioner; FSI_PREC_FP64 or
  * FSI_PREC_FP32_IR; opts.m must be the batch's m).  infos: [n], nullable.  Returns
