@@ -36,6 +36,7 @@
 #include <sys/stat.h>
 
 #include "internal.h"
+#include "pcnet.h"
 
 namespace fsi {
 
@@ -117,6 +118,11 @@ struct fsi_batch {
   int use_graph = 1;
   int64_t launches = 0;          // launches of this batch (graph replays count their nodes)
   int64_t launches_per_cycle = 0;
+  // flexible GMRES with each instance's attached network (NS batches): the directions
+  // Z [mm][ntot], set per solve
+  double* Zb = nullptr;
+  int64_t zb_len = 0;
+  int use_pc = 0, pc_alternate = 0;
   // work lists of the batched float32 NS coefficient product (built on first use)
   int4* nsq_eitems = nullptr;     // (instance, x block, y block, layer)
   int nsq_ne = 0;
@@ -153,7 +159,8 @@ __device__ __forceinline__ double* bslot(double* V, const int64_t* vbase, int b,
 // z_b = dinv_b * V_b[j] (and the float copy for float32 operators)
 __global__ void bk_precond(const int4* __restrict__ items, const int* __restrict__ act, double* V,
                            const int64_t* vbase, const int64_t* off, const int64_t* nloc, int M1, int j,
-                           const double* __restrict__ dinv, double* __restrict__ z, float* const* dx32) {
+                           const double* __restrict__ dinv, double* __restrict__ z, float* const* dx32,
+                           double* __restrict__ zs) {
   const int4 it = items[blockIdx.x];
   const int b = it.x;
   if (!act[b]) return;
@@ -163,6 +170,56 @@ __global__ void bk_precond(const int4* __restrict__ items, const int* __restrict
     const double v = dinv[off[b] + e] * bslot(V, vbase, b, M1, c, j)[threadIdx.x];
     z[off[b] + e] = v;
     if (dx32) dx32[b][e] = (float)v;
+    if (zs) zs[off[b] + e] = v;  // flexible GMRES keeps the direction
+  }
+}
+
+// t = V_j (concatenated float64 copy of basis slot j of the active instances)
+__global__ void bk_extract(const int4* __restrict__ items, const int* __restrict__ act, double* V,
+                           const int64_t* vbase, const int64_t* off, const int64_t* nloc, int M1, int j,
+                           double* __restrict__ t) {
+  const int4 it = items[blockIdx.x];
+  const int b = it.x;
+  if (!act[b]) return;
+  for (int64_t c = it.y; c < it.z; ++c) {
+    const int64_t e = c * BCH + threadIdx.x;
+    if (e >= nloc[b]) break;
+    t[off[b] + e] = bslot(V, vbase, b, M1, c, j)[threadIdx.x];
+  }
+}
+
+// z = Z_j (the network's direction as the operator input, with its float copy)
+__global__ void bk_zfill(const int4* __restrict__ items, const int* __restrict__ act, const double* __restrict__ zs,
+                         const int64_t* off, const int64_t* nloc, double* __restrict__ z, float* const* dx32) {
+  const int4 it = items[blockIdx.x];
+  const int b = it.x;
+  if (!act[b]) return;
+  for (int64_t c = it.y; c < it.z; ++c) {
+    const int64_t e = c * BCH + threadIdx.x;
+    if (e >= nloc[b]) break;
+    const double v = zs[off[b] + e];
+    z[off[b] + e] = v;
+    if (dx32) dx32[b][e] = (float)v;
+  }
+}
+
+// x += sum_{i < jend} y_i Z_i (flexible GMRES)
+__global__ void bk_zcombine(const int4* __restrict__ items, const BKry* __restrict__ K, const int* live,
+                            const double* __restrict__ Z, int64_t ntot, const int64_t* off, const int64_t* nloc,
+                            double* __restrict__ x) {
+  const int4 it = items[blockIdx.x];
+  const int b = it.x;
+  if (!live[b]) return;
+  __shared__ double ys[BMMAX];
+  const int jend = K[b].jend;
+  for (int i = threadIdx.x; i < jend; i += blockDim.x) ys[i] = K[b].y[i];
+  __syncthreads();
+  for (int64_t c = it.y; c < it.z; ++c) {
+    const int64_t e = c * BCH + threadIdx.x;
+    if (e >= nloc[b]) break;
+    double s = 0.0;
+    for (int i = 0; i < jend; ++i) s += ys[i] * Z[(int64_t)i * ntot + off[b] + e];
+    x[off[b] + e] += s;
   }
 }
 
@@ -652,9 +709,22 @@ int run_set(fsi_batch* b, const OpSet& s, int gate) { return s.launch(b, s.ops, 
 int enqueue_step(fsi_batch* b, int j, double rtol, bool f32) {
   const int NI = b->nitems, nb = b->n, M1 = b->M1;
   cudaStream_t s = b->stream;
-  BK_LAUNCH(b, P_KRYLOV, bk_precond<<<NI, BVB, 0, s>>>(b->items_dev, b->act, b->V, b->vbase_dev, b->off_dev,
-                                                         b->nloc_dev, M1, j, b->dinv, b->z,
-                                                         f32 ? b->dx32_dev : nullptr));
+  double* Zj = b->use_pc ? b->Zb + (int64_t)j * b->ntot : nullptr;
+  if (b->use_pc && !(b->pc_alternate && (j & 1))) {
+    // flexible GMRES, network direction: z_j = M_i(v_j) per instance (|v_j| = 1)
+    BK_LAUNCH(b, P_KRYLOV, bk_extract<<<NI, BVB, 0, s>>>(b->items_dev, b->act, b->V, b->vbase_dev, b->off_dev,
+                                                         b->nloc_dev, M1, j, b->t));
+    for (int i = 0; i < nb; ++i) {
+      fsi_mesh* m = b->meshes[i];
+      if (int rc = pcn::apply(m->pc, b->t + b->off[i], 1.0, b->dinv + b->off[i], Zj + b->off[i])) return rc;
+    }
+    BK_LAUNCH(b, P_KRYLOV, bk_zfill<<<NI, BVB, 0, s>>>(b->items_dev, b->act, Zj, b->off_dev, b->nloc_dev, b->z,
+                                                       f32 ? b->dx32_dev : nullptr));
+  } else {
+    BK_LAUNCH(b, P_KRYLOV, bk_precond<<<NI, BVB, 0, s>>>(b->items_dev, b->act, b->V, b->vbase_dev, b->off_dev,
+                                                           b->nloc_dev, M1, j, b->dinv, b->z,
+                                                           f32 ? b->dx32_dev : nullptr, Zj));
+  }
   int rc = run_set(b, b->jvp_inner, 1);
   if (rc) return rc;
   const int nvec = j + 1;
@@ -692,8 +762,12 @@ int enqueue_cycle(fsi_batch* b, double rtol, bool f32) {
     if (rc) return rc;
   }
   BK_LAUNCH(b, P_KRY_SMALL, bk_lsq<<<gx1(nb), 128, 0, s>>>(b->K, nb, b->live, b->mm));
-  BK_LAUNCH(b, P_KRYLOV, bk_combine<<<NI, BVB, 0, s>>>(b->items_dev, b->K, b->live, b->V, b->vbase_dev, b->off_dev,
-                                                        b->nloc_dev, M1, b->dinv, b->d));
+  if (b->use_pc)
+    BK_LAUNCH(b, P_KRYLOV, bk_zcombine<<<NI, BVB, 0, s>>>(b->items_dev, b->K, b->live, b->Zb, b->ntot, b->off_dev,
+                                                           b->nloc_dev, b->d));
+  else
+    BK_LAUNCH(b, P_KRYLOV, bk_combine<<<NI, BVB, 0, s>>>(b->items_dev, b->K, b->live, b->V, b->vbase_dev, b->off_dev,
+                                                          b->nloc_dev, M1, b->dinv, b->d));
   // true residual of the inner system: r = rin - A d (live instances)
   if (f32)
     BK_LAUNCH(b, P_KRY_CONV, bk_tofloat<<<NI, BVB, 0, s>>>(b->items_dev, b->live, b->off_dev, b->nloc_dev, b->d,
@@ -754,7 +828,7 @@ int inner_solve(fsi_batch* b, std::vector<int> live, double rtol, int max_iter, 
     first = false;
     if ((rc = upload_live(b, live))) return rc;
     // the legacy default stream cannot be captured: launch the cycle directly there
-    if (b->use_graph && b->stream != nullptr) {
+    if (b->use_graph && !b->use_pc && b->stream != nullptr) {
       if (!b->cycle || b->graph_rtol != rtol || b->graph_f32 != (int)f32) {
         if (b->cycle) cudaGraphExecDestroy(b->cycle);
         b->cycle = nullptr;
@@ -879,6 +953,7 @@ int fsi_batch_destroy(fsi_batch* b) {
   for (OpSet* s : {&b->jvp_inner, &b->jvp_d, &b->jvp_outer, &b->jvp_user}) cudaFree(s->ops);
   cudaFree(b->nsq_eitems);
   cudaFree(b->nsq_nitems);
+  cudaFree(b->Zb);
   cudaFree(b->geoms_dev), cudaFree(b->tiles_dev), cudaFree(b->items_dev), cudaFree(b->item_first_dev);
   cudaFree(b->V), cudaFree(b->vbase_dev), cudaFree(b->off_dev), cudaFree(b->nloc_dev), cudaFree(b->dx32_dev);
   cudaFree(b->w), cudaFree(b->z), cudaFree(b->r), cudaFree(b->t), cudaFree(b->dinv), cudaFree(b->d);
@@ -1002,10 +1077,31 @@ int fsi_batch_gmres(fsi_batch* b, const fsi_state* states, const double* rhs, do
                     fsi_solve_info* infos) {
   if (!b || !states || !rhs || !x || !o) return set_error(FSI_EINVAL, "fsi_batch_gmres: null argument");
   if (o->m != b->mm) return set_error(FSI_EINVAL, "fsi_batch_gmres: opts.m must equal the batch's restart length");
-  if (o->precond != FSI_PC_JACOBI && o->precond != FSI_PC_NONE)
-    return set_error(FSI_EINVAL, "fsi_batch_gmres: Jacobi or no preconditioner");
+  if (o->precond != FSI_PC_JACOBI && o->precond != FSI_PC_NONE && o->precond != FSI_PC_LEARNED)
+    return set_error(FSI_EINVAL, "fsi_batch_gmres: unknown preconditioner");
+  const bool learned = o->precond == FSI_PC_LEARNED;
+  if (learned) {
+    // flexible GMRES: every entry an NS block with a network attached, on the batch's stream
+    for (int i = 0; i < b->n; ++i) {
+      fsi_mesh* m = b->meshes[i];
+      if (b->blocks[i] != FSI_BLOCK_NS || !m->pc)
+        return set_error(FSI_EINVAL, "fsi_batch_gmres: FSI_PC_LEARNED needs NS entries with a network (fsi_set_pc)");
+      if (m->stream != b->stream)
+        return set_error(FSI_EINVAL, "fsi_batch_gmres: FSI_PC_LEARNED needs every instance on the batch's stream");
+    }
+    const int64_t zl = (int64_t)b->mm * b->ntot;
+    if (b->zb_len < zl) {
+      cudaFree(b->Zb);
+      b->Zb = nullptr;
+      b->zb_len = 0;
+      FSI_CUDA(cudaMalloc(&b->Zb, sizeof(double) * (size_t)zl));
+      b->zb_len = zl;
+    }
+  }
+  b->use_pc = learned ? 1 : 0;
+  b->pc_alternate = (learned && (o->flags & FSI_PC_ALTERNATE)) ? 1 : 0;
   const bool f32 = o->precision == FSI_PREC_FP32_IR;
-  const unsigned base = o->flags & ~(FSI_FP32 | FSI_HARVEST);
+  const unsigned base = o->flags & ~(FSI_FP32 | FSI_HARVEST | FSI_PC_ALTERNATE | FSI_NO_STALL_STOP);
   const unsigned inner = f32 ? (base | FSI_FP32) : base;
   const int nb = b->n, NI = b->nitems;
   cudaStream_t s = b->stream;
@@ -1015,14 +1111,14 @@ int fsi_batch_gmres(fsi_batch* b, const fsi_state* states, const double* rhs, do
   for (int i = 0; i < nb; ++i) {
     BlockInfo bi;
     if ((rc = block_info(b->meshes[i], b->blocks[i], &bi))) return rc;
-    if (o->precond == FSI_PC_JACOBI) {
+    if (o->precond != FSI_PC_NONE) {  // Jacobi, or the network's input scaling and alternate directions
       if ((rc = op_diag(b->meshes[i], bi, b->dinv + b->off[i], f32 ? (base | FSI_FP32) : base))) return rc;
     } else {
       std::vector<double> ones(bi.n, 1.0);
       FSI_CUDA(cudaMemcpy(b->dinv + b->off[i], ones.data(), sizeof(double) * bi.n, cudaMemcpyHostToDevice));
     }
   }
-  if (o->precond == FSI_PC_JACOBI)
+  if (o->precond != FSI_PC_NONE)
     BK_LAUNCH(b, P_KRYLOV, bk_recip<<<608, 256, 0, s>>>(b->dinv, b->ntot));
   if ((rc = record_set(b, &b->jvp_inner, inner, b->z, b->w)) || (rc = record_set(b, &b->jvp_d, inner, b->d, b->t)))
     return rc;
@@ -1309,8 +1405,11 @@ int fsi_batch_stepper_create(fsi_mesh* const* meshes, int32_t n, int32_t m, fsi_
 int fsi_batch_step(fsi_batch_stepper* s, fsi_state* states, const fsi_step_opts* o, fsi_step_info* infos) {
   if (!s || !states || !o || !infos) return set_error(FSI_EINVAL, "fsi_batch_step: null argument");
   if (o->k_max < 1) return set_error(FSI_EINVAL, "fsi_batch_step: k_max must be >= 1");
-  if (o->solve.precond != FSI_PC_JACOBI && o->solve.precond != FSI_PC_NONE)
-    return set_error(FSI_EINVAL, "fsi_batch_step: Jacobi or no preconditioner");
+  if (o->solve.precond != FSI_PC_JACOBI && o->solve.precond != FSI_PC_NONE && o->solve.precond != FSI_PC_LEARNED)
+    return set_error(FSI_EINVAL, "fsi_batch_step: unknown preconditioner");
+  // the network preconditions the NS blocks; the Allen-Cahn and B blocks use Jacobi
+  fsi_solve_opts other = o->solve;
+  if (other.precond == FSI_PC_LEARNED) other.precond = FSI_PC_JACOBI;
   const int n = s->n;
   std::vector<int64_t> a0(n), d0(n);
   int rc;
@@ -1326,8 +1425,8 @@ int fsi_batch_step(fsi_batch_stepper* s, fsi_state* states, const fsi_step_opts*
   for (int k = 0; k < o->k_max; ++k) {
     std::vector<double> ratio(n, 0.0);
     if ((rc = batch_block(s->ns, ns_inst, live, states, o->solve, s->rhs, s->dx, ratio, infos, 0)) ||
-        (rc = batch_block(s->ac, s->ac_inst, live, states, o->solve, s->rhs, s->dx, ratio, infos, 1)) ||
-        (rc = batch_block(s->bb, s->b_inst, live, states, o->solve, s->rhs, s->dx, ratio, infos, 2)))
+        (rc = batch_block(s->ac, s->ac_inst, live, states, other, s->rhs, s->dx, ratio, infos, 1)) ||
+        (rc = batch_block(s->bb, s->b_inst, live, states, other, s->rhs, s->dx, ratio, infos, 2)))
       return rc;
     int nlive = 0;
     for (int i = 0; i < n; ++i) {

@@ -5,7 +5,7 @@ The batched operator evaluates every element and node sum in the same order as t
 single-mesh launch (only the assignment of tiles to CTAs differs); the two kernels are
 separate instantiations of one body, so the compiler may contract a different set of
 multiply-adds: results agree to a few ulps, not bit for bit.  Batched GMRES follows
-the same algorithm per instance; its solutions are checked against the residual of
+the same algorithm per instance (flexible GMRES with each instance's network as well); its solutions are checked against the residual of
 the per-instance operator and against per-instance solves (two solutions that both
 meet rel-res 1e-10 differ by up to the condition number times 1e-10: measured up to
 2.2e-5 on these NS blocks, so the solutions are compared at 1e-4)."""
@@ -222,3 +222,103 @@ def test_batched_time_steps_match_per_instance_steps_and_the_oracle(precision):
                 if i == 0 and precision == fsi.FSI_PREC_FP64:
                     eo = np.linalg.norm(a[sl] - ref.xn[sl]) / np.linalg.norm(ref.xn[sl])
                     assert eo <= 1e-10, (s, sl, eo)
+
+
+@pytest.mark.parametrize("precision", [fsi.FSI_PREC_FP64, fsi.FSI_PREC_FP32_IR])
+def test_batched_flexible_gmres_with_the_network(precision):
+    """Flexible GMRES over a batch with each instance's own network (untrained seeded
+    weights, network and Jacobi directions alternately): every instance reaches rel-res
+    1e-10, checked with its own float64 operator, and its solution agrees with the
+    per-instance Jacobi solve at 1e-4 (both meet 1e-10; the difference is the conditioning
+    times 1e-10).  Without FSI_PC_ALTERNATE the solve still returns (network directions
+    only); an AC batch refuses the network."""
+    from workloads import he_normal_weights
+    descs, meshes, states, stream = _instances([8, 12, 16], seed=4)
+    pcs = []
+    for m in meshes:
+        pc = fsi.fsi_pc_create(m)
+        fsi.fsi_pc_set_weights(pc, he_normal_weights(pc.fan, 7))
+        fsi.fsi_set_pc(m, pc)
+        pcs.append(pc)
+    b = fsi.fsi_batch_create(meshes, block=fsi.FSI_BLOCK_NS, m=30)
+    rhs = []
+    with torch.cuda.stream(stream):
+        for i, m in enumerate(meshes):
+            r = torch.zeros(b.offsets[i + 1] - b.offsets[i], dtype=torch.float64, device=DEV)
+            fsi.fsi_residual(m, fsi.FSI_BLOCK_NS, *states[i], r)
+            rhs.append(r)
+    torch.cuda.synchronize()
+    o = fsi.solve_opts(m=30, rtol=1e-10, max_iter=4000, precision=precision, ir_inner_rtol=1e-3, ir_max=60)
+    jac = []
+    with torch.cuda.stream(stream):
+        for i, m in enumerate(meshes):
+            x = torch.zeros_like(rhs[i])
+            fsi.fsi_gmres(m, fsi.FSI_BLOCK_NS, *states[i], rhs[i], x, o)
+            jac.append(x)
+        ol = fsi.fsi_solve_opts.from_buffer_copy(o)
+        ol.precond = fsi.FSI_PC_LEARNED
+        ol.flags |= fsi.FSI_PC_ALTERNATE
+        xb = torch.zeros(b.offsets[-1], dtype=torch.float64, device=DEV)
+        infos = fsi.fsi_batch_gmres(b, states, _concat(rhs), xb, ol)
+    torch.cuda.synchronize()
+    for i, m in enumerate(meshes):
+        xi = xb[b.offsets[i]:b.offsets[i + 1]].contiguous()
+        assert infos[i].rel_res <= 1e-10
+        t = torch.zeros_like(xi)
+        with torch.cuda.stream(stream):
+            fsi.fsi_jvp(m, fsi.FSI_BLOCK_NS, *states[i], xi, t)
+        torch.cuda.synchronize()
+        assert float(torch.linalg.norm(rhs[i] - t) / torch.linalg.norm(rhs[i])) <= 1.5e-10
+        assert float(torch.linalg.norm(xi - jac[i]) / torch.linalg.norm(jac[i])) <= 1e-4
+    # network directions only: the call completes (convergence is not asserted)
+    ol.flags &= ~fsi.FSI_PC_ALTERNATE
+    ol.max_iter = 120
+    with torch.cuda.stream(stream):
+        fsi.fsi_batch_gmres(b, states, _concat(rhs), xb, ol, allow_noconv=True)
+    torch.cuda.synchronize()
+    ba = fsi.fsi_batch_create(meshes, block=fsi.FSI_BLOCK_AC(0), m=30)
+    with pytest.raises(fsi.FsiError) as e:
+        fsi.fsi_batch_gmres(ba, states, torch.zeros(ba.offsets[-1], dtype=torch.float64, device=DEV),
+                            torch.zeros(ba.offsets[-1], dtype=torch.float64, device=DEV), ol)
+    assert e.value.code == fsi.FSI_EINVAL
+
+
+def test_batched_time_steps_with_the_network():
+    """Batched steps whose NS solves use flexible GMRES with each instance's network
+    (alternate directions; Jacobi for the Allen-Cahn and B blocks) against per-instance
+    Jacobi steps: two steps of three fixed nonlinear iterations, every solve to rel-res
+    1e-12, the fields agree to 1e-8."""
+    from workloads import he_normal_weights
+    descs, xs = _cavity_states([5, 7, 6])
+    stream = torch.cuda.Stream()
+    o = fsi.solve_opts(m=30, rtol=1e-12, max_iter=6000)
+    singles, batched, meshes_b, pcs = [], [], [], []
+    for d, x in zip(descs, xs):
+        ms = fsi.fsi_create_mesh(d)
+        fsi.fsi_set_stream(ms, stream)
+        mb = fsi.fsi_create_mesh(d)
+        fsi.fsi_set_stream(mb, stream)
+        pc = fsi.fsi_pc_create(mb)
+        fsi.fsi_pc_set_weights(pc, he_normal_weights(pc.fan, 5))
+        fsi.fsi_set_pc(mb, pc)
+        pcs.append(pc)
+        singles.append((ms, [T(x), T(x), T(np.zeros_like(x))]))
+        batched.append([T(x), T(x), T(np.zeros_like(x))])
+        meshes_b.append(mb)
+    stepper = fsi.fsi_batch_stepper_create(meshes_b, m=30)
+    ol = fsi.fsi_solve_opts.from_buffer_copy(o)
+    ol.precond = fsi.FSI_PC_LEARNED
+    ol.flags |= fsi.FSI_PC_ALTERNATE
+    for s in range(2):
+        with torch.cuda.stream(stream):
+            for ms, st in singles:
+                fsi.fsi_step(ms, *st, k_max=3, fixed_iters=True, solve=o)
+            infos = fsi.fsi_batch_step(stepper, batched, k_max=3, fixed_iters=True, solve=ol)
+        torch.cuda.synchronize()
+        for i, d in enumerate(descs):
+            assert infos[i].nl_iters == 3 and infos[i].stalled_solves == 0
+            a = batched[i][1].cpu().numpy().reshape(d.ncomp, d.nn)
+            b = singles[i][1][1].cpu().numpy().reshape(d.ncomp, d.nn)
+            for sl in (slice(0, 3), slice(3, 4), slice(4, 6), slice(6, 12)):
+                e = np.linalg.norm(a[sl] - b[sl]) / np.linalg.norm(b[sl])
+                assert e <= 1e-8, (s, i, sl, e)
