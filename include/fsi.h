@@ -440,9 +440,13 @@ int fsi_batch_layout(const fsi_batch* batch, int64_t* offsets, int32_t* target_m
  * coefficients TMA-staged) and one node launch; AC and B batches: one persistent launch of
  * the re-interpolating element operators. */
 int fsi_batch_jvp(fsi_batch* batch, const fsi_state* states, const double* dx, double* y, uint32_t flags);
-/* fsi_gmres for every instance (Jacobi or no preconditioner; FSI_PREC_FP64 or
- * FSI_PREC_FP32_IR; opts.m must be the batch's m).  infos: [n], nullable.  Returns
- * FSI_ENOCONV if some instance misses rtol (its x holds the last iterate). */
+/* fsi_gmres for every instance (FSI_PREC_FP64 or FSI_PREC_FP32_IR; opts.m must be the
+ * batch's m).  Preconditioners: Jacobi, none, or FSI_PC_LEARNED for NS batches whose
+ * meshes all have a network attached (fsi_set_pc) and share the batch's stream: flexible
+ * GMRES keeping each instance's directions, the network applied per instance (with
+ * FSI_PC_ALTERNATE at even Arnoldi steps, Jacobi at odd ones), launched directly (no
+ * captured cycle).  infos: [n], nullable.  Returns FSI_ENOCONV if some instance misses
+ * rtol (its x holds the last iterate); FSI_EINVAL for a network on other blocks. */
 int fsi_batch_gmres(fsi_batch* batch, const fsi_state* states, const double* rhs, double* x,
                     const fsi_solve_opts* opts, fsi_solve_info* infos);
 /* the project's autotuner: times the batched operator apply over candidate launch
