@@ -1122,13 +1122,34 @@ int fsi_batch_gmres(fsi_batch* b, const fsi_state* states, const double* rhs, do
     BK_LAUNCH(b, P_KRYLOV, bk_recip<<<608, 256, 0, s>>>(b->dinv, b->ntot));
   if ((rc = record_set(b, &b->jvp_inner, inner, b->z, b->w)) || (rc = record_set(b, &b->jvp_d, inner, b->d, b->t)))
     return rc;
-  std::vector<int> iters(nb, 0), restarts(nb, 0), stalled(nb, 0), refin(nb, 0);
+  std::vector<int> iters(nb, 0), restarts(nb, 0), stalled(nb, 0), refin(nb, 0), fallback(nb, 0);
   std::vector<double> rel(nb, 0.0), inner_rel(nb, 0.0);
   std::vector<int> live(nb, 1);
   if (!f32) {
     FSI_CUDA(cudaMemcpyAsync(b->rin, rhs, sizeof(double) * b->ntot, cudaMemcpyDeviceToDevice, s));
     if ((rc = inner_solve(b, live, o->rtol, o->max_iter, false, iters, restarts, rel, stalled))) return rc;
     FSI_CUDA(cudaMemcpyAsync(x, b->d, sizeof(double) * b->ntot, cudaMemcpyDeviceToDevice, s));
+    if (b->use_pc) {
+      // instances the flexible solve left above rtol (a stalled network): Jacobi GMRES on
+      // their remaining residual (the last cycle's r = rhs - A x), x += d
+      std::vector<int> fb(nb, 0);
+      double worst = 0.0;
+      int nfb = 0;
+      for (int i = 0; i < nb; ++i)
+        if (rel[i] > o->rtol && iters[i] < o->max_iter) fb[i] = 1, ++nfb, worst = std::max(worst, rel[i]);
+      if (nfb) {
+        b->use_pc = 0;
+        FSI_CUDA(cudaMemcpyAsync(b->rin, b->r, sizeof(double) * b->ntot, cudaMemcpyDeviceToDevice, s));
+        std::vector<double> rel2(nb, 0.0);
+        std::vector<int> st2(nb, 0);
+        if ((rc = inner_solve(b, fb, o->rtol / worst, o->max_iter, false, iters, restarts, rel2, st2))) return rc;
+        if ((rc = upload_live(b, fb))) return rc;
+        BK_LAUNCH(b, P_KRYLOV, bk_axpy<<<NI, BVB, 0, s>>>(b->items_dev, b->live, b->off_dev, b->nloc_dev, 1.0, b->d,
+                                                           x));
+        for (int i = 0; i < nb; ++i)
+          if (fb[i]) rel[i] *= rel2[i], stalled[i] = st2[i], fallback[i] = 1;
+      }
+    }
   } else {
     // float32 operator inside float64 refinement: x = 0, r = rhs; repeat: A32 d = r,
     // x += d, r = rhs - A64 x
@@ -1165,6 +1186,7 @@ int fsi_batch_gmres(fsi_batch* b, const fsi_state* states, const double* rhs, do
       BK_LAUNCH(b, P_KRYLOV, bk_rn2<<<gx1(nb), 128, 0, s>>>(b->item_first_dev, b->part, b->K, b->live, nb,
                                                              b->out_dev));
       if ((rc = read_out(b))) return rc;
+      bool pc_stalled = false;
       for (int i = 0; i < nb; ++i) {
         if (!live[i]) continue;
         const double r2 = b->host_out[i];
@@ -1172,8 +1194,15 @@ int fsi_batch_gmres(fsi_batch* b, const fsi_state* states, const double* rhs, do
         prev[i] = rel[i];
         rel[i] = std::sqrt(r2) / bn[i];
         refin[i] = k + 1;
-        if (rel[i] > o->rtol && rel[i] > 0.9 * prev[i]) live[i] = 0, stalled[i] = 1;
+        const bool no_gain = rel[i] > o->rtol && rel[i] > 0.9 * prev[i];
+        if (b->use_pc && (st_in[i] || no_gain)) {
+          pc_stalled = true;  // the network failed its inner solve: Jacobi from here on
+          fallback[i] = 1;
+          continue;
+        }
+        if (no_gain) live[i] = 0, stalled[i] = 1;
       }
+      if (pc_stalled) b->use_pc = 0;
     }
   }
   bool all = true;
@@ -1186,9 +1215,11 @@ int fsi_batch_gmres(fsi_batch* b, const fsi_state* states, const double* rhs, do
       infos[i].applies = iters[i] + restarts[i] + refin[i];
       infos[i].rel_res = rel[i];
       infos[i].stalled = stalled[i];
+      infos[i].fallback = fallback[i];
     }
     all = all && rel[i] <= o->rtol;
   }
+  b->use_pc = 0;
   FSI_CUDA(cudaStreamSynchronize(s));
   if (!all) return set_error(FSI_ENOCONV, "batch GMRES: tolerance not reached by every instance");
   return FSI_OK;
