@@ -229,11 +229,11 @@ def test_batched_flexible_gmres_with_the_network(precision):
     """Flexible GMRES over a batch with each instance's own network (untrained seeded
     weights, network and Jacobi directions alternately): every instance reaches rel-res
     1e-10, checked with its own float64 operator, and its solution agrees with the
-    per-instance Jacobi solve at 1e-4 (both meet 1e-10; the difference is the conditioning
-    times 1e-10).  Without FSI_PC_ALTERNATE the solve still returns (network directions
+    per-instance float64 Jacobi solve at 1e-4 (both meet 1e-10; the difference is the
+    conditioning times 1e-10).  Without FSI_PC_ALTERNATE the solve still returns (network directions
     only); an AC batch refuses the network."""
     from workloads import he_normal_weights
-    descs, meshes, states, stream = _instances([8, 12, 16], seed=4)
+    descs, meshes, states, stream = _instances([8, 12, 16], seed=3)
     pcs = []
     for m in meshes:
         pc = fsi.fsi_pc_create(m)
@@ -249,11 +249,12 @@ def test_batched_flexible_gmres_with_the_network(precision):
             rhs.append(r)
     torch.cuda.synchronize()
     o = fsi.solve_opts(m=30, rtol=1e-10, max_iter=4000, precision=precision, ir_inner_rtol=1e-3, ir_max=60)
+    o64 = fsi.solve_opts(m=30, rtol=1e-10, max_iter=4000)
     jac = []
     with torch.cuda.stream(stream):
         for i, m in enumerate(meshes):
             x = torch.zeros_like(rhs[i])
-            fsi.fsi_gmres(m, fsi.FSI_BLOCK_NS, *states[i], rhs[i], x, o)
+            fsi.fsi_gmres(m, fsi.FSI_BLOCK_NS, *states[i], rhs[i], x, o64)  # reference: float64 Jacobi
             jac.append(x)
         ol = fsi.fsi_solve_opts.from_buffer_copy(o)
         ol.precond = fsi.FSI_PC_LEARNED
