@@ -123,6 +123,14 @@ struct fsi_batch {
   double* Zb = nullptr;
   int64_t zb_len = 0;
   int use_pc = 0, pc_alternate = 0;
+  // the network step of every instance as one captured graph: each instance's network on one
+  // of a few side streams (parallel branches), output into zt [ntot]
+  double* zt = nullptr;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  cudaGraphExec_t net_graph = nullptr;
+  int net_warm = 0;
   // work lists of the batched float32 NS coefficient product (built on first use)
   int4* nsq_eitems = nullptr;     // (instance, x block, y block, layer)
   int nsq_ne = 0;
@@ -188,17 +196,19 @@ __global__ void bk_extract(const int4* __restrict__ items, const int* __restrict
   }
 }
 
-// z = Z_j (the network's direction as the operator input, with its float copy)
-__global__ void bk_zfill(const int4* __restrict__ items, const int* __restrict__ act, const double* __restrict__ zs,
-                         const int64_t* off, const int64_t* nloc, double* __restrict__ z, float* const* dx32) {
+// the network's direction: Z_j = z = zt (with the float copy of z)
+__global__ void bk_zfill(const int4* __restrict__ items, const int* __restrict__ act, const double* __restrict__ zt,
+                         const int64_t* off, const int64_t* nloc, double* __restrict__ z, float* const* dx32,
+                         double* __restrict__ zs) {
   const int4 it = items[blockIdx.x];
   const int b = it.x;
   if (!act[b]) return;
   for (int64_t c = it.y; c < it.z; ++c) {
     const int64_t e = c * BCH + threadIdx.x;
     if (e >= nloc[b]) break;
-    const double v = zs[off[b] + e];
+    const double v = zt[off[b] + e];
     z[off[b] + e] = v;
+    zs[off[b] + e] = v;
     if (dx32) dx32[b][e] = (float)v;
   }
 }
@@ -705,6 +715,67 @@ int run_set(fsi_batch* b, const OpSet& s, int gate) { return s.launch(b, s.ops, 
     ++(b)->launches;                               \
   } while (0)
 
+// zt = M_i(t) for every instance (|t_i| = 1): the first time directly, one instance after
+// another on the batch's stream; afterwards through a graph captured once per solve in which
+// every instance's network runs on one of the side streams (independent branches the GPU
+// runs side by side; the small grids of one instance's layers leave most SMs idle)
+int net_step(fsi_batch* b) {
+  cudaStream_t s = b->stream;
+  const int nb = b->n;
+  if (!b->net_warm || !b->use_graph || s == nullptr) {
+    for (int i = 0; i < nb; ++i) {
+      fsi_mesh* m = b->meshes[i];
+      if (int rc = pcn::apply(m->pc, b->t + b->off[i], 1.0, b->dinv + b->off[i], b->zt + b->off[i])) return rc;
+    }
+    b->net_warm = 1;
+    return FSI_OK;
+  }
+  if (!b->net_graph) {
+    if (b->side.empty()) {
+      const int S = std::min(nb, 16);
+      b->side.resize(S);
+      b->join.resize(S);
+      for (int k = 0; k < S; ++k) {
+        FSI_CUDA(cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking));
+        FSI_CUDA(cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming));
+      }
+      FSI_CUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    }
+    const int S = (int)b->side.size();
+    std::vector<char> prof(nb);
+    for (int i = 0; i < nb; ++i) prof[i] = b->meshes[i]->prof.on, b->meshes[i]->prof.on = false;
+    cudaGraph_t g = nullptr;
+    FSI_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaEventRecord(b->fork, s);
+    for (int k = 0; k < S && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->side[k], b->fork, 0);
+    int rc = FSI_OK;
+    for (int i = 0; i < nb && e == cudaSuccess && !rc; ++i) {
+      fsi_mesh* m = b->meshes[i];
+      cudaStream_t saved = m->stream;
+      m->stream = b->side[i % S];
+      rc = pcn::apply(m->pc, b->t + b->off[i], 1.0, b->dinv + b->off[i], b->zt + b->off[i]);
+      m->stream = saved;
+    }
+    for (int k = 0; k < S && e == cudaSuccess; ++k) {
+      e = cudaEventRecord(b->join[k], b->side[k]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join[k], 0);
+    }
+    const cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    for (int i = 0; i < nb; ++i) b->meshes[i]->prof.on = prof[i];
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_check(e, "batch network step: capture");
+    if (e2 != cudaSuccess) return cuda_check(e2, "batch network step: end capture");
+    e = cudaGraphInstantiate(&b->net_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_check(e, "batch network step: instantiate");
+  }
+  FSI_CUDA(cudaGraphLaunch(b->net_graph, s));
+  return FSI_OK;
+}
+
 // one Arnoldi step j of every active instance
 int enqueue_step(fsi_batch* b, int j, double rtol, bool f32) {
   const int NI = b->nitems, nb = b->n, M1 = b->M1;
@@ -714,12 +785,9 @@ int enqueue_step(fsi_batch* b, int j, double rtol, bool f32) {
     // flexible GMRES, network direction: z_j = M_i(v_j) per instance (|v_j| = 1)
     BK_LAUNCH(b, P_KRYLOV, bk_extract<<<NI, BVB, 0, s>>>(b->items_dev, b->act, b->V, b->vbase_dev, b->off_dev,
                                                          b->nloc_dev, M1, j, b->t));
-    for (int i = 0; i < nb; ++i) {
-      fsi_mesh* m = b->meshes[i];
-      if (int rc = pcn::apply(m->pc, b->t + b->off[i], 1.0, b->dinv + b->off[i], Zj + b->off[i])) return rc;
-    }
-    BK_LAUNCH(b, P_KRYLOV, bk_zfill<<<NI, BVB, 0, s>>>(b->items_dev, b->act, Zj, b->off_dev, b->nloc_dev, b->z,
-                                                       f32 ? b->dx32_dev : nullptr));
+    if (int rc = net_step(b)) return rc;
+    BK_LAUNCH(b, P_KRYLOV, bk_zfill<<<NI, BVB, 0, s>>>(b->items_dev, b->act, b->zt, b->off_dev, b->nloc_dev, b->z,
+                                                       f32 ? b->dx32_dev : nullptr, Zj));
   } else {
     BK_LAUNCH(b, P_KRYLOV, bk_precond<<<NI, BVB, 0, s>>>(b->items_dev, b->act, b->V, b->vbase_dev, b->off_dev,
                                                            b->nloc_dev, M1, j, b->dinv, b->z,
@@ -950,6 +1018,11 @@ extern "C" {
 int fsi_batch_destroy(fsi_batch* b) {
   if (!b) return FSI_OK;
   if (b->cycle) cudaGraphExecDestroy(b->cycle);
+  if (b->net_graph) cudaGraphExecDestroy(b->net_graph);
+  for (cudaStream_t st : b->side) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);
+  if (b->fork) cudaEventDestroy(b->fork);
+  cudaFree(b->zt);
   for (OpSet* s : {&b->jvp_inner, &b->jvp_d, &b->jvp_outer, &b->jvp_user}) cudaFree(s->ops);
   cudaFree(b->nsq_eitems);
   cudaFree(b->nsq_nitems);
@@ -1097,6 +1170,10 @@ int fsi_batch_gmres(fsi_batch* b, const fsi_state* states, const double* rhs, do
       FSI_CUDA(cudaMalloc(&b->Zb, sizeof(double) * (size_t)zl));
       b->zb_len = zl;
     }
+    if (!b->zt) FSI_CUDA(cudaMalloc(&b->zt, sizeof(double) * (size_t)std::max<int64_t>(b->ntot, 1)));
+    // the networks read this solve's staged states: capture their step again
+    if (b->net_graph) cudaGraphExecDestroy(b->net_graph);
+    b->net_graph = nullptr;
   }
   b->use_pc = learned ? 1 : 0;
   b->pc_alternate = (learned && (o->flags & FSI_PC_ALTERNATE)) ? 1 : 0;
