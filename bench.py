@@ -289,7 +289,82 @@ def run_batch_case(count: int = 64, reps: int = 5, steps: int = 3):
                           "launches_per_instance_arm": 2 * count, "launches_batched": 3},
            "ns_solve_fp32ir_rtol1e-8": res, "max_solution_difference": diff}
     out["time_steps"] = batch_steps(fsi, torch, dev, wls, meshes, stream, steps)
+    out["time_steps_learned"] = batch_learned_steps(fsi, torch, dev, wls, meshes, stream, steps=2)
     print(json.dumps(out), flush=True)
+
+
+def batch_learned_steps(fsi, torch, dev, wls, meshes, stream, steps=2):
+    """Batched time steps with flexible GMRES in the NS solves (network and Jacobi directions
+    alternately; each instance's network step in one captured graph of parallel branches)
+    against batched Jacobi GMRES, from the same initial states (float32 refinement, rel-res
+    1e-8).  One network is trained on the largest instance (one harvesting Jacobi step, 360
+    synthetic pairs, 4,000 Adam steps; timed apart) and its weights and output scales are
+    given to every instance, each keeping its own input scale (from one pair at its state)."""
+    import numpy as np
+    from workloads import he_normal_weights
+    opts = fsi.solve_opts(m=30, rtol=1e-8, max_iter=6000, precision=fsi.FSI_PREC_FP32_IR, ir_inner_rtol=1e-3,
+                          ir_max=30)
+    big = max(range(len(wls)), key=lambda i: wls[i].desc.nn)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        st = list(initial_state(fsi, meshes[big], wls[big], torch, dev))
+        pct = fsi.fsi_pc_create(meshes[big], n_pairs_cap=512, linear=True, modulate=True)
+        fsi.fsi_pc_set_weights(pct, he_normal_weights(pct.fan, 3))
+        fsi.fsi_set_pc(meshes[big], pct)
+        hv = fsi.solve_opts(m=30, rtol=1e-8, max_iter=6000)
+        hv.flags |= fsi.FSI_HARVEST
+        fsi.fsi_step(meshes[big], *st, k_max=5, nl_tol=5e-4, solve=hv)
+        fsi.fsi_pc_add_smooth_pairs(pct, *st, 360, seed=1)
+        fsi.fsi_pc_fit_norm(pct)
+        npairs = fsi.fsi_pc_pairs(pct)
+        losses = fsi.fsi_pc_train(pct, np.random.default_rng(0).integers(0, npairs, size=4000), 2e-4)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    w = fsi.fsi_pc_get_weights(pct)
+    _, kc = fsi.fsi_pc_get_norm(pct)
+    pcs = []
+    for i, m in enumerate(meshes):
+        if i == big:
+            pcs.append(pct)
+            continue
+        with torch.cuda.stream(stream):
+            sti = list(initial_state(fsi, m, wls[i], torch, dev))
+            pc = fsi.fsi_pc_create(m, n_pairs_cap=1, linear=True, modulate=True)
+            fsi.fsi_pc_add_smooth_pairs(pc, *sti, 1, seed=2)  # this instance's input scale
+            db, _ = fsi.fsi_pc_get_norm(pc)
+            fsi.fsi_pc_set_norm(pc, db, kc)
+            fsi.fsi_pc_set_weights(pc, w)
+            fsi.fsi_set_pc(m, pc)
+        pcs.append(pc)
+    torch.cuda.synchronize()
+    arms = {}
+    for arm in ("jacobi", "learned"):
+        with torch.cuda.stream(stream):
+            sts = [list(initial_state(fsi, m, wl, torch, dev)) for m, wl in zip(meshes, wls)]
+        torch.cuda.synchronize()
+        stepper = fsi.fsi_batch_stepper_create(meshes, m=30)
+        o = fsi.fsi_solve_opts.from_buffer_copy(opts)
+        if arm == "learned":
+            o.precond = fsi.FSI_PC_LEARNED
+            o.flags |= fsi.FSI_PC_ALTERNATE
+        its, stalled, worst = [], 0, 0.0
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for _ in range(steps):
+                infos = fsi.fsi_batch_step(stepper, sts, k_max=5, nl_tol=5e-4, solve=o)
+                its.append(int(sum(i.gmres_iters_ns for i in infos)))
+                stalled += sum(i.stalled_solves for i in infos)
+                worst = max(worst, max(i.worst_rel_res for i in infos))
+            torch.cuda.synchronize()
+        arms[arm] = {"s_per_step_all_instances": round((time.perf_counter() - t0) / steps, 4),
+                     "ns_iterations_all_instances": its, "stalled_solves": stalled, "worst_rel_res": worst}
+        del stepper
+    for m in meshes:
+        fsi.fsi_set_pc(m, None)
+    return {"trained_on": wls[big].name, "train_s": round(train_s, 2),
+            "relative_loss_first_last": [round(float(losses[:50].mean()), 4), round(float(losses[-200:].mean()), 4)],
+            "steps": steps, **arms,
+            "speedup": round(arms["jacobi"]["s_per_step_all_instances"] / arms["learned"]["s_per_step_all_instances"], 3)}
 
 
 def batch_steps(fsi, torch, dev, wls, meshes, stream, steps):
