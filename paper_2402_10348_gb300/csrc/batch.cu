@@ -160,12 +160,35 @@ __device__ __forceinline__ void bsum_store(double (&acc)[K], int k, double* out)
   }
 }
 
-__device__ __forceinline__ double* bslot(double* V, const int64_t* vbase, int b, int M1, int64_t c, int i) {
+template <typename T, int K>
+__device__ __forceinline__ void bsum_store_t(T (&acc)[K], int k, double* out) {
+  __shared__ T smt[K][BVB / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    T v = acc[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) smt[i][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < k) {
+    T s = T(0);
+    for (int wi = 0; wi < BVB / 32; ++wi) s += smt[threadIdx.x][wi];
+    out[threadIdx.x] = (double)s;
+  }
+}
+
+// basis slot i of chunk c of instance b; the basis type VT is double for float64 solves and
+// float for the inner solves of float32 refinement (the same allocation, element offsets)
+template <typename VT>
+__device__ __forceinline__ VT* bslot(VT* V, const int64_t* vbase, int b, int M1, int64_t c, int i) {
   return V + vbase[b] + c * (int64_t)M1 * BCH + (int64_t)i * BCH;
 }
 
 // z_b = dinv_b * V_b[j] (and the float copy for float32 operators)
-__global__ void bk_precond(const int4* __restrict__ items, const int* __restrict__ act, double* V,
+template <typename VT>
+__global__ void bk_precond(const int4* __restrict__ items, const int* __restrict__ act, VT* V,
                            const int64_t* vbase, const int64_t* off, const int64_t* nloc, int M1, int j,
                            const double* __restrict__ dinv, double* __restrict__ z, float* const* dx32,
                            double* __restrict__ zs) {
@@ -175,7 +198,7 @@ __global__ void bk_precond(const int4* __restrict__ items, const int* __restrict
   for (int64_t c = it.y; c < it.z; ++c) {
     const int64_t e = c * BCH + threadIdx.x;
     if (e >= nloc[b]) break;
-    const double v = dinv[off[b] + e] * bslot(V, vbase, b, M1, c, j)[threadIdx.x];
+    const double v = dinv[off[b] + e] * (double)bslot(V, vbase, b, M1, c, j)[threadIdx.x];
     z[off[b] + e] = v;
     if (dx32) dx32[b][e] = (float)v;
     if (zs) zs[off[b] + e] = v;  // flexible GMRES keeps the direction
@@ -183,7 +206,8 @@ __global__ void bk_precond(const int4* __restrict__ items, const int* __restrict
 }
 
 // t = V_j (concatenated float64 copy of basis slot j of the active instances)
-__global__ void bk_extract(const int4* __restrict__ items, const int* __restrict__ act, double* V,
+template <typename VT>
+__global__ void bk_extract(const int4* __restrict__ items, const int* __restrict__ act, VT* V,
                            const int64_t* vbase, const int64_t* off, const int64_t* nloc, int M1, int j,
                            double* __restrict__ t) {
   const int4 it = items[blockIdx.x];
@@ -192,7 +216,7 @@ __global__ void bk_extract(const int4* __restrict__ items, const int* __restrict
   for (int64_t c = it.y; c < it.z; ++c) {
     const int64_t e = c * BCH + threadIdx.x;
     if (e >= nloc[b]) break;
-    t[off[b] + e] = bslot(V, vbase, b, M1, c, j)[threadIdx.x];
+    t[off[b] + e] = (double)bslot(V, vbase, b, M1, c, j)[threadIdx.x];
   }
 }
 
@@ -247,9 +271,9 @@ __global__ void bk_tofloat(const int4* __restrict__ items, const int* __restrict
 }
 
 // partials of V_b[i0 .. i0+kc) . w_b and (self) w_b . w_b; second pass only where reorth
-template <bool SELF>
+template <bool SELF, typename VT>
 __global__ void bk_mdot(const int4* __restrict__ items, const BKry* __restrict__ K, const int* __restrict__ act,
-                        const double* V,
+                        const VT* V,
                         const int64_t* vbase, const int64_t* off, const int64_t* nloc, int M1, int nvec,
                         const double* __restrict__ w, double* part, int second) {
   const int4 it = items[blockIdx.x];
@@ -258,14 +282,14 @@ __global__ void bk_mdot(const int4* __restrict__ items, const BKry* __restrict__
   const int i0 = blockIdx.y * BKC;
   const int kc = min(BKC, nvec - i0);
   if (kc <= 0 && !(SELF && blockIdx.y == 0)) return;
-  double acc[BKC + 1];
+  VT acc[BKC + 1];  // per-thread sums in the basis type, the CTA's sums stored as double
 #pragma unroll
-  for (int i = 0; i <= BKC; ++i) acc[i] = 0.0;
+  for (int i = 0; i <= BKC; ++i) acc[i] = VT(0);
   for (int64_t c = it.y; c < it.z; ++c) {
     const int64_t e = c * BCH + threadIdx.x;
     if (e >= nloc[b]) break;
-    const double wj = w[off[b] + e];
-    const double* blk = V + vbase[b] + c * (int64_t)M1 * BCH + (int64_t)i0 * BCH + threadIdx.x;
+    const VT wj = (VT)w[off[b] + e];
+    const VT* blk = V + vbase[b] + c * (int64_t)M1 * BCH + (int64_t)i0 * BCH + threadIdx.x;
 #pragma unroll
     for (int i = 0; i < BKC; ++i)
       if (i < kc) acc[i] += blk[i * BCH] * wj;
@@ -273,7 +297,7 @@ __global__ void bk_mdot(const int4* __restrict__ items, const BKry* __restrict__
   }
   double* out = part + (int64_t)blockIdx.x * PSTRIDE;
   __shared__ double res[BKC + 1];
-  bsum_store<BKC + 1>(acc, BKC + 1, res);
+  bsum_store_t<VT, BKC + 1>(acc, BKC + 1, res);
   __syncthreads();
   if ((int)threadIdx.x < kc) out[i0 + threadIdx.x] = res[threadIdx.x];
   if (SELF && blockIdx.y == 0 && threadIdx.x == 0) out[PSTRIDE - 1] = res[BKC];
@@ -296,30 +320,31 @@ __global__ void bk_reduce(const int* __restrict__ first, const double* __restric
 }
 
 // w_b -= sum_i h_i V_b[i] and the partial |w_b|^2 (slot 0)
+template <typename VT>
 __global__ void bk_update(const int4* __restrict__ items, const BKry* __restrict__ K, const int* __restrict__ act,
-                          const double* V,
+                          const VT* V,
                           const int64_t* vbase, const int64_t* off, const int64_t* nloc, int M1, int nvec,
                           double* __restrict__ w, double* part, int which, int second) {
   const int4 it = items[blockIdx.x];
   const int b = it.x;
   if (!act[b] || (second && !K[b].reorth)) return;
-  __shared__ double hs[BMMAX + 1];
+  __shared__ VT hs[BMMAX + 1];
   const double* h = which == 0 ? K[b].h : K[b].h2;
-  for (int i = threadIdx.x; i < nvec; i += blockDim.x) hs[i] = h[i];
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) hs[i] = (VT)h[i];
   __syncthreads();
-  double acc[1] = {0.0};
+  VT acc[1] = {VT(0)};
   for (int64_t c = it.y; c < it.z; ++c) {
     const int64_t e = c * BCH + threadIdx.x;
     if (e >= nloc[b]) break;
-    const double* blk = V + vbase[b] + c * (int64_t)M1 * BCH + threadIdx.x;
-    double s = 0.0;
+    const VT* blk = V + vbase[b] + c * (int64_t)M1 * BCH + threadIdx.x;
+    VT s = VT(0);
     for (int i = 0; i < nvec; ++i) s += hs[i] * blk[(int64_t)i * BCH];
-    const double v = w[off[b] + e] - s;
-    w[off[b] + e] = v;
+    const VT v = (VT)w[off[b] + e] - s;
+    w[off[b] + e] = (double)v;
     acc[0] += v * v;
   }
   __shared__ double res[1];
-  bsum_store<1>(acc, 1, res);
+  bsum_store_t<VT, 1>(acc, 1, res);
   __syncthreads();
   if (threadIdx.x == 0) part[(int64_t)blockIdx.x * PSTRIDE] = res[0];
 }
@@ -375,8 +400,9 @@ __global__ void bk_givens(BKry* K, int* act, int nb, int j, int mm, double rtol)
 }
 
 // V_b[j+1] = w_b / |w_b|
+template <typename VT>
 __global__ void bk_store(const int4* __restrict__ items, const BKry* __restrict__ K, const int* __restrict__ act,
-                         double* V, const int64_t* vbase,
+                         VT* V, const int64_t* vbase,
                          const int64_t* off, const int64_t* nloc, int M1, int slot, const double* __restrict__ src,
                          int from_rn2) {
   const int4 it = items[blockIdx.x];
@@ -387,7 +413,7 @@ __global__ void bk_store(const int4* __restrict__ items, const BKry* __restrict_
   for (int64_t c = it.y; c < it.z; ++c) {
     const int64_t e = c * BCH + threadIdx.x;
     if (e >= nloc[b]) break;
-    bslot(V, vbase, b, M1, c, slot)[threadIdx.x] = s * src[off[b] + e];
+    bslot(V, vbase, b, M1, c, slot)[threadIdx.x] = (VT)(s * src[off[b] + e]);
   }
 }
 
@@ -416,8 +442,9 @@ __global__ void bk_lsq(BKry* K, int nb, const int* live, int mm) {
 }
 
 // x_b += dinv_b * sum_{i < jend_b} y_i V_b[i]
+template <typename VT>
 __global__ void bk_combine(const int4* __restrict__ items, const BKry* __restrict__ K, const int* live,
-                           const double* V, const int64_t* vbase, const int64_t* off, const int64_t* nloc, int M1,
+                           const VT* V, const int64_t* vbase, const int64_t* off, const int64_t* nloc, int M1,
                            const double* __restrict__ dinv, double* __restrict__ x) {
   const int4 it = items[blockIdx.x];
   const int b = it.x;
@@ -429,9 +456,9 @@ __global__ void bk_combine(const int4* __restrict__ items, const BKry* __restric
   for (int64_t c = it.y; c < it.z; ++c) {
     const int64_t e = c * BCH + threadIdx.x;
     if (e >= nloc[b]) break;
-    const double* blk = V + vbase[b] + c * (int64_t)M1 * BCH + threadIdx.x;
+    const VT* blk = V + vbase[b] + c * (int64_t)M1 * BCH + threadIdx.x;
     double s = 0.0;
-    for (int i = 0; i < jend; ++i) s += ys[i] * blk[(int64_t)i * BCH];
+    for (int i = 0; i < jend; ++i) s += ys[i] * (double)blk[(int64_t)i * BCH];
     x[off[b] + e] += dinv[off[b] + e] * s;
   }
 }
@@ -776,20 +803,22 @@ int net_step(fsi_batch* b) {
   return FSI_OK;
 }
 
-// one Arnoldi step j of every active instance
-int enqueue_step(fsi_batch* b, int j, double rtol, bool f32) {
+// one Arnoldi step j of every active instance (basis type VT)
+template <typename VT>
+int enqueue_step_t(fsi_batch* b, int j, double rtol, bool f32) {
+  VT* V = reinterpret_cast<VT*>(b->V);
   const int NI = b->nitems, nb = b->n, M1 = b->M1;
   cudaStream_t s = b->stream;
   double* Zj = b->use_pc ? b->Zb + (int64_t)j * b->ntot : nullptr;
   if (b->use_pc && !(b->pc_alternate && (j & 1))) {
     // flexible GMRES, network direction: z_j = M_i(v_j) per instance (|v_j| = 1)
-    BK_LAUNCH(b, P_KRYLOV, bk_extract<<<NI, BVB, 0, s>>>(b->items_dev, b->act, b->V, b->vbase_dev, b->off_dev,
+    BK_LAUNCH(b, P_KRYLOV, bk_extract<VT><<<NI, BVB, 0, s>>>(b->items_dev, b->act, V, b->vbase_dev, b->off_dev,
                                                          b->nloc_dev, M1, j, b->t));
     if (int rc = net_step(b)) return rc;
     BK_LAUNCH(b, P_KRYLOV, bk_zfill<<<NI, BVB, 0, s>>>(b->items_dev, b->act, b->zt, b->off_dev, b->nloc_dev, b->z,
                                                        f32 ? b->dx32_dev : nullptr, Zj));
   } else {
-    BK_LAUNCH(b, P_KRYLOV, bk_precond<<<NI, BVB, 0, s>>>(b->items_dev, b->act, b->V, b->vbase_dev, b->off_dev,
+    BK_LAUNCH(b, P_KRYLOV, bk_precond<VT><<<NI, BVB, 0, s>>>(b->items_dev, b->act, V, b->vbase_dev, b->off_dev,
                                                            b->nloc_dev, M1, j, b->dinv, b->z,
                                                            f32 ? b->dx32_dev : nullptr, Zj));
   }
@@ -799,34 +828,44 @@ int enqueue_step(fsi_batch* b, int j, double rtol, bool f32) {
   const dim3 g2(NI, (nvec + BKC - 1) / BKC);
   for (int pass = 0; pass < 2; ++pass) {
     if (pass == 0)
-      BK_LAUNCH(b, P_KRY_DOT, bk_mdot<true><<<g2, BVB, 0, s>>>(b->items_dev, b->K, b->act, b->V, b->vbase_dev,
+      BK_LAUNCH(b, P_KRY_DOT, bk_mdot<true, VT><<<g2, BVB, 0, s>>>(b->items_dev, b->K, b->act, V, b->vbase_dev,
                                                                b->off_dev, b->nloc_dev, M1, nvec, b->w, b->part, 0));
     else
-      BK_LAUNCH(b, P_KRY_DOT, bk_mdot<false><<<g2, BVB, 0, s>>>(b->items_dev, b->K, b->act, b->V, b->vbase_dev,
+      BK_LAUNCH(b, P_KRY_DOT, bk_mdot<false, VT><<<g2, BVB, 0, s>>>(b->items_dev, b->K, b->act, V, b->vbase_dev,
                                                                 b->off_dev, b->nloc_dev, M1, nvec, b->w, b->part, 1));
     BK_LAUNCH(b, P_KRY_DOT, bk_reduce<<<nb, 128, 0, s>>>(b->item_first_dev, b->part, b->K, b->act, nvec,
                                                           pass == 0 ? 1 : 0, pass, pass));
-    BK_LAUNCH(b, P_KRY_UPD, bk_update<<<NI, BVB, 0, s>>>(b->items_dev, b->K, b->act, b->V, b->vbase_dev, b->off_dev,
+    BK_LAUNCH(b, P_KRY_UPD, bk_update<VT><<<NI, BVB, 0, s>>>(b->items_dev, b->K, b->act, V, b->vbase_dev, b->off_dev,
                                                           b->nloc_dev, M1, nvec, b->w, b->part, pass, pass));
     BK_LAUNCH(b, P_KRY_UPD, bk_norm_reduce<<<gx1(nb), 128, 0, s>>>(b->item_first_dev, b->part, b->K, b->act, nb,
                                                                     pass));
     if (pass == 0) BK_LAUNCH(b, P_KRY_SMALL, bk_orth_decide<<<gx1(nb), 128, 0, s>>>(b->K, b->act, nb, j));
   }
   BK_LAUNCH(b, P_KRY_SMALL, bk_givens<<<gx1(nb), 128, 0, s>>>(b->K, b->act, nb, j, b->mm, rtol));
-  BK_LAUNCH(b, P_KRYLOV, bk_store<<<NI, BVB, 0, s>>>(b->items_dev, b->K, b->act, b->V, b->vbase_dev, b->off_dev,
+  BK_LAUNCH(b, P_KRYLOV, bk_store<VT><<<NI, BVB, 0, s>>>(b->items_dev, b->K, b->act, V, b->vbase_dev, b->off_dev,
                                                       b->nloc_dev, M1, j + 1, b->w, 0));
   return FSI_OK;
 }
 
-// one restart cycle of the inner solve: rhs b->rin, solution b->d, residual b->r
+// one restart cycle of the inner solve: rhs b->rin, solution b->d, residual b->r; the
+// float32 refinement's inner solves keep a float32 basis
+template <typename VT>
+int enqueue_cycle_t(fsi_batch* b, double rtol, bool f32);
 int enqueue_cycle(fsi_batch* b, double rtol, bool f32) {
+  if (f32) return enqueue_cycle_t<float>(b, rtol, f32);
+  return enqueue_cycle_t<double>(b, rtol, f32);
+}
+
+template <typename VT>
+int enqueue_cycle_t(fsi_batch* b, double rtol, bool f32) {
+  VT* V = reinterpret_cast<VT*>(b->V);
   const int NI = b->nitems, nb = b->n, M1 = b->M1;
   cudaStream_t s = b->stream;
   BK_LAUNCH(b, P_KRY_SMALL, bk_cycle_start<<<gx1(nb), 128, 0, s>>>(b->K, b->act, nb, b->live, b->mm));
-  BK_LAUNCH(b, P_KRYLOV, bk_store<<<NI, BVB, 0, s>>>(b->items_dev, b->K, b->act, b->V, b->vbase_dev, b->off_dev,
+  BK_LAUNCH(b, P_KRYLOV, bk_store<VT><<<NI, BVB, 0, s>>>(b->items_dev, b->K, b->act, V, b->vbase_dev, b->off_dev,
                                                       b->nloc_dev, M1, 0, b->r, 1));
   for (int j = 0; j < b->mm; ++j) {
-    int rc = enqueue_step(b, j, rtol, f32);
+    int rc = enqueue_step_t<VT>(b, j, rtol, f32);
     if (rc) return rc;
   }
   BK_LAUNCH(b, P_KRY_SMALL, bk_lsq<<<gx1(nb), 128, 0, s>>>(b->K, nb, b->live, b->mm));
@@ -834,7 +873,7 @@ int enqueue_cycle(fsi_batch* b, double rtol, bool f32) {
     BK_LAUNCH(b, P_KRYLOV, bk_zcombine<<<NI, BVB, 0, s>>>(b->items_dev, b->K, b->live, b->Zb, b->ntot, b->off_dev,
                                                            b->nloc_dev, b->d));
   else
-    BK_LAUNCH(b, P_KRYLOV, bk_combine<<<NI, BVB, 0, s>>>(b->items_dev, b->K, b->live, b->V, b->vbase_dev, b->off_dev,
+    BK_LAUNCH(b, P_KRYLOV, bk_combine<VT><<<NI, BVB, 0, s>>>(b->items_dev, b->K, b->live, V, b->vbase_dev, b->off_dev,
                                                           b->nloc_dev, M1, b->dinv, b->d));
   // true residual of the inner system: r = rin - A d (live instances)
   if (f32)
