@@ -1147,7 +1147,25 @@ def run_learned_arm(fsi, torch, mesh, pc, solve, step, state, snapshot, args, st
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    # the same network inside float32 refinement: flexible inner solves (alternate directions)
+    o32 = fsi.fsi_solve_opts.from_buffer_copy(opts)
+    o32.precision = fsi.FSI_PREC_FP32_IR
+    o32.ir_inner_rtol = args.ir_inner_rtol
+    o32.ir_max = 30
+    restore()
+    step(o32)  # first use of the float32 staging with the network
+    restore()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    infos32 = [step(o32) for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms32 = e0.elapsed_time(e1)
+    fp32ir = {"s_per_timestep": round(ms32 / args.steps / 1e3, 5), "ns_iters": [i.gmres_iters_ns for i in infos32],
+              "worst_rel_res": max(i.worst_rel_res for i in infos32),
+              "fallback_solves": [i.fallback_solves for i in infos32]}
     return {
+        "float32_refinement": fp32ir,
         "network": "U-Net, 4 levels, 16 channels, 3x3x3 convolutions (tcgen05, bf16 x bf16 -> f32), "
                    "linear (no activation), inputs modulated by the solid indicator",
         "directions": "flexible GMRES, network and Jacobi directions alternately",
