@@ -146,3 +146,25 @@ def test_jvp_matches_finite_differences(block):
     xm[comps] -= h * dx
     fd = (R(xp) - R(xm)) / (2 * h)
     assert np.linalg.norm(J - fd) <= 1e-7 * np.linalg.norm(J)
+
+
+def test_box_mesh_generator_orientation_and_reproducibility():
+    """workloads.tet_box_mesh (the seeded input shared by the oracle and the GPU side): every
+    element positively oriented, six per cell, the same mesh for the same seed, a different
+    jitter for another seed, boundary nodes never moved."""
+    from workloads import tet_box_mesh
+    d = _desc(n=(3, 2, 4))
+    X1, c1 = tet_box_mesh(d, 0.3, seed=5)
+    X2, c2 = tet_box_mesh(d, 0.3, seed=5)
+    X3, _ = tet_box_mesh(d, 0.3, seed=6)
+    assert c1.shape == (6 * d.nx * d.ny * d.nz, 4)
+    assert np.array_equal(X1, X2) and np.array_equal(c1, c2)
+    assert not np.array_equal(X1, X3)
+    e1, e2, e3 = (X1[:, c1[:, a]] - X1[:, c1[:, 0]] for a in (1, 2, 3))
+    det = np.einsum("ie,ie->e", e1, np.cross(e2.T, e3.T).T)
+    assert (det > 0).all()
+    X0, _ = tet_box_mesh(d, 0.0)
+    n = np.arange(d.nn)
+    i, j, k = n % (d.nx + 1), (n // (d.nx + 1)) % (d.ny + 1), n // ((d.nx + 1) * (d.ny + 1))
+    bnd = (i == 0) | (i == d.nx) | (j == 0) | (j == d.ny) | (k == 0) | (k == d.nz)
+    assert np.array_equal(X1[:, bnd], X0[:, bnd])
