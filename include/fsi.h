@@ -184,7 +184,10 @@ int fsi_set_pressure_pin(fsi_mesh* mesh, int32_t active);
 #define FSI_HARVEST 0x10u
 /* solve flag with FSI_PC_LEARNED: flexible GMRES takes the network's direction at even
  * Arnoldi steps and the Jacobi direction D^{-1} v_j at odd ones, so that its
- * least-squares step weights the two kinds separately */
+ * least-squares step weights the two kinds separately.  The recommended mode: a linear
+ * network trained on smooth error pairs corrects the low-frequency part of the residual
+ * and leaves the high-frequency part to the Jacobi directions (with the network at every
+ * step a solve can stall and fall back to Jacobi) */
 #define FSI_PC_ALTERNATE 0x20u
 /* solve flag: never stop on stagnation.  Without it a solve stops ("stalled") when a
  * whole restart cycle reduces the true residual by less than 1 % (FP32_IR: when a
