@@ -759,7 +759,7 @@ int net_step(fsi_batch* b) {
   }
   if (!b->net_graph) {
     if (b->side.empty()) {
-      const int S = std::min(nb, 16);
+      const int S = std::min(nb, 32);
       b->side.resize(S);
       b->join.resize(S);
       for (int k = 0; k < S; ++k) {
