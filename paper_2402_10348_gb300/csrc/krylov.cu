@@ -90,6 +90,54 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[K], int kc, dou
   }
 }
 
+// The same for many float64 values with fewer float64 adds (this GPU issues them at a
+// small fraction of the float32 rate; a plain shuffle tree costs 5 adds a lane per value).
+// Inside a warp a transposing butterfly takes the first P values (P the largest power of
+// two <= K, at most 32): at shuffle distance 16 a lane keeps half of its values and adds
+// its partner's copy of that half, at distance 8 half of that half, and so on; after
+// log2 P levels the lane holds value number lane >> (5 - log2 P) summed over the lanes
+// that differ from it in the top log2 P bits, and plain shuffles over the remaining bits
+// finish the warp's sum (P - 1 + 5 - log2 P adds a lane).  Values past P take plain trees.
+template <int K>
+__device__ __forceinline__ void block_reduce_store_bf(double (&acc)[K], int kc, double* out, int stride) {
+  constexpr int P = K >= 32 ? 32 : K >= 16 ? 16 : K >= 8 ? 8 : K >= 4 ? 4 : K >= 2 ? 2 : 1;
+  constexpr int L = P == 32 ? 5 : P == 16 ? 4 : P == 8 ? 3 : P == 4 ? 2 : P == 2 ? 1 : 0;
+  __shared__ double smb[K][VB / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double a[P];
+#pragma unroll
+  for (int q = 0; q < P; ++q) a[q] = acc[q];
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
+    const int o = 16 >> l;
+    const int half = P >> (l + 1);
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int q = 0; q < half; ++q) {
+      const double send = up ? a[q] : a[q + half];  // the half the partner keeps
+      const double keep = up ? a[q + half] : a[q];
+      a[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  double s = a[0];
+#pragma unroll
+  for (int o = 16 >> L; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((lane & ((32 >> L) - 1)) == 0) smb[lane >> (5 - L)][warp] = s;
+#pragma unroll
+  for (int i = P; i < K; ++i) {
+    double v = acc[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) smb[i][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kc) {
+    double t = 0.0;
+    for (int wi = 0; wi < VB / 32; ++wi) t += smb[threadIdx.x][wi];
+    out[threadIdx.x * stride] = t;
+  }
+}
+
 // The same in float32 up to the CTA's sums, which are stored as float64: this GPU
 // issues float64 adds at 1/64 of the float32 rate, so a float64 tree over every
 // thread's sums costs more than the float32 basis kernel's streaming.
@@ -149,7 +197,7 @@ __global__ void __launch_bounds__(VB) mdot_kernel(const VT* __restrict__ V, int 
   double accd[NR];
 #pragma unroll
   for (int i = 0; i < NR; ++i) accd[i] = (double)acc[i];
-  block_reduce_store<NR>(accd, NA, part + (int64_t)ib * G + blockIdx.x, G);
+  block_reduce_store_bf<NR>(accd, NA, part + (int64_t)ib * G + blockIdx.x, G);
 }
 
 // The float32 basis: the same projections with 16-byte loads.  A CTA works on four
@@ -233,14 +281,18 @@ __device__ __forceinline__ VT lin_comb_chunk(const VT* __restrict__ hs, const VT
   return ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
 }
 
-// w -= sum_{i<k} h_i V_i ; part[cta] = partial of |w|^2   (w contiguous)
+// w -= sum_{i<k} h_i V_i ; part[cta] = partial of |w|^2   (w contiguous).  One fused
+// multiply-add per basis element, chained on the element's value of w (no partial sums
+// to add up afterwards: float64 adds are scarce on this GPU); the element's values of up
+// to UPB basis vectors are loaded ahead of the chain.
+constexpr int UPB = 32;
 template <typename VT>
-__global__ void __launch_bounds__(VB) upd_kernel(double* __restrict__ w, const VT* __restrict__ V, int M1, int k,
-                                                 const double* __restrict__ h, int64_t n, double* part,
-                                                 const int* skip) {
+__global__ void __launch_bounds__(VB, 2) upd_kernel(double* __restrict__ w, const VT* __restrict__ V, int M1, int k,
+                                                    const double* __restrict__ h, int64_t n, double* part,
+                                                    const int* skip) {
   if (skip && !*skip) return;
-  __shared__ VT hs[MMAX + 2];
-  for (int i = threadIdx.x; i < k; i += VB) hs[i] = (VT)h[i];
+  __shared__ VT nh[MMAX + 2];
+  for (int i = threadIdx.x; i < k; i += VB) nh[i] = -(VT)h[i];
   __syncthreads();
   const int G = gridDim.x;
   const int64_t nch = (n + CH - 1) / CH;
@@ -250,9 +302,21 @@ __global__ void __launch_bounds__(VB) upd_kernel(double* __restrict__ w, const V
   for (int64_t c = c0; c < c1; ++c) {
     const int64_t j = c * CH + threadIdx.x;
     if (j >= n) break;
-    const VT s = (VT)w[j] - lin_comb_chunk<VT>(hs, V + c * (int64_t)M1 * CH + threadIdx.x, k);
+    const VT* blk = V + c * (int64_t)M1 * CH + threadIdx.x;
+    VT s = (VT)w[j];
+    for (int i0 = 0; i0 < k; i0 += UPB) {
+      const int cnt = min(UPB, k - i0);
+      VT v[UPB];
+#pragma unroll
+      for (int u = 0; u < UPB; ++u) v[u] = u < cnt ? blk[(int64_t)(i0 + u) * CH] : VT(0);
+#pragma unroll
+      for (int u = 0; u < UPB; ++u) {
+        if (u >= cnt) break;
+        s = fma(nh[i0 + u], v[u], s);
+      }
+    }
     w[j] = (double)s;
-    nrm += s * s;
+    nrm = fma(s, s, nrm);
   }
   double nd[1] = {(double)nrm};
   block_reduce_store<1>(nd, 1, part + blockIdx.x, 1);
@@ -327,9 +391,9 @@ __global__ void __launch_bounds__(UDB) upd_dot_kernel(double* __restrict__ w, co
                                                       int k, const double* __restrict__ h, int64_t n, double* part) {
   extern __shared__ __align__(16) unsigned char upd_smem[];
   VT* sacc = reinterpret_cast<VT*>(upd_smem);  // [KMAX + 1][UDB]
-  __shared__ VT hs[KMAX];
+  __shared__ VT nhs[KMAX];
   const int t = threadIdx.x;
-  for (int i = t; i < KMAX; i += UDB) hs[i] = i < k ? (VT)h[i] : VT(0);
+  for (int i = t; i < KMAX; i += UDB) nhs[i] = i < k ? -(VT)h[i] : VT(0);
   for (int i = 0; i <= KMAX; ++i) sacc[i * UDB + t] = VT(0);
   __syncthreads();
   const int G = gridDim.x;
@@ -346,28 +410,33 @@ __global__ void __launch_bounds__(UDB) upd_dot_kernel(double* __restrict__ w, co
       VT v[KMAX];
 #pragma unroll
       for (int i = 0; i < KMAX; ++i) v[i] = i < k ? blk[i * CH] : VT(0);
-      VT s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+      // one fused multiply-add per basis value, chained on w's value, and none for the
+      // padding past k (float64 operations are what this kernel is bound by)
+      VT ww = (VT)w[j];
 #pragma unroll
-      for (int i = 0; i < KMAX; i += 4) {
-        s0 += hs[i] * v[i];
-        s1 += hs[i + 1] * v[i + 1];
-        s2 += hs[i + 2] * v[i + 2];
-        s3 += hs[i + 3] * v[i + 3];
+      for (int i = 0; i < KMAX; ++i) {
+        if (i >= k) break;
+        ww = fma(nhs[i], v[i], ww);
       }
-      const VT ww = (VT)w[j] - ((s0 + s1) + (s2 + s3));
       w[j] = (double)ww;
-      nrm += ww * ww;
+      nrm = fma(ww, ww, nrm);
 #pragma unroll
-      for (int i = 0; i < KMAX; ++i) sacc[i * UDB + t] += v[i] * ww;
+      for (int i = 0; i < KMAX; ++i) {
+        if (i >= k) break;
+        sacc[i * UDB + t] = fma(v[i], ww, sacc[i * UDB + t]);
+      }
     }
   }
   sacc[KMAX * UDB + t] = nrm;
   __syncthreads();
-  for (int i = t; i <= k; i += UDB) {
-    const int row = i < k ? i : KMAX;
-    double s = 0.0;
-    for (int q = 0; q < UDB; ++q) s += (double)sacc[row * UDB + q];
-    part[(int64_t)i * G + blockIdx.x] = s;
+  // one warp per row, lanes on consecutive columns, then a shuffle tree
+  const int lane = t & 31;
+  for (int i = t >> 5; i <= k; i += UDB / 32) {
+    const VT* rp = sacc + (i < k ? i : KMAX) * UDB;
+    double s = ((double)rp[lane] + (double)rp[lane + 32]) + ((double)rp[lane + 64] + (double)rp[lane + 96]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) part[(int64_t)i * G + blockIdx.x] = s;
   }
 }
 
@@ -406,6 +475,7 @@ __global__ void __launch_bounds__(UDB) upd_dot2_kernel(double* __restrict__ w, c
     float sx0 = 0.f, sx1 = 0.f, sy0 = 0.f, sy1 = 0.f;
 #pragma unroll
     for (int i = 0; i < KMAX; i += 2) {
+      if (i >= k) break;  // no work for the padding past k (hs[k] is 0 when k is odd)
       sx0 += hs[i] * v[i].x;
       sx1 += hs[i + 1] * v[i + 1].x;
       sy0 += hs[i] * v[i].y;
@@ -424,7 +494,10 @@ __global__ void __launch_bounds__(UDB) upd_dot2_kernel(double* __restrict__ w, c
     }
     nrm += wx * wx + wy * wy;
 #pragma unroll
-    for (int i = 0; i < KMAX; ++i) sacc[i * UDB + t] += v[i].x * wx + v[i].y * wy;
+    for (int i = 0; i < KMAX; ++i) {
+      if (i >= k) break;
+      sacc[i * UDB + t] += v[i].x * wx + v[i].y * wy;
+    }
   }
   sacc[KMAX * UDB + t] = nrm;
   __syncthreads();
