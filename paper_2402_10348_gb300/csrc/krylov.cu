@@ -475,7 +475,6 @@ __global__ void __launch_bounds__(UDB) upd_dot2_kernel(double* __restrict__ w, c
     float sx0 = 0.f, sx1 = 0.f, sy0 = 0.f, sy1 = 0.f;
 #pragma unroll
     for (int i = 0; i < KMAX; i += 2) {
-      if (i >= k) break;  // no work for the padding past k (hs[k] is 0 when k is odd)
       sx0 += hs[i] * v[i].x;
       sx1 += hs[i + 1] * v[i + 1].x;
       sy0 += hs[i] * v[i].y;
@@ -494,10 +493,7 @@ __global__ void __launch_bounds__(UDB) upd_dot2_kernel(double* __restrict__ w, c
     }
     nrm += wx * wx + wy * wy;
 #pragma unroll
-    for (int i = 0; i < KMAX; ++i) {
-      if (i >= k) break;
-      sacc[i * UDB + t] += v[i].x * wx + v[i].y * wy;
-    }
+    for (int i = 0; i < KMAX; ++i) sacc[i * UDB + t] += v[i].x * wx + v[i].y * wy;
   }
   sacc[KMAX * UDB + t] = nrm;
   __syncthreads();
