@@ -759,14 +759,27 @@ int net_step(fsi_batch* b) {
   }
   if (!b->net_graph) {
     if (b->side.empty()) {
+      // all side streams and events or none: a failure part-way releases what was made
       const int S = std::min(nb, 32);
-      b->side.resize(S);
-      b->join.resize(S);
-      for (int k = 0; k < S; ++k) {
-        FSI_CUDA(cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking));
-        FSI_CUDA(cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming));
+      std::vector<cudaStream_t> side(S, nullptr);
+      std::vector<cudaEvent_t> join(S, nullptr);
+      cudaEvent_t fork = nullptr;
+      cudaError_t ce = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+      for (int k = 0; k < S && ce == cudaSuccess; ++k) {
+        ce = cudaStreamCreateWithFlags(&side[k], cudaStreamNonBlocking);
+        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming);
       }
-      FSI_CUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+      if (ce != cudaSuccess) {
+        for (cudaStream_t x : side)
+          if (x) cudaStreamDestroy(x);
+        for (cudaEvent_t x : join)
+          if (x) cudaEventDestroy(x);
+        if (fork) cudaEventDestroy(fork);
+        return cuda_check(ce, "batch network step: side streams");
+      }
+      b->side = std::move(side);
+      b->join = std::move(join);
+      b->fork = fork;
     }
     const int S = (int)b->side.size();
     std::vector<char> prof(nb);
@@ -789,12 +802,12 @@ int net_step(fsi_batch* b) {
     }
     const cudaError_t e2 = cudaStreamEndCapture(s, &g);
     for (int i = 0; i < nb; ++i) b->meshes[i]->prof.on = prof[i];
-    if (rc) {
+    if (rc || e != cudaSuccess || e2 != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
-      return rc;
+      if (rc) return rc;
+      if (e != cudaSuccess) return cuda_check(e, "batch network step: capture");
+      return cuda_check(e2, "batch network step: end capture");
     }
-    if (e != cudaSuccess) return cuda_check(e, "batch network step: capture");
-    if (e2 != cudaSuccess) return cuda_check(e2, "batch network step: end capture");
     e = cudaGraphInstantiate(&b->net_graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_check(e, "batch network step: instantiate");
@@ -1352,9 +1365,17 @@ int fsi_batch_autotune(fsi_batch* b, const fsi_state* states, uint32_t flags, in
   if (f32)
     BK_LAUNCH(b, P_KRY_CONV, bk_tofloat<<<b->nitems, BVB, 0, s>>>(b->items_dev, nullptr, b->off_dev, b->nloc_dev,
                                                                   b->z, b->dx32_dev, 0));
-  cudaEvent_t e0, e1;
-  FSI_CUDA(cudaEventCreate(&e0));
-  FSI_CUDA(cudaEventCreate(&e1));
+  // the two timing events, destroyed on every return
+  struct Events {
+    cudaEvent_t e[2] = {nullptr, nullptr};
+    ~Events() {
+      for (cudaEvent_t x : e)
+        if (x) cudaEventDestroy(x);
+    }
+  } ev;
+  FSI_CUDA(cudaEventCreate(&ev.e[0]));
+  FSI_CUDA(cudaEventCreate(&ev.e[1]));
+  cudaEvent_t e0 = ev.e[0], e1 = ev.e[1];
   double best = 1e300;
   int btm = b->target_mult, bgm = b->grid_mult;
   for (int tm : {1, 2, 4, 8})
@@ -1372,8 +1393,6 @@ int fsi_batch_autotune(fsi_batch* b, const fsi_state* states, uint32_t flags, in
       const double us = 1e3 * ms / 5.0;
       if (us < best) best = us, btm = tm, bgm = gm;
     }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   if ((rc = build_tiles(b, btm, bgm))) return rc;
   cache_store(tune_key(b, flags), btm, bgm, best);
   if (target_mult) *target_mult = btm;

@@ -1468,11 +1468,24 @@ int fsi_pc_add_smooth_pairs(fsi_pc* pc, const fsi_state* st, int32_t count, uint
   double* dinv = reinterpret_cast<double*>(pc->gcat[0]);
   if ((rc = op_diag(m, b, dinv, FSI_ELASTIC_AUG))) return rc;
   if ((rc = vec_recip(m, dinv, dinv, b.n))) return rc;
-  double *z = nullptr, *y = nullptr, *part = nullptr;
   constexpr int NB = 152;
-  FSI_CUDA(cudaMalloc(&z, sizeof(double) * 2 * b.n + sizeof(double) * NB));
-  y = z + b.n;
-  part = y + b.n;
+  // the field, its product and the mean's partial sums; freed on every return (an early
+  // return from a failed launch included), after the stream has finished with them
+  struct Scratch {
+    double* p = nullptr;
+    cudaStream_t s = nullptr;
+    ~Scratch() {
+      if (p) {
+        cudaStreamSynchronize(s);
+        cudaFree(p);
+      }
+    }
+  } buf;
+  buf.s = m->stream;
+  FSI_CUDA(cudaMalloc(&buf.p, sizeof(double) * 2 * b.n + sizeof(double) * NB));
+  double* z = buf.p;
+  double* y = z + b.n;
+  double* part = y + b.n;
   const Geom& g = m->g;
   const int nmax = std::max(g.nx, std::max(g.ny, g.nz));
   for (int32_t k = 0; k < count && rc == FSI_OK; ++k) {
@@ -1493,7 +1506,6 @@ int fsi_pc_add_smooth_pairs(fsi_pc* pc, const fsi_state* st, int32_t count, uint
     rc = fsi::pcn::add_pair(pc, y, nullptr, z, nullptr, dinv);
   }
   const cudaError_t se = cudaStreamSynchronize(m->stream);
-  cudaFree(z);
   if (rc) return rc;
   if (se != cudaSuccess) return set_error(FSI_ECUDA, cudaGetErrorString(se));
   return FSI_OK;
