@@ -31,6 +31,14 @@ the steps in the order the paper states them:
   gridcell.py  grid-cell distance and ray-casting sign with non-duplicated plane
                partitioning (Section 3, Algorithms 1 and 2).
   diagnostics.py  solid centre of mass (Section 5.2) and point tracking (Appendix C).
+  pcnet.py     the learned right preconditioner of the NS block (not in the paper): the
+               3D convolutional U-Net, its loss, weight gradients, Adam, and the
+               flexible-GMRES apply, with the bfloat16 roundings of the GPU network
+               emulated where asked.
+  fields.py    the nodal state layout and the quadrature-point fields the operators
+               share.
+  blocks.py    block bookkeeping of the partitioned solve (Section 2.5): the NS, AC
+               and B blocks and their unknowns.
 
 Parity pins for every function live in tests/test_oracle_*.py.  Where a function is
 not pinned to something outside itself, its docstring says "parity unpinned".
