@@ -781,7 +781,7 @@ def operator_rates(prof: dict, nn: int) -> dict:
 
 
 def peaks(measured=None):
-    """Roofline denominators: HBM from MEASURED_PEAKS.json (the driver's copy figure),
+    """Roofline denominators: HBM from MEASURED_PEAKS.json (a measured copy figure),
     float32 / float64 FMA rates from fsi_probe_peaks on this GPU in the same run (else
     derived from unit counts: 152 SMs x 128 FP32 lanes, 2 DFMA per clock, x 2 flop x
     the maximum SM clock)."""
